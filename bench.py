@@ -1,0 +1,390 @@
+"""Benchmark: GCUPS of batched affine-gap alignment (score + traceback + CIGAR)
+on one GB300, on the mate-rescue workload (1M unaligned 150 bp mates, each
+against an 800 bp window placed from its mate; synthetic 100 Mbp genome).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+One step = one call of the library on the whole batch: staging (read packing,
+bucketing), the score pass, the reduced direction pass, traceback, CIGAR
+compaction and results.  `value` times steps whose inputs already sit in device
+memory (sa_align_batch_dev); `e2e` times sa_align_batch from pinned host
+buffers, host<->device copies included.  Cells = sum of n*m (full matrices).
+With --impl reference the CPU oracle is timed instead, on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GCUPS (affine DP incl. traceback) at 1 GB300 vs plain form; p50/p99 request latency"
+WORKLOAD = "mate_rescue: 1M jobs, 150 bp mate (reverse-complemented) vs 800 bp window, 100 Mbp GC41 genome + 5% repeats"
+OPS_PER_CELL = 6          # minimal lane-ops per cell update (roofline)
+LANES_PER_SM = 128        # 32-bit integer lanes per SM per clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--jobs", type=int, default=1_000_000)
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving latency run")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,utilization.gpu,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 10:
+                continue
+            try:
+                rows.append(dict(sm=float(f[1]), max=float(f[2]), util=float(f[3]), hw=f[6], hwt=f[7],
+                                 swt=f[8], swp=f[9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
+        load = [r for r in rows if r["util"] >= 50] or rows
+        reasons = sorted({name for r in load for name, key in
+                          (("hw_slowdown", "hw"), ("hw_thermal_slowdown", "hwt"),
+                           ("sw_thermal_slowdown", "swt"), ("sw_power_cap", "swp"))
+                          if r[key].lower() == "active"})
+        return {"sm_mhz": statistics.median(r["sm"] for r in load), "sm_max_mhz": max(r["max"] for r in rows),
+                "reasons": reasons, "samples": len(load)}
+
+
+# ---------------------------------------------------------------------------
+
+def traffic_from_profiles():
+    """DRAM bytes per launch of the score-pass kernel from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "fill_score_mate_rescue.md")
+    src = os.path.join(ROOT, "paper_1302_5507_gb300", "csrc", "fill.cuh")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s*\(fill\.cuh sha1 ([0-9a-f]+)\)", text)
+    if not m:
+        return None
+    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    return float(m.group(1)) if m.group(2) == sha else None
+
+
+def cpu_baseline(wl, target_s: float = 8.0):
+    import oracle
+    nthreads = oracle.threads()
+    probe = wl.subset(np.arange(min(2000, wl.n_jobs)))
+    t0 = time.perf_counter()
+    oracle.align(probe, n_threads=nthreads)
+    rate = probe.cells / (time.perf_counter() - t0)
+    n = int(min(wl.n_jobs, max(2000, target_s * rate / (wl.cells / wl.n_jobs))))
+    sample = wl.subset(np.arange(n))
+    t0 = time.perf_counter()
+    oracle.align(sample, n_threads=nthreads)
+    dt = time.perf_counter() - t0
+    return {"value": sample.cells / dt / 1e9, "unit": "GCUPS", "cores": nthreads, "kind": "oracle",
+            "sample": f"first {n} of {wl.n_jobs} jobs ({sample.cells:.3g} cells, {dt:.1f} s, LOCAL + CIGAR)"}
+
+
+def make_workload(rank: int, n_jobs: int):
+    import workloads
+    return workloads.mate_rescue(seed=1, n_pairs=n_jobs, first_item=rank * n_jobs)
+
+
+def run_reference(args, rank, world):
+    import workloads  # noqa: F401
+    if rank != 0:
+        return
+    wl = make_workload(0, args.jobs)
+    import oracle
+    nthreads = oracle.threads()
+    # each step: a bounded sample (about 2 s of oracle work), same workload and metric
+    probe = wl.subset(np.arange(1000))
+    t0 = time.perf_counter()
+    oracle.align(probe, n_threads=nthreads)
+    rate = probe.cells / (time.perf_counter() - t0)
+    n = int(max(1000, 2.0 * rate / (wl.cells / wl.n_jobs)))
+    times, cells = [], 0
+    for step in range(args.warmup + args.steps):
+        sub = wl.subset(np.arange(step * 997 % max(1, wl.n_jobs - n), step * 997 % max(1, wl.n_jobs - n) + n))
+        t0 = time.perf_counter()
+        oracle.align(sub, n_threads=nthreads)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+            cells += sub.cells
+    value = cells / sum(times) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "jobs_per_step": n, "mode": "LOCAL", "scoring": "1/2/2/1",
+                       "cache": "oracle on host cores"},
+            "cpu_baseline": {"value": value, "unit": "GCUPS", "cores": nthreads, "kind": "oracle",
+                             "sample": f"{n} consecutive jobs per step of {wl.n_jobs}"},
+            "e2e": {"value": value, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+    import paper_1302_5507_gb300 as sa
+    import __graft_entry__
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    __graft_entry__.build()
+    wl = make_workload(rank, args.jobs)
+    jobs = sa.jobs_array(wl.read_off, wl.read_len, wl.flags, wl.ref_pos, wl.win_len)
+    ref = sa.Reference(wl.ref, device=local_rank)
+    params = sa.make_params(profile=True)
+    cap = sa.cigar_max_ops(wl.read_len)
+    stream = torch.cuda.Stream(device=dev)
+    d_jobs = torch.from_numpy(jobs.view(np.uint8)).to(dev)
+    d_reads = torch.from_numpy(wl.reads).to(dev)
+    d_out = torch.empty(len(jobs) * 56, dtype=torch.uint8, device=dev)
+    d_cig = torch.empty(cap, dtype=torch.int32, device=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # --- device-resident steps
+    for _ in range(args.warmup):
+        ref.align_dev(d_jobs, d_reads, d_out, d_cig, params, stream=stream)
+    barrier()
+    fill_ms, stats = [], None
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        ev0.record(stream)
+        t_host = time.perf_counter()
+        for _ in range(args.steps):
+            ref.align_dev(d_jobs, d_reads, d_out, d_cig, params, stream=stream)
+            stats = ref.stats()
+            fill_ms.append(stats["ms_fill"])
+        ev1.record(stream)
+        barrier()
+        t_host = time.perf_counter() - t_host
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    cells_rank = wl.cells
+    cells_all = cells_rank * world
+    value = cells_all * args.steps / (ms / 1e3) / 1e9
+    launches = int(stats["kernel_launches"]) * args.steps
+
+    # --- end to end from pinned host memory (sa_align_batch)
+    h_jobs = torch.from_numpy(jobs.view(np.uint8)).pin_memory()
+    h_reads = torch.from_numpy(wl.reads).pin_memory()
+    h_out = torch.empty(len(jobs) * 56, dtype=torch.uint8).pin_memory()
+    h_cig = torch.empty(cap, dtype=torch.int32).pin_memory()
+    out_np = h_out.numpy().view(sa.RESULT_DTYPE)
+    cig_np = h_cig.numpy().view(np.uint32)
+    jobs_np = h_jobs.numpy().view(sa.JOB_DTYPE)
+    reads_np = h_reads.numpy()
+    e2e_params = sa.make_params()
+    for _ in range(max(1, args.warmup - 1)):
+        ref.align(jobs_np, reads_np, e2e_params, out=out_np, cigar=cig_np, stream=None)
+    barrier()
+    t0 = time.perf_counter()
+    used = 0
+    for _ in range(args.steps):
+        _, c = ref.align(jobs_np, reads_np, e2e_params, out=out_np, cigar=cig_np, stream=None)
+        used = len(c)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = cells_all * args.steps / e2e_s / 1e9
+
+    # --- plain form on the same workload (comparison form)
+    plain = None
+    if not args.no_plain:
+        pp = sa.make_params(form=sa.SA_FORM_PLAIN, profile=True)
+        ref.align_dev(d_jobs, d_reads, d_out, d_cig, pp, stream=stream)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        nplain = max(1, min(args.steps, 2))
+        for _ in range(nplain):
+            ref.align_dev(d_jobs, d_reads, d_out, d_cig, pp, stream=stream)
+        e1.record(stream)
+        barrier()
+        pms = e0.elapsed_time(e1) / nplain
+        plain = {"value": cells_rank / (pms / 1e3) / 1e9, "unit": "GCUPS", "ms_per_step": pms,
+                 "form": "plain: 65,536-job batches, one whole-window direction fill + one traceback launch each"}
+
+    ref_stats = ref.stats()
+    clocks = clk.summary()
+    sm_mhz = clocks["sm_mhz"] or 2070.0
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    peak = n_sm * LANES_PER_SM * sm_mhz * 1e6 / OPS_PER_CELL / 1e9
+    fill_avg = float(np.mean(fill_ms)) if fill_ms else 0.0
+    achieved = cells_rank / (fill_avg / 1e3) / 1e9 if fill_avg > 0 else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GCUPS",
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic_from_profiles(),
+                "kernel": "k_fill32 score pass (score, ends, colbest, second best)",
+                "peak_basis": f"{n_sm} SMs x {LANES_PER_SM} int lanes/clk x {sm_mhz:.0f} MHz (median under load) / {OPS_PER_CELL} ops per cell, int32"}
+
+    line = None
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "jobs_per_gpu": wl.n_jobs, "cells_per_gpu": cells_rank,
+                           "mode": "LOCAL", "scoring": "match 1, mismatch 2, gap open 2, gap extend 1",
+                           "form": "batched", "cache": "inputs + direction arena larger than L2 (no flush)",
+                           "parallelism": f"independent shards x{world}"},
+                "e2e": {"value": e2e_value, "unit": "GCUPS",
+                        "h2d_bytes_per_step": int(jobs.nbytes + wl.reads.nbytes),
+                        "d2h_bytes_per_step": int(len(jobs) * 56 + used * 4)},
+                "gpu_launches": launches,
+                "roofline": roofline,
+                "clocks": clocks,
+                "phases_ms": {k: ref_stats[k] for k in ("ms_stage", "ms_fill", "ms_rect", "ms_traceback",
+                                                        "ms_finalize", "ms_total")},
+                "plain_form": plain}
+
+    # --- serving latency (continuous batching), rank 0 only
+    if rank == 0 and not args.no_serving:
+        line["serving"] = serving_run(sa, ref, wl)
+    ref.close()
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def serving_run(sa, ref, wl, n_requests: int = 40, load: float = 0.8):
+    """Poisson arrivals of requests of U[1, 50000] jobs (n U[50,250], m U[2n,6n] on the
+    same genome) at `load` x the offline batched throughput; p50/p99 submit->result."""
+    import workloads
+    sizes, ppm = workloads.serving_arrivals(seed=3, n_requests=n_requests)
+    reqs = [workloads.serving_request(wl.ref, 3, k, int(sizes[k])) for k in range(n_requests)]
+    # offline batched throughput on the same requests
+    t0 = time.perf_counter()
+    for r in reqs[:8]:
+        ref.align(sa.jobs_array(r.read_off, r.read_len, r.flags, r.ref_pos, r.win_len), r.reads)
+    offline = sum(r.cells for r in reqs[:8]) / (time.perf_counter() - t0)
+    mean_cells = float(np.mean([r.cells for r in reqs]))
+    rate = load * offline / mean_cells            # requests per second
+    gaps = -np.log(ppm.astype(np.float64) / 1e6) / rate
+    lat, done_cells = [], 0
+    import queue as _queue
+    pending = _queue.Queue()
+    with sa.Server(ref, sa.make_params(), max_inflight=4) as srv:
+        def poller():
+            while True:
+                item = pending.get()
+                if item is None:
+                    return
+                tk, ts, r = item
+                srv.poll(tk, r.n_jobs, sa.cigar_max_ops(r.read_len), timeout_ms=-1)
+                lat.append(time.perf_counter() - ts)
+        th = threading.Thread(target=poller)
+        th.start()
+        t_start = time.perf_counter()
+        t_next = t_start
+        for k, r in enumerate(reqs):
+            t_next += gaps[k]
+            while time.perf_counter() < t_next:
+                time.sleep(min(0.001, max(0.0, t_next - time.perf_counter())))
+            jobs = sa.jobs_array(r.read_off, r.read_len, r.flags, r.ref_pos, r.win_len)
+            pending.put((srv.submit(jobs, r.reads), time.perf_counter(), r))
+            done_cells += r.cells
+        pending.put(None)
+        th.join()
+        wall = time.perf_counter() - t_start
+    lat_ms = np.array(lat) * 1e3
+    return {"requests": n_requests, "offered_load": load, "offline_gcups": offline / 1e9,
+            "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+            "gcups": done_cells / wall / 1e9, "genome": "the mate-rescue genome (100 Mbp)",
+            "poll": "one poller thread in submit order (FIFO admission)"}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    try:
+        run_ours(args, rank, world, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,196 @@
+/*
+ * sa.h -- batched affine-gap alignment of short reads against candidate
+ * reference windows on one GB300 (sm_103a).
+ *
+ * The operation is the dynamic programming of SOAP3-dp's gapped stage
+ * (Luo et al., arXiv:1302.5507, Methods section 3 "GPU-accelerated dynamic
+ * programming"): for a window T of length m and a read R of length n,
+ *   I(i,j) = max(M(i,j-1) + S_GO, I(i,j-1) + S_GE)      read base against a space
+ *   D(i,j) = max(M(i-1,j) + S_GO, D(i-1,j) + S_GE)      window base against a space
+ *   M(i,j) = max(M(i-1,j-1) + delta(T[i],R[j]), I(i,j), D(i,j))
+ * with I(i,0) = D(0,j) = -inf, M(i,0) = 0 and M(0,j) = S_GO + (j-1) S_GE.
+ * SA_GLOCAL is exactly that recurrence (the whole read, placed anywhere in the
+ * window, result max_i M(i,n)).  SA_LOCAL is Smith-Waterman: every cell is
+ * floored at 0, M(0,j) = 0 and the result is the best cell.
+ * The windows come from the candidate regions of the paper's steps 2 and 3
+ * (Methods section 3 and "Paired-end alignment": the region next to a mapped
+ * mate, inferred from the insert-size bounds); the library takes them as
+ * (position, length) into a device-resident reference.
+ *
+ * Every result is exact integer arithmetic and identical, field by field, to
+ * the plain full-matrix definition (including the tie rules below), whatever
+ * the internal width (16-bit packed with exact overflow detection, or 32-bit).
+ *
+ * Conventions
+ *  - Scores are BWA magnitudes (the paper adopts BWA's scoring scheme): match
+ *    a, mismatch b, gap open o, gap extend e, all >= 0; a gap of length L costs
+ *    o + L*e.  In the paper's signed form S_MA = a, S_MI = -b, S_GO = -(o+e),
+ *    S_GE = -e.  Limits: a, b, o + e <= 16383 and n * max(a, b, o + e) < 2^28.
+ *  - Best cell: the first maximum in window-major order (smallest reference
+ *    end, then smallest read end).  LOCAL with no positive cell: no alignment
+ *    (SA_RES_EMPTY, score 0, coordinates -1, second SA_NO_SCORE).
+ *  - Traceback from the best cell: stop (LOCAL cell value 0, or a border) >
+ *    diagonal > deletion > insertion; a gap run is extended only when that is
+ *    strictly better than opening it.  GLOCAL reaching the window start with
+ *    read bases left emits them as an insertion.
+ *  - Second best: colbest(i) = max_j M(i,j) (LOCAL) or M(i,n) (GLOCAL); the
+ *    largest colbest(i) over columns with |i - i*| >= n, smallest such i.
+ *  - CIGAR: BAM encoding (length << 4 | op), M=0 I=1 D=2 S=4; LOCAL soft-clips
+ *    the unaligned read ends.  At most 2n+3 ops per job.
+ *
+ * Ownership and errors
+ *  - The caller owns every buffer it passes.  sa_create_reference and
+ *    sa_submit copy their inputs before returning.  Handles are released only
+ *    by the matching destroy call.  No C++ exception crosses this interface.
+ *  - Every call returns SA_OK (0), SA_PENDING (1, sa_poll only) or a negative
+ *    error code; sa_last_error() gives a message for the calling thread.
+ *  - All GPU work runs on one device (the one the reference was created on).
+ */
+#ifndef SA_H
+#define SA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define SA_OK         0
+#define SA_PENDING    1     /* sa_poll: the request is not finished yet */
+#define SA_EINVAL    -1     /* bad argument: non-ACGT base, n or m out of range, window past the reference end */
+#define SA_ENOMEM    -2     /* device or host memory could not be obtained */
+#define SA_ECUDA     -3     /* a CUDA call failed (message in sa_last_error) */
+#define SA_ETIMEOUT  -4     /* sa_poll: timeout_ms elapsed */
+#define SA_EOVERFLOW -5     /* the CIGAR buffer is too small; *cigar_used says how much is needed */
+#define SA_ENOTFOUND -6     /* sa_poll: unknown or already collected ticket */
+#define SA_EBUSY     -7     /* sa_submit: the request can never fit the server's memory budget */
+
+#define SA_NO_SCORE  INT32_MIN   /* "no second-best location" */
+
+#define SA_MAX_READ   1024u      /* longest read (n) */
+#define SA_MAX_WINDOW 65536u     /* longest window (m) */
+
+/* job flags */
+#define SA_RC 1u                 /* align the reverse complement of the read */
+
+/* result flags */
+#define SA_RES_EMPTY     1u      /* LOCAL: no positive-scoring alignment */
+#define SA_RES_BELOW_MIN 2u      /* score < min_score: no traceback was run */
+
+typedef struct {
+    int32_t match, mismatch, gap_open, gap_extend;   /* BWA magnitudes, >= 0 */
+} sa_scoring;
+
+typedef enum { SA_LOCAL = 0, SA_GLOCAL = 1 } sa_mode;
+
+/* execution form (same results; see sa_align_batch) */
+typedef enum {
+    SA_FORM_BATCHED = 0,   /* length-bucketed persistent launches, score pass + reduced traceback */
+    SA_FORM_PLAIN   = 1    /* fixed-size batches, one full-direction fill launch + one traceback each */
+} sa_form;
+
+typedef struct {
+    sa_scoring sc;
+    int32_t mode;          /* sa_mode */
+    int32_t want_cigar;    /* 0: score, ends and second best only (begins -1, no CIGAR) */
+    int32_t width;         /* 0 auto, 16 (packed 16-bit + exact int32 rerun), 32 */
+    int32_t min_score;     /* results below it get SA_RES_BELOW_MIN and no traceback; INT32_MIN disables */
+    int32_t form;          /* sa_form */
+    int32_t profile;       /* nonzero: time each phase with CUDA events (sa_last_stats) */
+    int32_t _reserved[2];
+} sa_params;
+
+typedef struct {           /* 32 bytes */
+    uint64_t read_off;     /* offset of the read in the reads buffer */
+    uint32_t read_len;     /* n, 1..SA_MAX_READ */
+    uint32_t flags;        /* SA_RC */
+    uint64_t ref_pos;      /* window start in the reference (0-based) */
+    uint32_t win_len;      /* m, 1..SA_MAX_WINDOW, ref_pos + m <= reference length */
+    uint32_t _pad;
+} sa_job;
+
+typedef struct {           /* 56 bytes */
+    int32_t score;         /* best score (0 with SA_RES_EMPTY) */
+    int32_t second;        /* second best at a distinct location, SA_NO_SCORE if none */
+    int32_t read_begin;    /* 0-based in the (reverse-complemented if SA_RC) read; -1 if no traceback */
+    int32_t read_end;      /* exclusive */
+    int64_t ref_begin;     /* absolute reference coordinate; -1 if no traceback */
+    int64_t ref_end;       /* exclusive */
+    int64_t second_ref_end;/* exclusive end column of the second best; -1 if none */
+    uint32_t cigar_off;    /* first op in the cigar buffer */
+    uint32_t cigar_len;    /* number of ops */
+    uint32_t flags;        /* SA_RES_* */
+    uint32_t _pad;
+} sa_result;
+
+typedef struct {           /* statistics of the last call on a reference or server */
+    uint64_t jobs, cells;          /* sum of n*m */
+    uint64_t rect_cells;           /* cells of the direction-bit pass */
+    uint32_t overflow_reruns;      /* jobs recomputed in 32-bit after a 16-bit overflow */
+    uint32_t waves;                /* direction-arena waves */
+    uint32_t fill_launches;        /* score-pass kernel launches */
+    uint32_t kernel_launches;      /* all kernels launched by the call */
+    float ms_stage, ms_fill, ms_rerun, ms_rect, ms_traceback, ms_finalize;  /* with profile != 0 */
+    float ms_total;                /* device time of the whole call (profile != 0) */
+} sa_stats;
+
+typedef struct sa_reference sa_reference;
+typedef struct sa_server sa_server;
+
+/* Default parameters: scoring 1/2/2/1 (the BWA-form scheme consistent with the
+ * paper's default tolerance of one gap up to 68 bp or 23 one-base gaps for a
+ * 100 bp read), LOCAL, CIGAR on, width auto, min_score INT32_MIN, batched form. */
+void sa_default_params(sa_params* p);
+
+/* Pack len ACGT characters (case-insensitive; anything else is SA_EINVAL) to a
+ * 2-bit device-resident reference on `device`.  The input is copied. */
+int sa_create_reference(const char* acgt, uint64_t len, int device, sa_reference** out);
+int sa_destroy_reference(sa_reference* ref);
+uint64_t sa_reference_length(const sa_reference* ref);
+
+/* Align n_jobs jobs.  Host buffers: jobs[n_jobs], reads[reads_len] (ASCII),
+ * out[n_jobs], cigar[cigar_cap] (ops, compacted in job order; cigar_used, if
+ * not NULL, receives the number of ops written or needed).  cuda_stream is a
+ * cudaStream_t or NULL for a library-owned stream; the call returns when the
+ * results are in `out`.  Inputs are validated; on an error nothing is written
+ * to `out`.  Calls on the same reference are serialised. */
+int sa_align_batch(sa_reference* ref, const sa_params* params, const sa_job* jobs, uint32_t n_jobs,
+                   const char* reads, uint64_t reads_len, sa_result* out, uint32_t* cigar,
+                   uint64_t cigar_cap, uint64_t* cigar_used, void* cuda_stream);
+
+/* The same with every buffer in device memory of the reference's device
+ * (d_jobs, d_reads, d_out, d_cigar); the work is queued on cuda_stream and the
+ * call returns after it completes.  cigar_used is a host pointer. */
+int sa_align_batch_dev(sa_reference* ref, const sa_params* params, const sa_job* d_jobs,
+                       uint32_t n_jobs, const char* d_reads, uint64_t reads_len, sa_result* d_out,
+                       uint32_t* d_cigar, uint64_t cigar_cap, uint64_t* cigar_used,
+                       void* cuda_stream);
+
+/* Statistics of the last sa_align_batch / sa_align_batch_dev call on ref. */
+int sa_last_stats(const sa_reference* ref, sa_stats* out);
+
+/* Serving: a background thread admits submitted requests while device memory
+ * (hbm_budget bytes, 0 = 80% of free memory) and in-flight slots allow, and runs
+ * them on a pool of streams, so requests overlap on the device.  The reference
+ * stays device-resident.  max_inflight = 0 picks a default. */
+int sa_server_create(sa_reference* ref, const sa_params* params, uint64_t hbm_budget,
+                     uint32_t max_inflight, sa_server** out);
+/* Queue one request; jobs and reads are copied before the call returns. */
+int sa_submit(sa_server* srv, const sa_job* jobs, uint32_t n_jobs, const char* reads,
+              uint64_t reads_len, uint64_t* ticket);
+/* Wait up to timeout_ms (0 = just check, < 0 = forever) for a request.  On
+ * SA_OK the results are copied to out/cigar and the ticket is released; on
+ * SA_PENDING / SA_ETIMEOUT nothing is written.  SA_EOVERFLOW keeps the ticket. */
+int sa_poll(sa_server* srv, uint64_t ticket, int timeout_ms, sa_result* out, uint32_t* cigar,
+            uint64_t cigar_cap, uint64_t* cigar_used);
+int sa_server_destroy(sa_server* srv);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* sa_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SA_H */

@@ -14,12 +14,13 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import subprocess
 
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SO = os.path.join(_HERE, "liboracle.so")
+_SO = os.path.join(_HERE, f"liboracle.{platform.machine()}.so")
 _lib = None
 
 LOCAL, GLOCAL = 0, 1

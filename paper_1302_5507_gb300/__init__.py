@@ -1,0 +1,306 @@
+"""Python binding of libsa (include/sa.h): batched affine-gap alignment of short
+reads against candidate reference windows on one GB300.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``libsa.so`` built from ``csrc/`` (``python -m paper_1302_5507_gb300.build``
+or ``__graft_entry__.build()``).  Importing the binding without the library
+raises; there is no CPU fallback.
+
+The C entry points are exposed under their own names (``sa_create_reference``,
+``sa_align_batch``, ``sa_align_batch_dev``, ``sa_server_create``, ``sa_submit``,
+``sa_poll``, ...), and ``Reference`` / ``Server`` wrap them for numpy and torch
+buffers.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsa.so")
+
+SA_OK, SA_PENDING = 0, 1
+SA_EINVAL, SA_ENOMEM, SA_ECUDA, SA_ETIMEOUT, SA_EOVERFLOW, SA_ENOTFOUND, SA_EBUSY = -1, -2, -3, -4, -5, -6, -7
+SA_NO_SCORE = -(2 ** 31)
+SA_LOCAL, SA_GLOCAL = 0, 1
+SA_FORM_BATCHED, SA_FORM_PLAIN = 0, 1
+SA_RC = 1
+SA_RES_EMPTY, SA_RES_BELOW_MIN = 1, 2
+SA_MAX_READ, SA_MAX_WINDOW = 1024, 65536
+OPS = "MIDNSHP=X"
+
+
+class sa_scoring(ctypes.Structure):
+    _fields_ = [("match", ctypes.c_int32), ("mismatch", ctypes.c_int32),
+                ("gap_open", ctypes.c_int32), ("gap_extend", ctypes.c_int32)]
+
+
+class sa_params(ctypes.Structure):
+    _fields_ = [("sc", sa_scoring), ("mode", ctypes.c_int32), ("want_cigar", ctypes.c_int32),
+                ("width", ctypes.c_int32), ("min_score", ctypes.c_int32), ("form", ctypes.c_int32),
+                ("profile", ctypes.c_int32), ("_reserved", ctypes.c_int32 * 2)]
+
+
+class sa_stats(ctypes.Structure):
+    _fields_ = [("jobs", ctypes.c_uint64), ("cells", ctypes.c_uint64), ("rect_cells", ctypes.c_uint64),
+                ("overflow_reruns", ctypes.c_uint32), ("waves", ctypes.c_uint32),
+                ("fill_launches", ctypes.c_uint32), ("kernel_launches", ctypes.c_uint32),
+                ("ms_stage", ctypes.c_float), ("ms_fill", ctypes.c_float), ("ms_rerun", ctypes.c_float),
+                ("ms_rect", ctypes.c_float), ("ms_traceback", ctypes.c_float),
+                ("ms_finalize", ctypes.c_float), ("ms_total", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+JOB_DTYPE = np.dtype([("read_off", np.uint64), ("read_len", np.uint32), ("flags", np.uint32),
+                      ("ref_pos", np.uint64), ("win_len", np.uint32), ("_pad", np.uint32)])
+RESULT_DTYPE = np.dtype([("score", np.int32), ("second", np.int32), ("read_begin", np.int32),
+                         ("read_end", np.int32), ("ref_begin", np.int64), ("ref_end", np.int64),
+                         ("second_ref_end", np.int64), ("cigar_off", np.uint32),
+                         ("cigar_len", np.uint32), ("flags", np.uint32), ("_pad", np.uint32)])
+assert JOB_DTYPE.itemsize == 32 and RESULT_DTYPE.itemsize == 56
+
+_lib = None
+_VP, _U32, _U64, _I32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32
+
+
+def lib():
+    """Load libsa.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(the CUDA library is required; there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        L.sa_default_params.argtypes = [ctypes.POINTER(sa_params)]
+        L.sa_default_params.restype = None
+        L.sa_create_reference.argtypes = [ctypes.c_char_p, _U64, ctypes.c_int, ctypes.POINTER(_VP)]
+        L.sa_destroy_reference.argtypes = [_VP]
+        L.sa_reference_length.argtypes = [_VP]
+        L.sa_reference_length.restype = _U64
+        L.sa_align_batch.argtypes = [_VP, ctypes.POINTER(sa_params), _VP, _U32, _VP, _U64, _VP, _VP,
+                                     _U64, ctypes.POINTER(_U64), _VP]
+        L.sa_align_batch_dev.argtypes = L.sa_align_batch.argtypes
+        L.sa_last_stats.argtypes = [_VP, ctypes.POINTER(sa_stats)]
+        L.sa_server_create.argtypes = [_VP, ctypes.POINTER(sa_params), _U64, _U32, ctypes.POINTER(_VP)]
+        L.sa_submit.argtypes = [_VP, _VP, _U32, _VP, _U64, ctypes.POINTER(_U64)]
+        L.sa_poll.argtypes = [_VP, _U64, ctypes.c_int, _VP, _VP, _U64, ctypes.POINTER(_U64)]
+        L.sa_server_destroy.argtypes = [_VP]
+        L.sa_last_error.restype = ctypes.c_char_p
+        for name in ("sa_create_reference", "sa_destroy_reference", "sa_align_batch",
+                     "sa_align_batch_dev", "sa_last_stats", "sa_server_create", "sa_submit",
+                     "sa_poll", "sa_server_destroy"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+class SAError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libsa error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc):
+    if rc < 0:
+        raise SAError(rc, lib().sa_last_error().decode(errors="replace"))
+    return rc
+
+
+# ---------------------------------------------------------------------------
+# the C entry points under their own names
+
+def sa_default_params() -> sa_params:
+    p = sa_params()
+    lib().sa_default_params(ctypes.byref(p))
+    return p
+
+
+def sa_last_error() -> str:
+    return lib().sa_last_error().decode(errors="replace")
+
+
+def sa_create_reference(acgt, device: int = 0):
+    buf = acgt if isinstance(acgt, (bytes, bytearray)) else np.ascontiguousarray(acgt, np.uint8).tobytes()
+    h = _VP()
+    _check(lib().sa_create_reference(buf, len(buf), device, ctypes.byref(h)))
+    return h
+
+
+def sa_destroy_reference(h):
+    return _check(lib().sa_destroy_reference(h))
+
+
+def sa_align_batch(h, params, jobs_ptr, n_jobs, reads_ptr, reads_len, out_ptr, cigar_ptr, cigar_cap,
+                   stream=None):
+    used = _U64(0)
+    rc = lib().sa_align_batch(h, ctypes.byref(params), jobs_ptr, n_jobs, reads_ptr, reads_len, out_ptr,
+                              cigar_ptr, cigar_cap, ctypes.byref(used), stream)
+    return rc, used.value
+
+
+def sa_align_batch_dev(h, params, jobs_ptr, n_jobs, reads_ptr, reads_len, out_ptr, cigar_ptr, cigar_cap,
+                       stream=None):
+    used = _U64(0)
+    rc = lib().sa_align_batch_dev(h, ctypes.byref(params), jobs_ptr, n_jobs, reads_ptr, reads_len,
+                                  out_ptr, cigar_ptr, cigar_cap, ctypes.byref(used), stream)
+    return rc, used.value
+
+
+def sa_last_stats(h) -> sa_stats:
+    s = sa_stats()
+    _check(lib().sa_last_stats(h, ctypes.byref(s)))
+    return s
+
+
+def sa_server_create(h, params, hbm_budget=0, max_inflight=0):
+    s = _VP()
+    _check(lib().sa_server_create(h, ctypes.byref(params), hbm_budget, max_inflight, ctypes.byref(s)))
+    return s
+
+
+def sa_submit(s, jobs_ptr, n_jobs, reads_ptr, reads_len):
+    t = _U64(0)
+    _check(lib().sa_submit(s, jobs_ptr, n_jobs, reads_ptr, reads_len, ctypes.byref(t)))
+    return t.value
+
+
+def sa_poll(s, ticket, timeout_ms, out_ptr, cigar_ptr, cigar_cap):
+    used = _U64(0)
+    rc = lib().sa_poll(s, ticket, timeout_ms, out_ptr, cigar_ptr, cigar_cap, ctypes.byref(used))
+    return rc, used.value
+
+
+def sa_server_destroy(s):
+    return _check(lib().sa_server_destroy(s))
+
+
+# ---------------------------------------------------------------------------
+# numpy / torch conveniences
+
+def make_params(scoring=(1, 2, 2, 1), mode=SA_LOCAL, want_cigar=True, width=0,
+                min_score=SA_NO_SCORE, form=SA_FORM_BATCHED, profile=False) -> sa_params:
+    p = sa_default_params()
+    p.sc.match, p.sc.mismatch, p.sc.gap_open, p.sc.gap_extend = scoring
+    p.mode, p.want_cigar, p.width = mode, int(bool(want_cigar)), width
+    p.min_score, p.form, p.profile = min_score, form, int(bool(profile))
+    return p
+
+
+def jobs_array(read_off, read_len, flags, ref_pos, win_len) -> np.ndarray:
+    j = np.zeros(len(read_len), JOB_DTYPE)
+    j["read_off"], j["read_len"], j["flags"] = read_off, read_len, flags
+    j["ref_pos"], j["win_len"] = ref_pos, win_len
+    return j
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None and a.size else None
+
+
+def cigar_max_ops(read_len) -> int:
+    return int((2 * np.asarray(read_len, np.int64) + 3).sum())
+
+
+def cigar_string(ops) -> str:
+    return "".join(f"{int(x) >> 4}{OPS[int(x) & 15]}" for x in ops)
+
+
+class Reference:
+    """A device-resident 2-bit reference (sa_create_reference)."""
+
+    def __init__(self, acgt, device: int = 0):
+        self.h = sa_create_reference(acgt, device)
+        self.device = device
+
+    def close(self):
+        if self.h:
+            sa_destroy_reference(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __len__(self):
+        return int(lib().sa_reference_length(self.h))
+
+    def stats(self) -> dict:
+        return sa_last_stats(self.h).as_dict()
+
+    def align(self, jobs: np.ndarray, reads: np.ndarray, params: sa_params | None = None,
+              out: np.ndarray | None = None, cigar: np.ndarray | None = None, stream=None):
+        """Host buffers in, host results out (sa_align_batch)."""
+        params = params or make_params()
+        jobs = np.ascontiguousarray(jobs, JOB_DTYPE)
+        reads = np.ascontiguousarray(reads, np.uint8)
+        n = len(jobs)
+        if out is None:
+            out = np.zeros(n, RESULT_DTYPE)
+        if cigar is None:
+            cigar = np.zeros(max(1, cigar_max_ops(jobs["read_len"])), np.uint32)
+        rc, used = sa_align_batch(self.h, params, _ptr(jobs), n, _ptr(reads), reads.size, _ptr(out),
+                                  _ptr(cigar), cigar.size, stream)
+        _check(rc)
+        return out, cigar[:used]
+
+    def align_dev(self, jobs, reads, out, cigar, params: sa_params | None = None, stream=None):
+        """Device tensors (torch) in and out (sa_align_batch_dev); returns ops used."""
+        params = params or make_params()
+        st = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+        rc, used = sa_align_batch_dev(self.h, params, ctypes.c_void_p(jobs.data_ptr()),
+                                      jobs.numel() * jobs.element_size() // 32,
+                                      ctypes.c_void_p(reads.data_ptr()), reads.numel(),
+                                      ctypes.c_void_p(out.data_ptr()),
+                                      ctypes.c_void_p(cigar.data_ptr()) if cigar is not None else None,
+                                      cigar.numel() if cigar is not None else 0, st)
+        _check(rc)
+        return used
+
+
+class Server:
+    """Serving loop (sa_server_create / sa_submit / sa_poll)."""
+
+    def __init__(self, ref: Reference, params: sa_params | None = None, hbm_budget: int = 0,
+                 max_inflight: int = 0):
+        self.ref = ref
+        self.h = sa_server_create(ref.h, params or make_params(), hbm_budget, max_inflight)
+
+    def submit(self, jobs: np.ndarray, reads: np.ndarray) -> int:
+        jobs = np.ascontiguousarray(jobs, JOB_DTYPE)
+        reads = np.ascontiguousarray(reads, np.uint8)
+        return sa_submit(self.h, _ptr(jobs), len(jobs), _ptr(reads), reads.size)
+
+    def poll(self, ticket: int, n_jobs: int, max_ops: int, timeout_ms: int = -1):
+        """(rc, results, cigar) -- results/cigar are None unless rc == SA_OK."""
+        out = np.zeros(n_jobs, RESULT_DTYPE)
+        cigar = np.zeros(max(1, max_ops), np.uint32)
+        rc, used = sa_poll(self.h, ticket, timeout_ms, _ptr(out), _ptr(cigar), cigar.size)
+        if rc == SA_OK:
+            return rc, out, cigar[:used]
+        if rc in (SA_PENDING, SA_ETIMEOUT):
+            return rc, None, None
+        _check(rc)
+        return rc, None, None
+
+    def close(self):
+        if self.h:
+            sa_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

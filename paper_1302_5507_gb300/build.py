@@ -1,0 +1,88 @@
+"""Build libsa.so (the CUDA library) in-tree with nvcc for sm_103a.
+
+One translation unit per wavefront configuration (fill_cfg.cu with -DSA_CFG=c)
+plus the staging, dispatch and API units, compiled in parallel, then linked
+into ``paper_1302_5507_gb300/libsa.so``.  Objects go to ``_build/`` next to this
+file and are reused while their sources are unchanged.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import glob
+import os
+import platform
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+INCLUDE = os.path.join(ROOT, "include")
+OUT = os.path.join(HERE, "libsa.so")
+BUILD = os.path.join(HERE, "_build")
+NUM_CFG = 14
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", f"-I{INCLUDE}", f"-I{CSRC}",
+         "--expt-relaxed-constexpr"]
+
+
+def _nvcc() -> str:
+    for cand in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", shutil.which("nvcc")):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libsa")
+
+
+def _units():
+    units = [(os.path.join(CSRC, "fill_cfg.cu"), f"fill_cfg{c}.o", [f"-DSA_CFG={c}"])
+             for c in range(NUM_CFG)]
+    for name in ("fill_dispatch.cu", "stage.cu", "api.cu"):
+        units.append((os.path.join(CSRC, name), name.replace(".cu", ".o"), []))
+    return units
+
+
+def _deps_mtime() -> float:
+    files = glob.glob(os.path.join(CSRC, "*.cu*")) + glob.glob(os.path.join(CSRC, "*.h")) + \
+        [os.path.join(INCLUDE, "sa.h"), os.path.abspath(__file__)]
+    return max(os.path.getmtime(f) for f in files)
+
+
+def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -> str:
+    os.makedirs(BUILD, exist_ok=True)
+    dep = _deps_mtime()
+    # objects and library built on another machine type are never reused
+    stamp = os.path.join(BUILD, "machine")
+    machine = platform.machine()
+    if not os.path.exists(stamp) or open(stamp).read().strip() != machine:
+        force = True
+    if not force and os.path.exists(OUT) and os.path.getmtime(OUT) >= dep:
+        return OUT
+    nvcc = _nvcc()
+    todo = []
+    for src, obj, extra in _units():
+        objp = os.path.join(BUILD, obj)
+        if force or not os.path.exists(objp) or os.path.getmtime(objp) < dep:
+            todo.append([nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", objp])
+    jobs = jobs or max(1, min(len(todo) or 1, os.cpu_count() or 1))
+
+    def run(cmd):
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
+        if verbose and r.stderr:
+            sys.stderr.write(r.stderr)
+
+    with cf.ThreadPoolExecutor(jobs) as ex:
+        list(ex.map(run, todo))
+    objs = [os.path.join(BUILD, obj) for _, obj, _ in _units()]
+    tmp = OUT + ".tmp"
+    subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], check=True, capture_output=True)
+    os.replace(tmp, OUT)
+    with open(stamp, "w") as f:
+        f.write(machine)
+    return OUT
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose=True))

@@ -1,0 +1,898 @@
+// C ABI of libsa and its host runtime: device-resident reference, per-context
+// workspaces, the batched and plain execution forms, and the serving loop.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "kernels.h"
+
+using namespace sa;
+
+// ---------------------------------------------------------------------------
+// errors
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CU(expr)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (expr);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            cudaGetLastError();                                                         \
+            return fail(e_ == cudaErrorMemoryAllocation ? SA_ENOMEM : SA_ECUDA,         \
+                        "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_),         \
+                        __FILE__, __LINE__);                                            \
+        }                                                                               \
+    } while (0)
+
+#define TRY(expr)                     \
+    do {                              \
+        int rc_ = (expr);             \
+        if (rc_ != SA_OK) return rc_; \
+    } while (0)
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    int ensure(size_t bytes, const char* what) {
+        if (bytes <= cap && p) return SA_OK;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        size_t nb = std::max<size_t>(bytes + bytes / 8, 1 << 16);
+        cudaError_t e = cudaMalloc(&p, nb);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return fail(SA_ENOMEM, "cudaMalloc of %zu bytes for %s failed: %s", nb, what,
+                        cudaGetErrorString(e));
+        }
+        cap = nb;
+        return SA_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// layout of the plan block (device, mirrored to pinned host memory)
+struct PlanBlock {
+    PlanStats st;
+    uint32_t hist[kNumKeys];
+    uint32_t key_off[kNumKeys + 1];
+    uint32_t cursor[kNumKeys];
+    uint32_t cfg_begin[kNumCfg + 1];
+    uint32_t _pad;
+    uint64_t totals[4];
+};
+
+// Device buffers of one computation at a time (grown on demand, reused).
+struct Workspace {
+    DevBuf jobs, reads, out, cigar;          // inputs/outputs of the host-buffer entry points
+    DevBuf key, order, rpack, state, rect, tb, count, coff, sizes, offs, bsum;
+    DevBuf colbest, tmp_ops, arena, plan, counters;
+    PlanBlock* h_plan = nullptr;             // pinned mirror of the plan block
+    cudaEvent_t ev[16] = {};
+    bool ev_ok = false;
+    void release() {
+        DevBuf* all[] = {&jobs, &reads, &out, &cigar, &key, &order, &rpack, &state, &rect, &tb,
+                         &count, &coff, &sizes, &offs, &bsum, &colbest, &tmp_ops, &arena,
+                         &plan, &counters};
+        for (DevBuf* b : all) b->release();
+        if (h_plan) cudaFreeHost(h_plan);
+        h_plan = nullptr;
+        if (ev_ok)
+            for (auto& e : ev) cudaEventDestroy(e);
+        ev_ok = false;
+    }
+};
+
+// What a computation needs: the reference and a workspace of its own.
+struct Ctx {
+    const uint32_t* d_words;
+    uint64_t len;
+    int num_sms;
+    Workspace* ws;
+    sa_stats* last;
+};
+
+}  // namespace
+
+struct sa_reference {
+    int device = 0;
+    uint64_t len = 0;
+    uint32_t* d_words = nullptr;
+    int num_sms = 0;
+    cudaStream_t own = nullptr;
+    std::mutex mu;
+    Workspace ws;
+    sa_stats last{};
+    Ctx ctx() { return Ctx{d_words, len, num_sms, &ws, &last}; }
+};
+
+// ---------------------------------------------------------------------------
+// the computation
+
+namespace {
+
+int check_params(const sa_params* p, Score* sc) {
+    if (!p) return fail(SA_EINVAL, "params is NULL");
+    const sa_scoring& s = p->sc;
+    if (s.match < 0 || s.mismatch < 0 || s.gap_open < 0 || s.gap_extend < 0)
+        return fail(SA_EINVAL, "scores are magnitudes and must be >= 0");
+    if (s.match > 16383 || s.mismatch > 16383 || (int64_t)s.gap_open + s.gap_extend > 16383)
+        return fail(SA_EINVAL, "match, mismatch and gap_open + gap_extend must be <= 16383");
+    if (p->mode != SA_LOCAL && p->mode != SA_GLOCAL) return fail(SA_EINVAL, "mode must be SA_LOCAL or SA_GLOCAL");
+    if (p->width != 0 && p->width != 16 && p->width != 32) return fail(SA_EINVAL, "width must be 0, 16 or 32");
+    if (p->form != SA_FORM_BATCHED && p->form != SA_FORM_PLAIN) return fail(SA_EINVAL, "unknown form");
+    sc->a = s.match;
+    sc->b = -s.mismatch;
+    sc->GO = -(s.gap_open + s.gap_extend);
+    sc->GE = -s.gap_extend;
+    sc->dm = sc->a - sc->GO;
+    sc->dx = sc->b - sc->GO;
+    sc->mode = p->mode;
+    return SA_OK;
+}
+
+int ensure_events(Workspace& ws) {
+    if (ws.ev_ok) return SA_OK;
+    for (auto& e : ws.ev) CU(cudaEventCreate(&e));
+    ws.ev_ok = true;
+    return SA_OK;
+}
+
+struct Timer {
+    Workspace& ws;
+    cudaStream_t st;
+    bool on;
+    int next = 0;
+    Timer(Workspace& w, cudaStream_t s, bool enabled) : ws(w), st(s), on(enabled) {}
+    int mark() {
+        if (!on || next >= 16) return -1;
+        cudaEventRecord(ws.ev[next], st);
+        return next++;
+    }
+    float ms(int a, int b) {
+        if (!on || a < 0 || b < 0) return 0.f;
+        float t = 0.f;
+        cudaEventSynchronize(ws.ev[b]);
+        cudaEventElapsedTime(&t, ws.ev[a], ws.ev[b]);
+        return t;
+    }
+};
+
+constexpr uint32_t kPlainBatch = 65536;     // jobs per launch of the plain form
+constexpr int kBlock = 128;
+
+int check_bad_read(PlanBlock* dp, PlanBlock* hp, cudaStream_t st) {
+    CU(cudaMemcpyAsync(&hp->st.bad_read, &dp->st.bad_read, 4, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (hp->st.bad_read != 0xffffffffu)
+        return fail(SA_EINVAL, "job %u: read has a base other than A, C, G, T", hp->st.bad_read);
+    return SA_OK;
+}
+
+// The whole computation on device buffers.  If grow_cigar is given, the ops
+// go to that (grown) buffer instead of d_cigar; cigar_cap still bounds them.
+int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs, uint32_t n_jobs,
+               const char* d_reads, uint64_t reads_len, sa_result* d_out, uint32_t* d_cigar,
+               uint64_t cigar_cap, uint64_t* cigar_used, DevBuf* grow_cigar, cudaStream_t st) {
+    Workspace& ws = *X.ws;
+    sa_stats stats{};
+    stats.jobs = n_jobs;
+    if (cigar_used) *cigar_used = 0;
+    if (n_jobs == 0) {
+        *X.last = stats;
+        return SA_OK;
+    }
+    const bool plain = P->form == SA_FORM_PLAIN;
+    const bool want_cigar = P->want_cigar != 0;
+    const int mode = P->mode;
+    const int32_t min_score = P->min_score;
+    if (P->profile) TRY(ensure_events(ws));
+    Timer tm(ws, st, P->profile != 0);
+    const int t0 = tm.mark();
+    uint32_t launches = 0;
+
+    // --- plan: validation, buckets, statistics
+    TRY(ws.plan.ensure(sizeof(PlanBlock), "plan"));
+    if (!ws.h_plan) CU(cudaMallocHost((void**)&ws.h_plan, sizeof(PlanBlock)));
+    PlanBlock* dp = ws.plan.as<PlanBlock>();
+    PlanBlock* hp = ws.h_plan;
+    CU(cudaMemsetAsync(dp, 0, sizeof(PlanBlock), st));
+    CU(cudaMemsetAsync(&dp->st.bad_job, 0xff, sizeof(uint32_t) * 2, st));
+    TRY(ws.key.ensure((size_t)n_jobs * sizeof(uint16_t), "keys"));
+    TRY(ws.counters.ensure(256 * sizeof(uint32_t), "counters"));
+    CU(cudaMemsetAsync(ws.counters.p, 0, 256 * sizeof(uint32_t), st));
+    int counter_next = 0;
+    launch_plan(d_jobs, n_jobs, reads_len, (int64_t)X.len, ws.key.as<uint16_t>(), dp->hist, &dp->st, st);
+    launches++;
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(hp, dp, offsetof(PlanBlock, key_off), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (hp->st.bad_job != 0xffffffffu)
+        return fail(SA_EINVAL, "job %u is invalid (read length 1..%u, window 1..%u inside the reference, "
+                    "read inside the reads buffer, flags SA_RC only)", hp->st.bad_job, SA_MAX_READ, SA_MAX_WINDOW);
+    const uint32_t max_n = hp->st.max_n, max_m = hp->st.max_m;
+    stats.cells = hp->st.cells;
+    uint32_t cfg_count[kNumCfg], cfg_begin[kNumCfg + 1];
+    {
+        uint32_t acc = 0;
+        for (int c = 0; c < kNumCfg; c++) {
+            cfg_begin[c] = acc;
+            uint32_t s = 0;
+            for (int k = 0; k < kNumSizeCls; k++) s += hp->hist[c * kNumSizeCls + k];
+            cfg_count[c] = s;
+            acc += s;
+        }
+        cfg_begin[kNumCfg] = acc;
+    }
+    const int plain_cfg = cfg_for_rows((int)max_n);
+
+    // --- buffers
+    const uint32_t rw = (max_n + 15) / 16;
+    TRY(ws.order.ensure((size_t)n_jobs * 4, "order"));
+    TRY(ws.rpack.ensure((size_t)n_jobs * rw * 4, "packed reads"));
+    TRY(ws.state.ensure((size_t)n_jobs * sizeof(JobState), "job state"));
+    TRY(ws.rect.ensure((size_t)n_jobs * sizeof(Rect), "rectangles"));
+    TRY(ws.tb.ensure((size_t)n_jobs * sizeof(TbOut), "traceback"));
+    TRY(ws.count.ensure((size_t)n_jobs * 4, "cigar counts"));
+    TRY(ws.coff.ensure((size_t)n_jobs * 8, "cigar offsets"));
+    TRY(ws.sizes.ensure((size_t)n_jobs * 8, "rect sizes"));
+    TRY(ws.offs.ensure((size_t)n_jobs * 8, "rect offsets"));
+    TRY(ws.bsum.ensure(scan_bsum_len(n_jobs) * 8, "scan"));
+    const uint32_t tmp_stride = 2 * max_n + 3;
+    if (want_cigar) TRY(ws.tmp_ops.ensure((size_t)n_jobs * tmp_stride * 4, "cigar scratch"));
+    CU(cudaMemcpyAsync(dp->cfg_begin, cfg_begin, sizeof(cfg_begin), cudaMemcpyHostToDevice, st));
+
+    // persistent grids: resident 128-thread blocks per SM of each kernel
+    auto grid_for = [&](int cfg, int kind) {
+        int bps = fill_max_blocks_per_sm(cfg, kind, mode);
+        if (bps < 1) bps = 1;
+        return X.num_sms * bps;
+    };
+    int max_groups = 1;
+    for (int c = 0; c < kNumCfg; c++) {
+        if (plain ? c != plain_cfg : !cfg_count[c]) continue;
+        const int kind = plain ? (int)kFillPlain : (int)kFillScore;
+        const int groups = grid_for(c, kind) * (kBlock / 32) * (32 / cfg_L(c));
+        max_groups = std::max(max_groups, groups);
+    }
+    TRY(ws.colbest.ensure((size_t)max_groups * max_m * 4, "column maxima"));
+
+    // --- stage: order, packed reads
+    if (!plain) {
+        launch_plan_order(ws.key.as<uint16_t>(), n_jobs, dp->hist, dp->key_off, dp->cursor,
+                          ws.order.as<uint32_t>(), st);
+        launches += 2;
+    } else {
+        launch_iota(ws.order.as<uint32_t>(), n_jobs, st);
+        launches++;
+    }
+    launch_pack_reads(d_jobs, n_jobs, reinterpret_cast<const uint8_t*>(d_reads),
+                      ws.rpack.as<uint32_t>(), rw, &dp->st.bad_read, st);
+    launches++;
+    CU(cudaGetLastError());
+    const int t1 = tm.mark();
+
+    FillArgs base{};
+    base.ref = X.d_words;
+    base.ref_len = (int64_t)X.len;
+    base.jobs = d_jobs;
+    base.rpack = ws.rpack.as<uint32_t>();
+    base.rw = rw;
+    base.order = ws.order.as<uint32_t>();
+    base.sc = sc;
+    base.state = ws.state.as<JobState>();
+    base.colbest = ws.colbest.as<int32_t>();
+    base.cb_stride = max_m;
+    base.rect = ws.rect.as<Rect>();
+    base.wave = 0;
+    uint32_t* counters = ws.counters.as<uint32_t>();
+    auto next_counter = [&]() { return counters + (counter_next++ % 256); };
+
+    int tfill1 = -1, trect0 = -1, trect1 = -1, ttb1 = -1;
+    if (!plain) {
+        // --- score pass: one persistent launch per non-empty length bucket
+        for (int c = 0; c < kNumCfg; c++) {
+            if (!cfg_count[c]) continue;
+            FillLaunch fl{};
+            fl.args = base;
+            fl.args.pos_begin = cfg_begin[c];
+            fl.args.pos_count = cfg_count[c];
+            fl.args.item_counter = next_counter();
+            fl.kind = kFillScore;
+            fl.block = kBlock;
+            const uint32_t G = 32 / cfg_L(c);
+            const uint64_t warps_needed = (cfg_count[c] + G - 1) / G;
+            fl.grid = (int)std::min<uint64_t>(grid_for(c, kFillScore), (warps_needed + 3) / 4);
+            fl.stream = st;
+            launch_fill_cfg(c, fl);
+            stats.fill_launches++;
+            launches++;
+        }
+        CU(cudaGetLastError());
+        tfill1 = tm.mark();
+
+        if (want_cigar) {
+            // --- reduced traceback: rectangles, arena waves, direction pass, walk
+            launch_rect_plan(d_jobs, ws.order.as<uint32_t>(), n_jobs, ws.state.as<JobState>(), sc,
+                             min_score, 0, ws.rect.as<Rect>(), ws.sizes.as<uint64_t>(), st);
+            launch_scan_u64(ws.sizes.as<uint64_t>(), n_jobs, ws.offs.as<uint64_t>(),
+                            ws.bsum.as<uint64_t>(), &dp->totals[0], st);
+            launches += 4;
+            CU(cudaGetLastError());
+            CU(cudaMemcpyAsync(&hp->totals[0], &dp->totals[0], 8, cudaMemcpyDeviceToHost, st));
+            TRY(check_bad_read(dp, hp, st));
+            const uint64_t total_words = hp->totals[0];
+            // largest item: G jobs of the largest rectangle (bounded by the whole window)
+            uint64_t item_max = 0;
+            for (int c = 0; c < kNumCfg; c++)
+                if (cfg_count[c])
+                    item_max = std::max<uint64_t>(item_max, (uint64_t)(32 / cfg_L(c)) *
+                                                      dir_words(cfg_L(c), cfg_K(c), (int)max_m));
+            size_t free_b = 0, tot_b = 0;
+            CU(cudaMemGetInfo(&free_b, &tot_b));
+            const uint64_t avail = (uint64_t)((double)(free_b + ws.arena.cap) * 0.6) / 4;
+            uint64_t arena_words = total_words ? total_words : 1;
+            uint64_t wave_words = 0;   // 0: everything in one wave
+            if (arena_words > avail) {
+                arena_words = std::max<uint64_t>(avail, 2 * item_max);
+                wave_words = arena_words - item_max;
+            }
+            TRY(ws.arena.ensure(arena_words * 4, "direction arena"));
+            launch_rect_assign(ws.order.as<uint32_t>(), n_jobs, ws.offs.as<uint64_t>(), dp->cfg_begin,
+                               wave_words, ws.rect.as<Rect>(), &dp->st.max_wave, st);
+            launches++;
+            const uint32_t waves = wave_words ? (uint32_t)((total_words + wave_words - 1) / wave_words) : 1;
+            stats.waves = waves;
+            trect0 = tm.mark();
+            for (uint32_t wv = 0; wv < waves; wv++) {
+                for (int c = 0; c < kNumCfg; c++) {
+                    if (!cfg_count[c]) continue;
+                    FillLaunch fl{};
+                    fl.args = base;
+                    fl.args.pos_begin = cfg_begin[c];
+                    fl.args.pos_count = cfg_count[c];
+                    fl.args.item_counter = next_counter();
+                    fl.args.arena = ws.arena.as<uint32_t>();
+                    fl.args.wave = (int)wv;
+                    fl.kind = kFillRect;
+                    fl.block = kBlock;
+                    const uint32_t G = 32 / cfg_L(c);
+                    const uint64_t warps_needed = (cfg_count[c] + G - 1) / G;
+                    fl.grid = (int)std::min<uint64_t>(grid_for(c, kFillRect), (warps_needed + 3) / 4);
+                    fl.stream = st;
+                    launch_fill_cfg(c, fl);
+                    launches++;
+                }
+                if (wv == 0) trect1 = tm.mark();
+                launch_traceback(d_jobs, 0, n_jobs, ws.state.as<JobState>(), ws.rect.as<Rect>(),
+                                 ws.arena.as<uint32_t>(), (int)wv, mode, 0, -1, min_score,
+                                 ws.tmp_ops.as<uint32_t>(), tmp_stride, ws.tb.as<TbOut>(), st);
+                launches++;
+                CU(cudaGetLastError());
+            }
+            ttb1 = tm.mark();
+        } else {
+            TRY(check_bad_read(dp, hp, st));
+        }
+    } else {
+        // --- plain form: fixed-size batches in job order, one configuration for the
+        // longest read, whole-window direction bits, one fill + one traceback each
+        const int c = plain_cfg;
+        const int L = cfg_L(c), K = cfg_K(c);
+        const uint32_t G = 32 / L;
+        const uint64_t stride = dir_words(L, K, (int)max_m);
+        const uint32_t B = std::min(n_jobs, kPlainBatch);
+        TRY(ws.arena.ensure((size_t)B * stride * 4, "direction arena"));
+        for (uint32_t j0 = 0; j0 < n_jobs; j0 += B) {
+            const uint32_t nb = std::min(B, n_jobs - j0);
+            launch_plain_rect(d_jobs, j0, nb, stride, ws.rect.as<Rect>(), st);
+            FillLaunch fl{};
+            fl.args = base;
+            fl.args.pos_begin = j0;
+            fl.args.pos_count = nb;
+            fl.args.item_counter = next_counter();
+            fl.args.arena = ws.arena.as<uint32_t>();
+            fl.args.plain = 1;
+            fl.kind = kFillPlain;
+            fl.block = kBlock;
+            const uint64_t warps_needed = (nb + G - 1) / G;
+            fl.grid = (int)std::min<uint64_t>(grid_for(c, kFillPlain), (warps_needed + 3) / 4);
+            fl.stream = st;
+            launch_fill_cfg(c, fl);
+            stats.fill_launches++;
+            launches += 2;
+            if (want_cigar) {
+                launch_traceback(d_jobs, j0, nb, ws.state.as<JobState>(), ws.rect.as<Rect>(),
+                                 ws.arena.as<uint32_t>(), 0, mode, 1, c, min_score,
+                                 ws.tmp_ops.as<uint32_t>(), tmp_stride, ws.tb.as<TbOut>(), st);
+                launches++;
+            }
+            CU(cudaGetLastError());
+        }
+        tfill1 = tm.mark();
+        TRY(check_bad_read(dp, hp, st));
+    }
+
+    // --- results
+    const int tfin0 = tm.mark();
+    launch_cigar_count(d_jobs, n_jobs, ws.state.as<JobState>(), ws.tb.as<TbOut>(), mode,
+                       want_cigar ? 1 : 0, min_score, ws.count.as<uint32_t>(), st);
+    launch_scan_u32(ws.count.as<uint32_t>(), n_jobs, ws.coff.as<uint64_t>(), ws.bsum.as<uint64_t>(),
+                    &dp->totals[1], st);
+    launches += 4;
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(&hp->totals[1], &dp->totals[1], 8, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    const uint64_t ops_total = hp->totals[1];
+    if (cigar_used) *cigar_used = ops_total;
+    if (ops_total > cigar_cap)
+        return fail(SA_EOVERFLOW, "CIGAR buffer holds %llu ops, %llu needed",
+                    (unsigned long long)cigar_cap, (unsigned long long)ops_total);
+    if (ops_total > 0xffffffffull)
+        return fail(SA_EOVERFLOW, "more than 2^32 CIGAR ops in one call; split the batch");
+    uint32_t* dst = d_cigar;
+    if (grow_cigar) {
+        TRY(grow_cigar->ensure(ops_total * 4 + 4, "cigar"));
+        dst = grow_cigar->as<uint32_t>();
+    } else if (ops_total && !dst) {
+        return fail(SA_EOVERFLOW, "no CIGAR buffer, %llu ops needed", (unsigned long long)ops_total);
+    }
+    launch_finalize(d_jobs, n_jobs, ws.state.as<JobState>(), ws.tb.as<TbOut>(),
+                    ws.count.as<uint32_t>(), ws.coff.as<uint64_t>(), ws.tmp_ops.as<uint32_t>(),
+                    tmp_stride, mode, want_cigar ? 1 : 0, min_score, d_out, dst, st);
+    launches++;
+    CU(cudaGetLastError());
+    const int tfin1 = tm.mark();
+    CU(cudaStreamSynchronize(st));
+    stats.kernel_launches = launches;
+    if (P->profile) {
+        stats.ms_stage = tm.ms(t0, t1);
+        stats.ms_fill = tm.ms(t1, tfill1);
+        stats.ms_rect = tm.ms(trect0, trect1);
+        stats.ms_traceback = tm.ms(trect1, ttb1);
+        stats.ms_finalize = tm.ms(tfin0, tfin1);
+        stats.ms_total = tm.ms(t0, tfin1);
+    }
+    *X.last = stats;
+    return SA_OK;
+}
+
+// Host-buffer form on top of run_device: copy in, compute, copy out.
+int run_host(Ctx& X, const sa_params* P, const Score& sc, const sa_job* jobs, uint32_t n_jobs,
+             const char* reads, uint64_t reads_len, sa_result* out, uint32_t* cigar,
+             uint64_t cigar_cap, uint64_t* cigar_used, cudaStream_t st) {
+    Workspace& ws = *X.ws;
+    if (cigar_used) *cigar_used = 0;
+    if (n_jobs == 0) return SA_OK;
+    TRY(ws.jobs.ensure((size_t)n_jobs * sizeof(sa_job), "jobs"));
+    TRY(ws.reads.ensure(reads_len + 16, "reads"));
+    TRY(ws.out.ensure((size_t)n_jobs * sizeof(sa_result), "results"));
+    CU(cudaMemcpyAsync(ws.jobs.p, jobs, (size_t)n_jobs * sizeof(sa_job), cudaMemcpyHostToDevice, st));
+    if (reads_len) CU(cudaMemcpyAsync(ws.reads.p, reads, reads_len, cudaMemcpyHostToDevice, st));
+    uint64_t used = 0;
+    const int rc = run_device(X, P, sc, ws.jobs.as<sa_job>(), n_jobs, ws.reads.as<char>(), reads_len,
+                              ws.out.as<sa_result>(), nullptr, cigar_cap, &used, &ws.cigar, st);
+    if (cigar_used) *cigar_used = used;
+    if (rc != SA_OK) return rc;
+    if (used && !cigar) return fail(SA_EOVERFLOW, "cigar is NULL, %llu ops needed", (unsigned long long)used);
+    CU(cudaMemcpyAsync(out, ws.out.p, (size_t)n_jobs * sizeof(sa_result), cudaMemcpyDeviceToHost, st));
+    if (used) CU(cudaMemcpyAsync(cigar, ws.cigar.p, used * 4, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    return SA_OK;
+}
+
+cudaStream_t pick_stream(sa_reference* R, void* s) {
+    return s ? static_cast<cudaStream_t>(s) : R->own;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// serving
+
+namespace {
+
+struct Request {
+    uint64_t ticket = 0;
+    std::vector<sa_job> jobs;
+    std::vector<char> reads;
+    uint64_t est_bytes = 0;
+    int rc = SA_PENDING;
+    std::string err;
+    std::vector<sa_result> out;
+    std::vector<uint32_t> cigar;
+};
+
+}  // namespace
+
+struct sa_server {
+    sa_reference* ref = nullptr;
+    sa_params params{};
+    Score sc{};
+    uint64_t budget = 0;
+    uint64_t in_use = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::shared_ptr<Request>> queue;
+    std::map<uint64_t, std::shared_ptr<Request>> tickets;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    struct Slot {
+        Workspace ws;
+        sa_stats last{};
+        cudaStream_t stream = nullptr;
+        std::thread th;
+    };
+    std::vector<std::unique_ptr<Slot>> slots;
+};
+
+namespace {
+
+// Device memory one request needs while it runs (workspace buffers and the
+// direction arena, bounded by whole-window direction bits).
+uint64_t estimate_bytes(const sa_job* jobs, uint32_t n, uint64_t reads_len) {
+    uint64_t b = reads_len + (uint64_t)n * (sizeof(sa_job) + sizeof(sa_result) + 64 + 8 * 7);
+    uint32_t max_n = 1;
+    for (uint32_t k = 0; k < n; k++) {
+        const uint32_t rn = std::min(jobs[k].read_len, SA_MAX_READ), m = std::min(jobs[k].win_len, SA_MAX_WINDOW);
+        max_n = std::max(max_n, rn);
+        const int c = cfg_for_rows((int)std::max(rn, 1u));
+        b += 4 * dir_words(cfg_L(c), cfg_K(c), (int)m) + (uint64_t)4 * ((rn + 15) / 16);
+    }
+    b += (uint64_t)n * (2 * max_n + 3) * 4;
+    return b;
+}
+
+void slot_main(sa_server* S, sa_server::Slot* slot) {
+    cudaSetDevice(S->ref->device);
+    for (;;) {
+        std::shared_ptr<Request> rq;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            // FIFO admission: the head request starts when the memory budget allows
+            S->cv_work.wait(lk, [&] {
+                return S->stop || (!S->queue.empty() &&
+                                   S->in_use + S->queue.front()->est_bytes <= S->budget);
+            });
+            if (S->stop) return;
+            rq = S->queue.front();
+            S->queue.pop_front();
+            S->in_use += rq->est_bytes;
+        }
+        Ctx X{S->ref->d_words, S->ref->len, S->ref->num_sms, &slot->ws, &slot->last};
+        const uint32_t n = (uint32_t)rq->jobs.size();
+        rq->out.resize(n);
+        uint64_t used = 0;
+        // CIGAR capacity: 2n+3 ops per job bounds every job
+        uint64_t cap = 0;
+        for (const sa_job& j : rq->jobs) cap += 2ull * j.read_len + 3;
+        rq->cigar.resize(cap);
+        const int rc = run_host(X, &S->params, S->sc, rq->jobs.data(), n, rq->reads.data(),
+                                rq->reads.size(), rq->out.data(), rq->cigar.data(), cap, &used,
+                                slot->stream);
+        std::string msg = rc == SA_OK ? std::string() : std::string(g_err);
+        rq->cigar.resize(used);
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->in_use -= rq->est_bytes;
+            rq->err = msg;
+            rq->rc = rc;
+            rq->jobs.clear();
+            rq->jobs.shrink_to_fit();
+            rq->reads.clear();
+            rq->reads.shrink_to_fit();
+        }
+        S->cv_done.notify_all();
+        S->cv_work.notify_all();
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+
+extern "C" {
+
+const char* sa_last_error(void) { return g_err; }
+
+void sa_default_params(sa_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->sc.match = 1;
+    p->sc.mismatch = 2;
+    p->sc.gap_open = 2;
+    p->sc.gap_extend = 1;
+    p->mode = SA_LOCAL;
+    p->want_cigar = 1;
+    p->width = 0;
+    p->min_score = INT32_MIN;
+    p->form = SA_FORM_BATCHED;
+    p->profile = 0;
+}
+
+int sa_create_reference(const char* acgt, uint64_t len, int device, sa_reference** out) {
+    try {
+        g_err[0] = 0;
+        if (!out) return fail(SA_EINVAL, "out is NULL");
+        *out = nullptr;
+        if (!acgt) return fail(SA_EINVAL, "acgt is NULL");
+        if (len == 0) return fail(SA_EINVAL, "empty reference");
+        int ndev = 0;
+        CU(cudaGetDeviceCount(&ndev));
+        if (device < 0 || device >= ndev) return fail(SA_EINVAL, "device %d not present (%d devices)", device, ndev);
+        CU(cudaSetDevice(device));
+        std::unique_ptr<sa_reference> R(new (std::nothrow) sa_reference());
+        if (!R) return fail(SA_ENOMEM, "host allocation failed");
+        R->device = device;
+        R->len = len;
+        CU(cudaDeviceGetAttribute(&R->num_sms, cudaDevAttrMultiProcessorCount, device));
+        CU(cudaStreamCreateWithFlags(&R->own, cudaStreamNonBlocking));
+        const uint64_t words = (len + 15) / 16 + kRefFrontPad + kRefTailPad;
+        CU(cudaMalloc(&R->d_words, words * 4));
+        CU(cudaMemsetAsync(R->d_words, 0, words * 4, R->own));
+        const uint64_t chunk = 256ull << 20;  // multiple of 16
+        uint8_t* stage = nullptr;
+        unsigned long long* bad = nullptr;
+        int rc = SA_OK;
+        unsigned long long hbad = ~0ull;
+        if (cudaMalloc(&stage, std::min<uint64_t>(chunk, len)) != cudaSuccess ||
+            cudaMalloc(&bad, sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(SA_ENOMEM, "staging allocation failed");
+        }
+        if (rc == SA_OK) {
+            cudaMemsetAsync(bad, 0xff, sizeof(unsigned long long), R->own);
+            for (uint64_t off = 0; off < len && rc == SA_OK; off += chunk) {
+                const uint64_t sz = std::min(chunk, len - off);
+                if (cudaMemcpyAsync(stage, acgt + off, sz, cudaMemcpyHostToDevice, R->own) != cudaSuccess)
+                    rc = fail(SA_ECUDA, "reference upload failed");
+                launch_pack_ref(stage, sz, off, R->d_words + kRefFrontPad, bad, R->own);
+            }
+            cudaMemcpyAsync(&hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost, R->own);
+            const cudaError_t e = cudaStreamSynchronize(R->own);
+            if (rc == SA_OK && e != cudaSuccess) rc = fail(SA_ECUDA, "reference packing failed: %s", cudaGetErrorString(e));
+        }
+        if (stage) cudaFree(stage);
+        if (bad) cudaFree(bad);
+        if (rc == SA_OK && hbad != ~0ull) rc = fail(SA_EINVAL, "reference position %llu is not A, C, G or T", hbad);
+        if (rc != SA_OK) {
+            cudaFree(R->d_words);
+            cudaStreamDestroy(R->own);
+            return rc;
+        }
+        *out = R.release();
+        return SA_OK;
+    } catch (...) {
+        return fail(SA_ENOMEM, "unexpected host exception");
+    }
+}
+
+int sa_destroy_reference(sa_reference* R) {
+    if (!R) return fail(SA_EINVAL, "reference is NULL");
+    try {
+        cudaSetDevice(R->device);
+        {
+            std::lock_guard<std::mutex> lk(R->mu);
+            cudaStreamSynchronize(R->own);
+            R->ws.release();
+            cudaFree(R->d_words);
+            cudaStreamDestroy(R->own);
+        }
+        delete R;
+        return SA_OK;
+    } catch (...) {
+        return fail(SA_ECUDA, "unexpected host exception");
+    }
+}
+
+uint64_t sa_reference_length(const sa_reference* R) { return R ? R->len : 0; }
+
+int sa_last_stats(const sa_reference* R, sa_stats* out) {
+    if (!R || !out) return fail(SA_EINVAL, "NULL argument");
+    *out = R->last;
+    return SA_OK;
+}
+
+int sa_align_batch_dev(sa_reference* R, const sa_params* P, const sa_job* d_jobs, uint32_t n_jobs,
+                       const char* d_reads, uint64_t reads_len, sa_result* d_out, uint32_t* d_cigar,
+                       uint64_t cigar_cap, uint64_t* cigar_used, void* stream) {
+    try {
+        g_err[0] = 0;
+        if (!R) return fail(SA_EINVAL, "reference is NULL");
+        Score sc;
+        TRY(check_params(P, &sc));
+        if (n_jobs && (!d_jobs || !d_out)) return fail(SA_EINVAL, "NULL job or result buffer");
+        if (n_jobs && !d_reads) return fail(SA_EINVAL, "reads is NULL");
+        std::lock_guard<std::mutex> lk(R->mu);
+        CU(cudaSetDevice(R->device));
+        Ctx X = R->ctx();
+        return run_device(X, P, sc, d_jobs, n_jobs, d_reads, reads_len, d_out, d_cigar, cigar_cap,
+                          cigar_used, nullptr, pick_stream(R, stream));
+    } catch (...) {
+        return fail(SA_ENOMEM, "unexpected host exception");
+    }
+}
+
+int sa_align_batch(sa_reference* R, const sa_params* P, const sa_job* jobs, uint32_t n_jobs,
+                   const char* reads, uint64_t reads_len, sa_result* out, uint32_t* cigar,
+                   uint64_t cigar_cap, uint64_t* cigar_used, void* stream) {
+    try {
+        g_err[0] = 0;
+        if (!R) return fail(SA_EINVAL, "reference is NULL");
+        Score sc;
+        TRY(check_params(P, &sc));
+        if (n_jobs && (!jobs || !out)) return fail(SA_EINVAL, "NULL job or result buffer");
+        if (n_jobs && !reads) return fail(SA_EINVAL, "reads is NULL");
+        std::lock_guard<std::mutex> lk(R->mu);
+        CU(cudaSetDevice(R->device));
+        Ctx X = R->ctx();
+        return run_host(X, P, sc, jobs, n_jobs, reads, reads_len, out, cigar, cigar_cap, cigar_used,
+                        pick_stream(R, stream));
+    } catch (...) {
+        return fail(SA_ENOMEM, "unexpected host exception");
+    }
+}
+
+int sa_server_create(sa_reference* R, const sa_params* P, uint64_t hbm_budget, uint32_t max_inflight,
+                     sa_server** out) {
+    try {
+        g_err[0] = 0;
+        if (!R || !out) return fail(SA_EINVAL, "NULL argument");
+        *out = nullptr;
+        Score sc;
+        TRY(check_params(P, &sc));
+        CU(cudaSetDevice(R->device));
+        if (hbm_budget == 0) {
+            size_t fr = 0, tot = 0;
+            CU(cudaMemGetInfo(&fr, &tot));
+            hbm_budget = (uint64_t)(0.8 * (double)fr);
+        }
+        if (max_inflight == 0) max_inflight = 4;
+        if (max_inflight > 64) return fail(SA_EINVAL, "max_inflight must be <= 64");
+        std::unique_ptr<sa_server> S(new (std::nothrow) sa_server());
+        if (!S) return fail(SA_ENOMEM, "host allocation failed");
+        S->ref = R;
+        S->params = *P;
+        S->params.profile = 0;
+        S->sc = sc;
+        S->budget = hbm_budget;
+        for (uint32_t k = 0; k < max_inflight; k++) {
+            auto slot = std::make_unique<sa_server::Slot>();
+            CU(cudaStreamCreateWithFlags(&slot->stream, cudaStreamNonBlocking));
+            S->slots.push_back(std::move(slot));
+        }
+        for (auto& slot : S->slots) slot->th = std::thread(slot_main, S.get(), slot.get());
+        *out = S.release();
+        return SA_OK;
+    } catch (...) {
+        return fail(SA_ENOMEM, "unexpected host exception");
+    }
+}
+
+int sa_submit(sa_server* S, const sa_job* jobs, uint32_t n_jobs, const char* reads, uint64_t reads_len,
+              uint64_t* ticket) {
+    try {
+        g_err[0] = 0;
+        if (!S || !ticket) return fail(SA_EINVAL, "NULL argument");
+        if (n_jobs && (!jobs || !reads)) return fail(SA_EINVAL, "NULL jobs or reads");
+        auto rq = std::make_shared<Request>();
+        rq->jobs.assign(jobs, jobs + n_jobs);
+        rq->reads.assign(reads, reads + reads_len);
+        rq->est_bytes = estimate_bytes(jobs, n_jobs, reads_len);
+        if (rq->est_bytes > S->budget)
+            return fail(SA_EBUSY, "request needs about %llu bytes of device memory, the budget is %llu",
+                        (unsigned long long)rq->est_bytes, (unsigned long long)S->budget);
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            rq->ticket = S->next_ticket++;
+            S->tickets[rq->ticket] = rq;
+            S->queue.push_back(rq);
+            *ticket = rq->ticket;
+        }
+        S->cv_work.notify_all();
+        return SA_OK;
+    } catch (...) {
+        return fail(SA_ENOMEM, "unexpected host exception");
+    }
+}
+
+int sa_poll(sa_server* S, uint64_t ticket, int timeout_ms, sa_result* out, uint32_t* cigar,
+            uint64_t cigar_cap, uint64_t* cigar_used) {
+    try {
+        g_err[0] = 0;
+        if (!S) return fail(SA_EINVAL, "server is NULL");
+        std::unique_lock<std::mutex> lk(S->mu);
+        auto it = S->tickets.find(ticket);
+        if (it == S->tickets.end()) return fail(SA_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+        std::shared_ptr<Request> rq = it->second;
+        auto done = [&] { return rq->rc != SA_PENDING; };
+        if (!done()) {
+            if (timeout_ms == 0) return SA_PENDING;
+            if (timeout_ms < 0) {
+                S->cv_done.wait(lk, done);
+            } else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done)) {
+                return fail(SA_ETIMEOUT, "ticket %llu not finished after %d ms", (unsigned long long)ticket, timeout_ms);
+            }
+        }
+        if (rq->rc != SA_OK) {
+            const int rc = rq->rc;
+            snprintf(g_err, sizeof(g_err), "%s", rq->err.c_str());
+            S->tickets.erase(ticket);
+            return rc;
+        }
+        if (cigar_used) *cigar_used = rq->cigar.size();
+        if (rq->cigar.size() > cigar_cap || (!rq->cigar.empty() && !cigar))
+            return fail(SA_EOVERFLOW, "CIGAR buffer holds %llu ops, %zu needed",
+                        (unsigned long long)cigar_cap, rq->cigar.size());
+        if (!rq->out.empty()) {
+            if (!out) return fail(SA_EINVAL, "out is NULL");
+            std::memcpy(out, rq->out.data(), rq->out.size() * sizeof(sa_result));
+        }
+        if (!rq->cigar.empty()) std::memcpy(cigar, rq->cigar.data(), rq->cigar.size() * 4);
+        S->tickets.erase(ticket);
+        return SA_OK;
+    } catch (...) {
+        return fail(SA_ENOMEM, "unexpected host exception");
+    }
+}
+
+int sa_server_destroy(sa_server* S) {
+    if (!S) return fail(SA_EINVAL, "server is NULL");
+    try {
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->stop = true;
+            for (auto& rq : S->queue) {       // never started: fail them
+                rq->rc = SA_ECUDA;
+                rq->err = "server destroyed before the request ran";
+            }
+            S->queue.clear();
+        }
+        S->cv_work.notify_all();
+        S->cv_done.notify_all();
+        for (auto& slot : S->slots)
+            if (slot->th.joinable()) slot->th.join();
+        cudaSetDevice(S->ref->device);
+        for (auto& slot : S->slots) {
+            cudaStreamSynchronize(slot->stream);
+            slot->ws.release();
+            cudaStreamDestroy(slot->stream);
+        }
+        delete S;
+        return SA_OK;
+    } catch (...) {
+        return fail(SA_ECUDA, "unexpected host exception");
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,302 @@
+// Wavefront DP kernels (32-bit).
+//
+// Computes the recurrence of SOAP3-dp, Methods section 3 (the I/D/M tables,
+// here E/F/H) for one job per group of L lanes.  Lane g of the group owns the
+// K consecutive read rows g*K .. g*K+K-1 and keeps, for each of them, H(i-1,j)
+// + S_GO and F(i-1,j) in registers.  At wavefront step s lane g computes
+// column i = s - g + 1 (the window streams through the group, skewed by one
+// column per lane); the H and E values of the lane's bottom row and the
+// running column maximum move to the next lane with a shuffle.  No DP table
+// is kept in memory: the paper's improved form already keeps only two rows of
+// M and D, this form keeps none (the direction bits, when wanted, are the
+// only per-cell output).
+//
+// LOCAL pads the group's rows at the top (rows j <= 0 never match, so they
+// stay at H = 0 and feed row 1 exactly the border values H(i,0) = 0,
+// E(i,0) = -inf); GLOCAL pads at the bottom and reads row n by index.
+//
+// Three variants (template flags):
+//   BEST && !DIR  score pass: best cell, colbest(i), second best
+//   DIR && !BEST  direction pass over a sub-rectangle (reduced traceback)
+//   DIR && BEST   plain form: direction bits over the whole window + best
+#pragma once
+
+#include "sa_internal.cuh"
+
+namespace sa {
+
+__device__ __forceinline__ int32_t addmax(int32_t a, int32_t b, int32_t c) {
+    return __viaddmax_s32(a, b, c);   // max(a + b, c)
+}
+
+template <int L, int K>
+__device__ __forceinline__ uint32_t load_window16(const FillArgs& A, int64_t wstart, int b, int g) {
+    // 8 bases for columns of block b of lane g: positions wstart + 8b - g .. +7
+    int64_t p0 = wstart + 8 * (int64_t)b - g;
+    if (p0 > A.ref_len) p0 = A.ref_len;          // junk steps past the data: stay in the padding
+    const int64_t wi = p0 >> 4;                  // floor (p0 >= -32 > -16*kRefFrontPad)
+    const uint32_t sh = (uint32_t)(p0 & 15) * 2u;
+    const uint32_t* base = A.ref + kRefFrontPad;
+    const uint64_t v = ((uint64_t)__ldg(base + wi + 1) << 32) | (uint64_t)__ldg(base + wi);
+    return (uint32_t)(v >> sh) & 0xFFFFu;
+}
+
+template <int L, int K, int MODE, bool DIR, bool BEST>
+__global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
+    static_assert(32 % L == 0, "L must divide 32");
+    static_assert(K >= 1 && K <= 32, "K in 1..32");
+    constexpr int G = 32 / L;
+    constexpr bool LOCAL = (MODE == SA_LOCAL);
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int g = lane % L;
+    const int grp = lane / L;
+    const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    int32_t* cb = BEST ? A.colbest + (size_t)(gwarp * G + grp) * A.cb_stride : nullptr;
+    const Score S = A.sc;
+    const uint32_t count = A.count_ptr ? *A.count_ptr : A.pos_count;
+
+    for (;;) {
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(A.item_counter, 1u);
+        item = __shfl_sync(FULL, item, 0);
+        if (item * (uint32_t)G >= count) break;
+        const uint32_t p = item * G + grp;
+        const bool has = p < count;
+        const uint32_t job = has ? __ldg(A.order + A.pos_begin + p) : 0u;
+
+        // geometry of this group's task
+        int n = 0, rows = 0, w = 0;
+        int64_t wstart = 0;
+        uint64_t aoff = 0;
+        if (has) {
+            const sa_job J = A.jobs[job];
+            n = (int)J.read_len;
+            if (DIR) {
+                const Rect R = A.rect[job];
+                if (R.w > 0 && R.wave == A.wave) {
+                    rows = R.rows;
+                    w = R.w;
+                    wstart = (int64_t)J.ref_pos + R.i_lo - 1;
+                    aoff = R.off;
+                }
+            } else {
+                rows = n;
+                w = (int)J.win_len;
+                wstart = (int64_t)J.ref_pos;
+            }
+        }
+        const int nblk = w > 0 ? (w + L - 1 + 7) >> 3 : 0;
+        int nblk_warp = nblk;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) nblk_warp = max(nblk_warp, __shfl_xor_sync(FULL, nblk_warp, o));
+        if (nblk_warp == 0) continue;
+
+        const int pad = LOCAL ? (L * K - rows) : 0;
+        // match masks: bit r of mX is set when the lane's row r holds base X
+        uint32_t mA = 0, mC = 0, mG = 0, mT = 0;
+        {
+            const uint32_t* rp = A.rpack + (size_t)job * A.rw;
+#pragma unroll
+            for (int r = 0; r < K; r++) {
+                const int j = g * K + r + 1 - pad;
+                if (w > 0 && j >= 1 && j <= rows) {
+                    const uint32_t code = (__ldg(rp + ((j - 1) >> 4)) >> (2 * ((j - 1) & 15))) & 3u;
+                    const uint32_t bit = 1u << r;
+                    mA |= code == 0 ? bit : 0u;
+                    mC |= code == 1 ? bit : 0u;
+                    mG |= code == 2 ? bit : 0u;
+                    mT |= code == 3 ? bit : 0u;
+                }
+            }
+        }
+
+        // column-0 state: H(0,j) (+ S_GO), F(0,j) = -inf
+        int32_t HG[K], F[K];
+        auto h0 = [&](int j) -> int32_t {   // H(0, j)
+            return (!LOCAL && j >= 1) ? S.GO + (j - 1) * S.GE : 0;
+        };
+        auto reset_col0 = [&]() {
+#pragma unroll
+            for (int r = 0; r < K; r++) {
+                HG[r] = h0(g * K + r + 1 - pad) + S.GO;
+                F[r] = kNeg32;
+            }
+        };
+        reset_col0();
+        const int32_t hup0 = h0(g * K - pad) + S.GO;   // H(0, first row - 1) + S_GO
+        int32_t h_up_prev = hup0;
+        int32_t hg_bot = HG[K - 1], e_bot = kNeg32, cm_bot = 0;
+
+        // best tracking (LOCAL) and the row of H(., n) (GLOCAL)
+        int32_t bv = 0, bi = 0, br = 0;
+        const int gn = LOCAL ? 0 : (rows - 1) / K;
+        const int rn = LOCAL ? 0 : (rows - 1) % K;
+
+        uint32_t wb_next = load_window16<L, K>(A, wstart, 0, g);
+        for (int b = 0; b < nblk_warp; b++) {
+            const uint32_t wb = wb_next;
+            wb_next = load_window16<L, K>(A, wstart, b + 1, g);
+            uint32_t dw[K];
+            if (DIR) {
+#pragma unroll
+                for (int k = 0; k < K; k++) dw[k] = 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int s = 8 * b + u;
+                const int i = s - g + 1;
+                int32_t hg_up = __shfl_up_sync(FULL, hg_bot, 1, L);
+                int32_t e_up = __shfl_up_sync(FULL, e_bot, 1, L);
+                int32_t cm_up = 0;
+                if (BEST && LOCAL) cm_up = __shfl_up_sync(FULL, cm_bot, 1, L);
+                if (g == 0) { hg_up = S.GO; e_up = kNeg32; cm_up = 0; }
+                int32_t diag = h_up_prev;
+                h_up_prev = hg_up;
+                const uint32_t t = (wb >> (2 * u)) & 3u;
+                const uint32_t mk = t == 0 ? mA : (t == 1 ? mC : (t == 2 ? mG : mT));
+                int32_t e = e_up, hga = hg_up;
+                int32_t lm = 0;
+#pragma unroll
+                for (int r = 0; r < K; r++) {
+                    const int32_t d = ((mk >> r) & 1u) ? S.dm : S.dx;
+                    const int32_t gv = diag + d;          // H(i-1,j-1) + delta
+                    diag = HG[r];
+                    int32_t f, h;
+                    if (!DIR) {
+                        f = addmax(F[r], S.GE, HG[r]);    // max(F(i-1,j)+GE, H(i-1,j)+GO)
+                        e = addmax(e, S.GE, hga);         // max(E(i,j-1)+GE, H(i,j-1)+GO)
+                        h = LOCAL ? __vimax3_s32_relu(gv, e, f) : __vimax3_s32(gv, e, f);
+                    } else {
+                        const int32_t fe = F[r] + S.GE;
+                        const bool fopen = HG[r] >= fe;
+                        f = fopen ? HG[r] : fe;
+                        const int32_t ee = e + S.GE;
+                        const bool eopen = hga >= ee;
+                        e = eopen ? hga : ee;
+                        const bool pF = f >= e;
+                        const int32_t ef = pF ? f : e;
+                        const bool pG = gv >= ef;
+                        h = pG ? gv : ef;
+                        uint32_t src = pG ? 1u : (pF ? 2u : 3u);
+                        if (LOCAL && h <= 0) { h = 0; src = 0u; }
+                        const uint32_t nib = src | (eopen ? 0u : 4u) | (fopen ? 0u : 8u);
+                        const int q = u * K + r;          // compile-time after unrolling
+                        dw[q >> 3] |= nib << (4 * (q & 7));
+                    }
+                    F[r] = f;
+                    HG[r] = h + S.GO;
+                    hga = HG[r];
+                    if (BEST && LOCAL) lm = max(lm, h);
+                }
+                hg_bot = HG[K - 1];
+                e_bot = e;
+                if (s < g) {                              // before this lane's first column
+                    reset_col0();
+                    h_up_prev = hup0;
+                }
+                const bool active = (i >= 1) && (i <= w);
+                if (BEST) {
+                    if (LOCAL) {
+                        const int32_t cm = max(cm_up, lm);
+                        cm_bot = cm;
+                        if (active) {
+                            if (g == L - 1) cb[i - 1] = cm;
+                            if (lm > bv) {
+                                bv = lm;
+                                bi = i;
+                                int rr = K - 1;
+#pragma unroll
+                                for (int r = K - 1; r >= 0; r--)
+                                    if (HG[r] - S.GO == lm) rr = r;
+                                br = rr;
+                            }
+                        }
+                    } else if (active && g == gn) {
+                        int32_t hv = HG[0];
+#pragma unroll
+                        for (int r = 1; r < K; r++)
+                            if (r == rn) hv = HG[r];
+                        cb[i - 1] = hv - S.GO;
+                    }
+                }
+                if (DIR && b < nblk) {
+                    // words whose last nibble was produced in this step are complete
+#pragma unroll
+                    for (int k = 0; k < K; k++) {
+                        if ((8 * k + 7) / K == u)
+                            A.arena[aoff + ((uint64_t)b * K + k) * L + g] = dw[k];
+                    }
+                }
+            }
+        }
+
+        if (BEST) {
+            __syncwarp();
+            int32_t best;
+            int istar, jstar;
+            bool empty = false;
+            if (LOCAL) {
+                int bj = g * K + br + 1 - pad;
+#pragma unroll
+                for (int o = 1; o < L; o <<= 1) {
+                    const int32_t ov = __shfl_xor_sync(FULL, bv, o, L);
+                    const int oi = __shfl_xor_sync(FULL, bi, o, L);
+                    const int oj = __shfl_xor_sync(FULL, bj, o, L);
+                    if (ov > bv || (ov == bv && (oi < bi || (oi == bi && oj < bj)))) {
+                        bv = ov; bi = oi; bj = oj;
+                    }
+                }
+                best = bv;
+                istar = bi;
+                jstar = bj;
+                empty = bv <= 0;
+            } else {
+                int32_t v = kNeg32;
+                int vi = 0;
+                for (int ii = g + 1; ii <= w; ii += L) {
+                    const int32_t x = cb[ii - 1];
+                    if (vi == 0 || x > v) { v = x; vi = ii; }
+                }
+#pragma unroll
+                for (int o = 1; o < L; o <<= 1) {
+                    const int32_t ov = __shfl_xor_sync(FULL, v, o, L);
+                    const int oi = __shfl_xor_sync(FULL, vi, o, L);
+                    if (oi != 0 && (vi == 0 || ov > v || (ov == v && oi < vi))) { v = ov; vi = oi; }
+                }
+                best = v;
+                istar = vi;
+                jstar = rows;
+            }
+            int32_t sv = SA_NO_SCORE;
+            int si = 0;
+            if (!empty) {
+                for (int ii = g + 1; ii <= w; ii += L) {
+                    const int dd = ii > istar ? ii - istar : istar - ii;
+                    if (dd < n) continue;
+                    const int32_t x = cb[ii - 1];
+                    if (si == 0 || x > sv) { sv = x; si = ii; }
+                }
+#pragma unroll
+                for (int o = 1; o < L; o <<= 1) {
+                    const int32_t ov = __shfl_xor_sync(FULL, sv, o, L);
+                    const int oi = __shfl_xor_sync(FULL, si, o, L);
+                    if (oi != 0 && (si == 0 || ov > sv || (ov == sv && oi < si))) { sv = ov; si = oi; }
+                }
+            }
+            if (g == 0 && has) {
+                JobState st;
+                st.best = empty ? 0 : best;
+                st.i_star = empty ? 0 : istar;
+                st.j_star = empty ? 0 : jstar;
+                st.second = empty ? SA_NO_SCORE : sv;
+                st.second_i = empty ? 0 : si;
+                st.flags = empty ? kStEmpty : 0u;
+                A.state[job] = st;
+            }
+            __syncwarp();
+        }
+    }
+}
+
+}  // namespace sa

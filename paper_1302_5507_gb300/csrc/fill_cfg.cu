@@ -1,0 +1,61 @@
+// One configuration's wavefront kernels (compiled once per configuration with
+// -DSA_CFG=<index>, so the translation units build in parallel).
+#include "fill.cuh"
+#include "kernels.h"
+
+#ifndef SA_CFG
+#error "compile with -DSA_CFG=<configuration index>"
+#endif
+
+namespace sa {
+
+namespace {
+constexpr int kL = kCfgs[SA_CFG].L;
+constexpr int kK = kCfgs[SA_CFG].K;
+
+template <int MODE, bool DIR, bool BEST>
+void launch_one(const FillLaunch& fl) {
+    k_fill32<kL, kK, MODE, DIR, BEST><<<fl.grid, fl.block, 0, fl.stream>>>(fl.args);
+}
+
+template <int MODE, bool DIR, bool BEST>
+int blocks_per_sm() {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fill32<kL, kK, MODE, DIR, BEST>, 128, 0);
+    return nb;
+}
+}  // namespace
+
+template <>
+void launch_fill<SA_CFG>(const FillLaunch& fl) {
+    const bool local = fl.args.sc.mode == SA_LOCAL;
+    switch (fl.kind) {
+    case kFillScore:
+        local ? launch_one<SA_LOCAL, false, true>(fl) : launch_one<SA_GLOCAL, false, true>(fl);
+        break;
+    case kFillRect:
+        local ? launch_one<SA_LOCAL, true, false>(fl) : launch_one<SA_GLOCAL, true, false>(fl);
+        break;
+    case kFillPlain:
+        local ? launch_one<SA_LOCAL, true, true>(fl) : launch_one<SA_GLOCAL, true, true>(fl);
+        break;
+    default:
+        break;
+    }
+}
+
+template <>
+int fill_blocks_per_sm<SA_CFG>(int kind, int mode) {
+    const bool local = mode == SA_LOCAL;
+    switch (kind) {
+    case kFillScore:
+        return local ? blocks_per_sm<SA_LOCAL, false, true>() : blocks_per_sm<SA_GLOCAL, false, true>();
+    case kFillRect:
+        return local ? blocks_per_sm<SA_LOCAL, true, false>() : blocks_per_sm<SA_GLOCAL, true, false>();
+    case kFillPlain:
+        return local ? blocks_per_sm<SA_LOCAL, true, true>() : blocks_per_sm<SA_GLOCAL, true, true>();
+    }
+    return 0;
+}
+
+}  // namespace sa

@@ -1,0 +1,64 @@
+// Host-side launch wrappers of the libsa kernels (stage.cu, fill_cfg*.cu).
+#pragma once
+
+#include "sa_internal.cuh"
+
+namespace sa {
+
+struct PlanStats {                 // filled by the plan kernel (device)
+    uint32_t max_n, max_m;
+    unsigned long long cells;
+    uint32_t bad_job;              // first invalid job (UINT32_MAX: none)
+    uint32_t bad_read;             // first job with a non-ACGT base (UINT32_MAX: none)
+    uint32_t max_wave;             // last direction-arena wave with work
+    uint32_t _pad;
+    unsigned long long bad_ref_pos;
+};
+
+struct TbOut {                     // traceback result of one job
+    int32_t n_rev;                 // ops written (reverse order) to the temporary slot
+    int32_t read_begin;            // 0-based
+    int32_t ref_begin_rel;         // 0-based, relative to the job's window start
+};
+
+void launch_pack_ref(const uint8_t* ascii, uint64_t len, uint64_t base_off, uint32_t* words,
+                     unsigned long long* bad_pos, cudaStream_t st);
+void launch_plan(const sa_job* jobs, uint32_t n_jobs, uint64_t reads_len, int64_t ref_len,
+                 uint16_t* key, uint32_t* hist, PlanStats* stats, cudaStream_t st);
+void launch_plan_order(const uint16_t* key, uint32_t n_jobs, const uint32_t* hist,
+                       uint32_t* key_off, uint32_t* cursor, uint32_t* order, cudaStream_t st);
+void launch_pack_reads(const sa_job* jobs, uint32_t n_jobs, const uint8_t* reads, uint32_t* rpack,
+                       uint32_t rw, unsigned* bad_job, cudaStream_t st);
+void launch_rect_plan(const sa_job* jobs, const uint32_t* order, uint32_t n_pos,
+                      const JobState* state, const Score& sc, int32_t min_score, int plain,
+                      Rect* rect, uint64_t* sizes, cudaStream_t st);
+void launch_rect_assign(const uint32_t* order, uint32_t n_pos, const uint64_t* offs,
+                        const uint32_t* cfg_begin, uint64_t wave_words, Rect* rect,
+                        uint32_t* max_wave, cudaStream_t st);
+void launch_plain_rect(const sa_job* jobs, uint32_t j0, uint32_t nb, uint64_t stride, Rect* rect,
+                       cudaStream_t st);
+void launch_scan_u64(const uint64_t* in, uint64_t n, uint64_t* out, uint64_t* bsum, uint64_t* total,
+                     cudaStream_t st);
+void launch_scan_u32(const uint32_t* in, uint64_t n, uint64_t* out, uint64_t* bsum, uint64_t* total,
+                     cudaStream_t st);
+void launch_traceback(const sa_job* jobs, uint32_t job_begin, uint32_t n_jobs, const JobState* state,
+                      const Rect* rect, const uint32_t* arena, int wave, int mode, int plain,
+                      int cfg_force, int32_t min_score, uint32_t* tmp_ops, uint32_t tmp_stride,
+                      TbOut* tb, cudaStream_t st);
+void launch_iota(uint32_t* p, uint32_t n, cudaStream_t st);
+void launch_cigar_count(const sa_job* jobs, uint32_t n_jobs, const JobState* state, const TbOut* tb,
+                        int mode, int want_cigar, int32_t min_score, uint32_t* count,
+                        cudaStream_t st);
+void launch_finalize(const sa_job* jobs, uint32_t n_jobs, const JobState* state, const TbOut* tb,
+                     const uint32_t* count, const uint64_t* coff, const uint32_t* tmp_ops,
+                     uint32_t tmp_stride, int mode, int want_cigar, int32_t min_score,
+                     sa_result* out, uint32_t* cigar, cudaStream_t st);
+
+// the wavefront kernels, dispatched by configuration index
+void launch_fill_cfg(int cfg, const FillLaunch& fl);
+int fill_max_blocks_per_sm(int cfg, int kind, int mode);
+
+// scan scratch: number of uint64 block sums needed for n elements
+inline uint64_t scan_bsum_len(uint64_t n) { return (n + 1023) / 1024 + 1; }
+
+}  // namespace sa

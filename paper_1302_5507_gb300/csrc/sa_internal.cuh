@@ -1,0 +1,143 @@
+// Internal definitions shared by the CUDA translation units of libsa.
+//
+// Notation follows SOAP3-dp, Methods section 3: T = window (length m, column
+// index i), R = read (length n, row index j).  H = M (best), E = I (read base
+// against a space, runs along j), F = D (window base against a space, runs
+// along i).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "sa.h"
+
+namespace sa {
+
+// "minus infinity" of the 32-bit kernels: far below any reachable score
+// (|score| < 2^28 by the interface limits) and safe to add one gap penalty to.
+constexpr int32_t kNeg32 = -(1 << 29);
+// "minus infinity" of the 16-bit packed kernels; host checks keep every
+// reachable 16-bit value above it (see width selection in api.cu).
+constexpr int32_t kNeg16 = -16384;
+
+// Reference: 2-bit codes A=0 C=1 G=2 T=3, 16 bases per uint32 (base p in bits
+// 2*(p&15) of word p>>4).  The device copy has kRefFrontPad words before base
+// 0 and kRefTailPad after the last word, so the wavefront can load whole words
+// around the window edges without bounds checks.
+constexpr int kRefFrontPad = 4;
+constexpr int kRefTailPad = 8;
+
+// Lane-group configurations of the wavefront kernels: a group of L lanes
+// (L divides 32) works on one job (two jobs in the packed 16-bit kernel); each
+// lane owns K consecutive read rows, so a group covers L*K >= n rows.
+struct Cfg { int L, K; };
+constexpr int kNumCfg = 14;
+constexpr Cfg kCfgs[kNumCfg] = {
+    {8, 4}, {8, 7}, {8, 10}, {8, 13}, {8, 16}, {8, 19}, {8, 22}, {8, 25}, {8, 28}, {8, 32},
+    {32, 10}, {32, 16}, {32, 24}, {32, 32}};
+
+// run-time lookups (device code cannot index the host constexpr table)
+__host__ __device__ inline int cfg_L(int c) { return c < 10 ? 8 : 32; }
+__host__ __device__ inline int cfg_K(int c) {
+    switch (c) {
+    case 0: return 4;   case 1: return 7;   case 2: return 10;  case 3: return 13;
+    case 4: return 16;  case 5: return 19;  case 6: return 22;  case 7: return 25;
+    case 8: return 28;  case 9: return 32;  case 10: return 10; case 11: return 16;
+    case 12: return 24; default: return 32;
+    }
+}
+
+__host__ __device__ inline int cfg_for_rows(int n) {
+    for (int c = 0; c < kNumCfg; c++)
+        if (cfg_L(c) * cfg_K(c) >= n) return c;
+    return -1;
+}
+
+// Size classes order jobs inside one configuration (largest windows first).
+constexpr int kNumSizeCls = 40;
+__host__ __device__ inline int size_class(uint32_t m) {
+    int lg = 0;
+    for (uint32_t v = m; v > 1u; v >>= 1) lg++;
+    int half = (lg > 0) ? (int)((m >> (lg - 1)) & 1u) : 0;
+    int c = 2 * lg + half;
+    return c < kNumSizeCls ? c : kNumSizeCls - 1;
+}
+constexpr int kNumKeys = kNumCfg * kNumSizeCls;
+
+// Signed scoring in the paper's form plus the constants the kernels use.
+struct Score {
+    int32_t a, b, GO, GE;     // S_MA, S_MI, S_GO, S_GE
+    int32_t dm, dx;           // a - GO, b - GO (diagonal term in the H+GO representation)
+    int32_t mode;             // SA_LOCAL / SA_GLOCAL
+};
+
+// Per-job result of the score pass.
+struct JobState {
+    int32_t best;       // best score
+    int32_t i_star;     // 1-based window column of the best cell (0: none)
+    int32_t j_star;     // 1-based read row of the best cell
+    int32_t second;     // second best (SA_NO_SCORE if none)
+    int32_t second_i;   // 1-based column of the second best (0: none)
+    uint32_t flags;     // kStEmpty, kStOverflow
+};
+constexpr uint32_t kStEmpty = 1u;      // LOCAL: no positive cell
+constexpr uint32_t kStOverflow = 2u;   // 16-bit pass may have overflowed: recompute in 32-bit
+
+// Sub-problem of the direction-bit pass: rows 1..rows of the read against the
+// window columns i_lo..i_lo+w-1 (1-based); w == 0 means "no traceback".
+struct Rect {
+    uint64_t off;       // first word of its direction bits in the arena (within its wave)
+    int32_t i_lo;
+    int32_t w;
+    int32_t rows;
+    int32_t start_i;    // traceback start cell in rect coordinates
+    int32_t start_j;
+    int32_t wave;
+};
+
+// Arguments of the wavefront kernels.
+struct FillArgs {
+    const uint32_t* ref;          // padded packed reference (base 0 at ref + kRefFrontPad words)
+    int64_t ref_len;              // bases
+    const sa_job* jobs;
+    const uint32_t* rpack;        // packed reads, rw words per job
+    uint32_t rw;
+    const uint32_t* order;        // job ids in processing order
+    uint32_t pos_begin;           // first position of this launch in `order`
+    uint32_t pos_count;           // positions in this launch (if count_ptr == nullptr)
+    const uint32_t* count_ptr;    // device count (overflow rerun lists)
+    uint32_t* item_counter;       // persistent work counter (zeroed before launch)
+    Score sc;
+    JobState* state;              // per job id
+    int32_t* colbest;             // per group scratch, cb_stride words each
+    uint32_t cb_stride;
+    const Rect* rect;             // direction pass: per job id
+    uint32_t* arena;              // direction bits
+    int32_t wave;                 // direction pass: only jobs of this wave
+    int32_t plain;                // direction pass over whole windows (plain form)
+};
+
+struct FillLaunch {
+    FillArgs args;
+    int kind;                     // kFillScore / kFillRect / kFillPlain / kFillScore16
+    int grid, block;
+    cudaStream_t stream;
+};
+enum { kFillScore = 0, kFillRect = 1, kFillPlain = 2, kFillScore16 = 3 };
+
+// per-configuration launchers (one translation unit per configuration)
+template <int C> void launch_fill(const FillLaunch& fl);
+template <int C> int fill_blocks_per_sm(int kind, int mode);   // resident 128-thread blocks per SM
+
+// direction-bit layout shared by the wavefront kernels and the traceback:
+// a job's bits are blocks of 8 wavefront steps; in a block, lane g of the
+// group stores K words, word w of lane g at ((block*K + w) * L + g); nibble q =
+// step_in_block*K + r of lane g lives in word q/8, bits 4*(q%8).
+// A nibble: bits 0-1 source of H (0 stop, 1 diagonal, 2 F/deletion,
+// 3 E/insertion), bit 2 E extends, bit 3 F extends.
+__host__ __device__ inline uint64_t dir_words(int L, int K, int w) {
+    uint64_t blocks = (uint64_t)(w + L - 1 + 7) / 8;
+    return blocks * (uint64_t)K * (uint64_t)L;
+}
+
+}  // namespace sa

@@ -1,0 +1,577 @@
+// Staging, planning, traceback and result kernels of libsa.
+//
+//  pack_ref       ASCII reference -> 2-bit words (validation included)
+//  plan           per job: validation, length bucket + size class, statistics
+//  plan_scan      bucket histogram -> offsets (one block)
+//  plan_scatter   job ids into bucket order
+//  pack_reads     ASCII reads -> 2-bit words, reverse complement for SA_RC jobs
+//  rect_plan      per job: the sub-rectangle that holds every optimal path
+//  scan_u64       exclusive prefix sums (3-phase)
+//  traceback      walk the direction bits from the best cell (one thread per job)
+//  finalize       sa_result + compacted CIGAR in job order
+#include <cstdio>
+
+#include "kernels.h"
+
+namespace sa {
+
+__device__ __forceinline__ int base_code(uint8_t c) {
+    switch (c) {
+    case 'A': case 'a': return 0;
+    case 'C': case 'c': return 1;
+    case 'G': case 'g': return 2;
+    case 'T': case 't': return 3;
+    }
+    return -1;
+}
+
+// ---------------------------------------------------------------------------
+// reference packing: one thread per output word (16 bases)
+
+__global__ void k_pack_ref(const uint8_t* __restrict__ ascii, uint64_t len, uint64_t base_off,
+                           uint32_t* __restrict__ words, unsigned long long* bad_pos) {
+    const uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t p0 = w * 16;
+    if (p0 >= len) return;
+    uint32_t v = 0;
+    for (int k = 0; k < 16; k++) {
+        const uint64_t p = p0 + k;
+        if (p >= len) break;
+        const int c = base_code(ascii[p]);
+        if (c < 0) { atomicMin(bad_pos, (unsigned long long)(base_off + p)); continue; }
+        v |= (uint32_t)c << (2 * k);
+    }
+    words[(base_off / 16) + w] = v;
+}
+
+void launch_pack_ref(const uint8_t* ascii, uint64_t len, uint64_t base_off, uint32_t* words,
+                     unsigned long long* bad_pos, cudaStream_t st) {
+    const uint64_t nw = (len + 15) / 16;
+    if (!nw) return;
+    k_pack_ref<<<(unsigned)((nw + 255) / 256), 256, 0, st>>>(ascii, len, base_off, words, bad_pos);
+}
+
+// ---------------------------------------------------------------------------
+// planning
+
+__global__ void k_plan(const sa_job* __restrict__ jobs, uint32_t n_jobs, uint64_t reads_len,
+                       int64_t ref_len, uint16_t* __restrict__ key, uint32_t* __restrict__ hist,
+                       PlanStats* stats) {
+    __shared__ uint32_t sh[kNumKeys];
+    for (int k = threadIdx.x; k < kNumKeys; k += blockDim.x) sh[k] = 0;
+    __syncthreads();
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t maxn = 0, maxm = 0;
+    unsigned long long cells = 0;
+    if (j < n_jobs) {
+        const sa_job J = jobs[j];
+        const uint32_t n = J.read_len, m = J.win_len;
+        bool ok = n >= 1 && n <= SA_MAX_READ && m >= 1 && m <= SA_MAX_WINDOW &&
+                  J.ref_pos <= (uint64_t)ref_len && (uint64_t)m <= (uint64_t)ref_len - J.ref_pos &&
+                  J.read_off <= reads_len && (uint64_t)n <= reads_len - J.read_off &&
+                  (J.flags & ~SA_RC) == 0u;
+        if (!ok) {
+            atomicMin(&stats->bad_job, j);
+            key[j] = 0;
+        } else {
+            const int c = cfg_for_rows((int)n);
+            const int k = c * kNumSizeCls + (kNumSizeCls - 1 - size_class(m));
+            key[j] = (uint16_t)k;
+            atomicAdd(&sh[k], 1u);
+            maxn = n;
+            maxm = m;
+            cells = (unsigned long long)n * m;
+        }
+    }
+    // warp-aggregate the statistics
+    for (int o = 16; o >= 1; o >>= 1) {
+        maxn = max(maxn, __shfl_xor_sync(0xffffffffu, maxn, o));
+        maxm = max(maxm, __shfl_xor_sync(0xffffffffu, maxm, o));
+        cells += __shfl_xor_sync(0xffffffffu, cells, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&stats->max_n, maxn);
+        atomicMax(&stats->max_m, maxm);
+        atomicAdd(&stats->cells, cells);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < kNumKeys; k += blockDim.x)
+        if (sh[k]) atomicAdd(&hist[k], sh[k]);
+}
+
+__global__ void k_plan_scan(const uint32_t* __restrict__ hist, uint32_t* __restrict__ key_off,
+                            uint32_t* __restrict__ cursor) {
+    // one block: exclusive scan of kNumKeys counts (serial per warp is plenty here)
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int k = 0; k < kNumKeys; k++) {
+            key_off[k] = acc;
+            acc += hist[k];
+        }
+        key_off[kNumKeys] = acc;
+    }
+    for (int k = threadIdx.x; k < kNumKeys; k += blockDim.x) cursor[k] = 0;
+}
+
+__global__ void k_plan_scatter(const uint16_t* __restrict__ key, uint32_t n_jobs,
+                               const uint32_t* __restrict__ key_off, uint32_t* __restrict__ cursor,
+                               uint32_t* __restrict__ order) {
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_jobs) return;
+    const int k = key[j];
+    order[key_off[k] + atomicAdd(&cursor[k], 1u)] = j;
+}
+
+void launch_plan(const sa_job* jobs, uint32_t n_jobs, uint64_t reads_len, int64_t ref_len,
+                 uint16_t* key, uint32_t* hist, PlanStats* stats, cudaStream_t st) {
+    if (!n_jobs) return;
+    k_plan<<<(n_jobs + 255) / 256, 256, 0, st>>>(jobs, n_jobs, reads_len, ref_len, key, hist, stats);
+}
+
+void launch_plan_order(const uint16_t* key, uint32_t n_jobs, const uint32_t* hist,
+                       uint32_t* key_off, uint32_t* cursor, uint32_t* order, cudaStream_t st) {
+    k_plan_scan<<<1, 256, 0, st>>>(hist, key_off, cursor);
+    if (n_jobs)
+        k_plan_scatter<<<(n_jobs + 255) / 256, 256, 0, st>>>(key, n_jobs, key_off, cursor, order);
+}
+
+// ---------------------------------------------------------------------------
+// read packing: one warp per job, one lane per output word
+
+__global__ void k_pack_reads(const sa_job* __restrict__ jobs, uint32_t n_jobs,
+                             const uint8_t* __restrict__ reads, uint32_t* __restrict__ rpack,
+                             uint32_t rw, unsigned* bad_job) {
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n_jobs) return;
+    const sa_job J = jobs[warp];
+    const uint32_t n = J.read_len;
+    const bool rc = (J.flags & SA_RC) != 0u;
+    const uint8_t* r = reads + J.read_off;
+    uint32_t* out = rpack + (size_t)warp * rw;
+    bool bad = false;
+    for (uint32_t wi = lane; wi * 16 < n; wi += 32) {
+        uint32_t v = 0;
+        for (int k = 0; k < 16; k++) {
+            const uint32_t p = wi * 16 + k;
+            if (p >= n) break;
+            int c = base_code(rc ? r[n - 1 - p] : r[p]);
+            if (c < 0) { bad = true; c = 0; }
+            if (rc) c = 3 - c;   // complement: A<->T, C<->G
+            v |= (uint32_t)c << (2 * k);
+        }
+        out[wi] = v;
+    }
+    if (bad) atomicMin(bad_job, warp);
+}
+
+void launch_pack_reads(const sa_job* jobs, uint32_t n_jobs, const uint8_t* reads, uint32_t* rpack,
+                       uint32_t rw, unsigned* bad_job, cudaStream_t st) {
+    if (!n_jobs) return;
+    const uint64_t threads = (uint64_t)n_jobs * 32;
+    k_pack_reads<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(jobs, n_jobs, reads, rpack, rw,
+                                                                      bad_job);
+}
+
+// ---------------------------------------------------------------------------
+// reduced traceback rectangle.
+//
+// Every alignment path that ends at the best cell (i*, j*) with the best score
+// uses at most j* read bases (#M + #I <= j*) and, because each deleted window
+// base costs at least e, at most (a*j* - best)/e deletions (#D).  Its first
+// cell is therefore at column >= i* - j* - (a*j* - best)/e.  The DP restricted
+// to columns [i_lo, i*] and rows [1, j*] (with the border of a fresh DP on its
+// left) reproduces every value on such a path and every comparison the
+// traceback makes, so the walk from its corner gives the same CIGAR.
+// With e = 0 the bound does not exist and the whole window is used.
+
+__global__ void k_rect_plan(const sa_job* __restrict__ jobs, const uint32_t* __restrict__ order,
+                            uint32_t n_pos, const JobState* __restrict__ state, Score sc,
+                            int32_t min_score, int plain, Rect* __restrict__ rect,
+                            uint64_t* __restrict__ sizes) {
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_pos) return;
+    const uint32_t job = order[p];
+    const sa_job J = jobs[job];
+    const JobState st = state[job];
+    Rect R;
+    R.off = 0;
+    R.wave = 0;
+    R.i_lo = 1;
+    R.w = 0;
+    R.rows = 0;
+    R.start_i = 0;
+    R.start_j = 0;
+    const int c = cfg_for_rows((int)J.read_len);
+    const bool tb = !(st.flags & kStEmpty) && st.best >= min_score;
+    if (plain) {
+        // direction bits over the whole window for every job (the best cell is
+        // only known after the fill, so the start cell is set by the traceback)
+        R.i_lo = 1;
+        R.w = (int)J.win_len;
+        R.rows = (int)J.read_len;
+    } else if (tb) {
+        const int istar = st.i_star, jstar = st.j_star;
+        int64_t span = istar;
+        const int32_t e = -sc.GE;
+        if (e > 0) {
+            const int64_t slack = (int64_t)sc.a * jstar - st.best;
+            span = (int64_t)jstar + (slack > 0 ? slack / e : 0);
+        }
+        int64_t ilo = (int64_t)istar - span + 1;
+        if (ilo < 1) ilo = 1;
+        R.i_lo = (int)ilo;
+        R.w = istar - (int)ilo + 1;
+        R.rows = jstar;
+        R.start_i = R.w;
+        R.start_j = jstar;
+    }
+    rect[job] = R;
+    sizes[p] = R.w > 0 ? dir_words(cfg_L(c), cfg_K(c), R.w) : 0;
+}
+
+void launch_rect_plan(const sa_job* jobs, const uint32_t* order, uint32_t n_pos,
+                      const JobState* state, const Score& sc, int32_t min_score, int plain,
+                      Rect* rect, uint64_t* sizes, cudaStream_t st) {
+    if (!n_pos) return;
+    k_rect_plan<<<(n_pos + 255) / 256, 256, 0, st>>>(jobs, order, n_pos, state, sc, min_score, plain,
+                                                      rect, sizes);
+}
+
+// wave assignment: an item (the G jobs a warp takes at once) belongs to the wave
+// of its first job, so every item fits the arena slack (cap - item_max).
+__global__ void k_rect_assign(const uint32_t* __restrict__ order, uint32_t n_pos,
+                              const uint64_t* __restrict__ offs, const uint32_t* __restrict__ cfg_begin,
+                              uint64_t wave_words, Rect* __restrict__ rect, uint32_t* max_wave) {
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_pos) return;
+    const uint32_t job = order[p];
+    // configuration of this position and the first position of its item
+    int c = 0;
+    while (c + 1 < kNumCfg && cfg_begin[c + 1] <= p) c++;
+    const uint32_t G = 32 / cfg_L(c);
+    const uint32_t first = cfg_begin[c] + ((p - cfg_begin[c]) / G) * G;
+    const uint64_t wv = wave_words ? offs[first] / wave_words : 0;
+    Rect R = rect[job];
+    R.wave = (int)wv;
+    R.off = offs[p] - wv * wave_words;
+    rect[job] = R;
+    if (R.w > 0) atomicMax(max_wave, (uint32_t)wv);
+}
+
+void launch_rect_assign(const uint32_t* order, uint32_t n_pos, const uint64_t* offs,
+                        const uint32_t* cfg_begin, uint64_t wave_words, Rect* rect,
+                        uint32_t* max_wave, cudaStream_t st) {
+    if (!n_pos) return;
+    k_rect_assign<<<(n_pos + 255) / 256, 256, 0, st>>>(order, n_pos, offs, cfg_begin, wave_words,
+                                                        rect, max_wave);
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan of uint64 (or uint32 widened) values: block sums, scan of the
+// block sums in one block, then per-block scan with the carried offset
+
+constexpr int kScanBlock = 1024;
+
+template <typename T>
+__device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t* total) {
+    __shared__ uint64_t warp_sums[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        uint64_t s = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    const uint64_t before = wid ? warp_sums[wid - 1] : 0;
+    *total = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+template <typename T>
+__global__ void k_scan_reduce(const T* __restrict__ in, uint64_t n, uint64_t* __restrict__ bsum) {
+    const uint64_t i = blockIdx.x * (uint64_t)kScanBlock + threadIdx.x;
+    uint64_t v = i < n ? (uint64_t)in[i] : 0;
+    uint64_t tot;
+    block_excl_scan<T>(v, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_blocksums(uint64_t* __restrict__ bsum, uint32_t nb, uint64_t* total_out) {
+    __shared__ uint64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (uint32_t base = 0; base < nb; base += kScanBlock) {
+        const uint32_t i = base + threadIdx.x;
+        const uint64_t v = i < nb ? bsum[i] : 0;
+        uint64_t tot;
+        const uint64_t ex = block_excl_scan<uint64_t>(v, &tot);
+        if (i < nb) bsum[i] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total_out = carry;
+}
+
+template <typename T>
+__global__ void k_scan_apply(const T* __restrict__ in, uint64_t n, const uint64_t* __restrict__ bsum,
+                             uint64_t* __restrict__ out) {
+    const uint64_t i = blockIdx.x * (uint64_t)kScanBlock + threadIdx.x;
+    uint64_t v = i < n ? (uint64_t)in[i] : 0;
+    uint64_t tot;
+    const uint64_t ex = block_excl_scan<T>(v, &tot);
+    if (i < n) out[i] = bsum[blockIdx.x] + ex;
+}
+
+template <typename T>
+static void scan_impl(const T* in, uint64_t n, uint64_t* out, uint64_t* bsum, uint64_t* total,
+                      cudaStream_t st) {
+    if (!n) {
+        cudaMemsetAsync(total, 0, sizeof(uint64_t), st);
+        return;
+    }
+    const uint32_t nb = (uint32_t)((n + kScanBlock - 1) / kScanBlock);
+    k_scan_reduce<T><<<nb, kScanBlock, 0, st>>>(in, n, bsum);
+    k_scan_blocksums<<<1, kScanBlock, 0, st>>>(bsum, nb, total);
+    k_scan_apply<T><<<nb, kScanBlock, 0, st>>>(in, n, bsum, out);
+}
+
+void launch_scan_u64(const uint64_t* in, uint64_t n, uint64_t* out, uint64_t* bsum, uint64_t* total,
+                     cudaStream_t st) {
+    scan_impl<uint64_t>(in, n, out, bsum, total, st);
+}
+void launch_scan_u32(const uint32_t* in, uint64_t n, uint64_t* out, uint64_t* bsum, uint64_t* total,
+                     cudaStream_t st) {
+    scan_impl<uint32_t>(in, n, out, bsum, total, st);
+}
+
+// ---------------------------------------------------------------------------
+// traceback: one thread per job, walking the direction nibbles of its rectangle
+// (the same priority as the definition: stop > diagonal > D > I, gaps opened on
+// ties, which the nibbles encode cell by cell).  Ops are written in reverse
+// order, run-length merged, into the job's temporary slot.
+
+__device__ __forceinline__ uint32_t nibble_at(const uint32_t* __restrict__ arena, uint64_t off,
+                                              int L, int K, int pad, int i, int j) {
+    const int idx = j - 1 + pad;
+    const int g = idx / K, r = idx - g * K;
+    const int s = i - 1 + g;
+    const int b = s >> 3, u = s & 7;
+    const int q = u * K + r;
+    const uint32_t word = arena[off + ((uint64_t)b * K + (q >> 3)) * L + g];
+    return (word >> (4 * (q & 7))) & 15u;
+}
+
+__global__ void k_traceback(const sa_job* __restrict__ jobs, uint32_t job_begin, uint32_t n_jobs,
+                            const JobState* __restrict__ state, const Rect* __restrict__ rect,
+                            const uint32_t* __restrict__ arena, int wave, int mode, int plain,
+                            int cfg_force, int32_t min_score, uint32_t* __restrict__ tmp_ops,
+                            uint32_t tmp_stride, TbOut* __restrict__ tb) {
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= n_jobs) return;
+    const uint32_t job = job_begin + tid;
+    const Rect R = rect[job];
+    if (R.w <= 0 || R.wave != wave) return;
+    const sa_job J = jobs[job];
+    const JobState st = state[job];
+    TbOut out;
+    out.n_rev = 0;
+    out.read_begin = -1;
+    out.ref_begin_rel = -1;
+    int si = R.start_i, sj = R.start_j;
+    if (plain) {
+        // whole-window direction bits: start at the best cell found by the same fill
+        if ((st.flags & kStEmpty) || st.best < min_score) { tb[job] = out; return; }
+        si = st.i_star;
+        sj = st.j_star;
+    }
+    const int c = cfg_force >= 0 ? cfg_force : cfg_for_rows((int)J.read_len);
+    const int L = cfg_L(c), K = cfg_K(c);
+    const int pad = (mode == SA_LOCAL) ? L * K - R.rows : 0;
+    uint32_t* ops = tmp_ops + (uint64_t)job * tmp_stride;
+    int nrev = 0;
+    uint32_t cur_op = 15u, cur_len = 0;
+    auto emit = [&](uint32_t op, uint32_t len) {
+        if (op == cur_op) { cur_len += len; return; }
+        if (cur_len) ops[nrev++] = (cur_len << 4) | cur_op;
+        cur_op = op;
+        cur_len = len;
+    };
+    int i = si, j = sj;
+    int state_ = 0;   // 0 H, 1 E (insertion), 2 F (deletion)
+    const uint64_t off = R.off;
+    for (;;) {
+        if (state_ == 0) {
+            if (i == 0 || j == 0) break;
+            const uint32_t nib = nibble_at(arena, off, L, K, pad, i, j);
+            const uint32_t src = nib & 3u;
+            if (src == 0u) break;
+            if (src == 1u) { emit(0u, 1u); i--; j--; }
+            else if (src == 2u) state_ = 2;
+            else state_ = 1;
+        } else if (state_ == 2) {
+            const uint32_t nib = nibble_at(arena, off, L, K, pad, i, j);
+            emit(2u, 1u);
+            i--;
+            state_ = (nib & 8u) ? 2 : 0;
+        } else {
+            const uint32_t nib = nibble_at(arena, off, L, K, pad, i, j);
+            emit(1u, 1u);
+            j--;
+            state_ = (nib & 4u) ? 1 : 0;
+        }
+    }
+    if (mode == SA_GLOCAL && j > 0) { emit(1u, (uint32_t)j); j = 0; }
+    if (cur_len) ops[nrev++] = (cur_len << 4) | cur_op;
+    out.n_rev = nrev;
+    out.read_begin = j;
+    out.ref_begin_rel = (R.i_lo - 1) + i;
+    tb[job] = out;
+}
+
+void launch_traceback(const sa_job* jobs, uint32_t job_begin, uint32_t n_jobs, const JobState* state,
+                      const Rect* rect, const uint32_t* arena, int wave, int mode, int plain,
+                      int cfg_force, int32_t min_score, uint32_t* tmp_ops, uint32_t tmp_stride,
+                      TbOut* tb, cudaStream_t st) {
+    if (!n_jobs) return;
+    k_traceback<<<(n_jobs + 127) / 128, 128, 0, st>>>(jobs, job_begin, n_jobs, state, rect, arena,
+                                                       wave, mode, plain, cfg_force, min_score,
+                                                       tmp_ops, tmp_stride, tb);
+}
+
+__global__ void k_iota(uint32_t* __restrict__ p, uint32_t n) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) p[k] = k;
+}
+
+void launch_iota(uint32_t* p, uint32_t n, cudaStream_t st) {
+    if (!n) return;
+    k_iota<<<(n + 255) / 256, 256, 0, st>>>(p, n);
+}
+
+// plain form: the whole window of every job of a batch, fixed stride per job
+__global__ void k_plain_rect(const sa_job* __restrict__ jobs, uint32_t j0, uint32_t nb,
+                             uint64_t stride, Rect* __restrict__ rect) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nb) return;
+    const sa_job J = jobs[j0 + k];
+    Rect R;
+    R.off = (uint64_t)k * stride;
+    R.i_lo = 1;
+    R.w = (int)J.win_len;
+    R.rows = (int)J.read_len;
+    R.start_i = 0;
+    R.start_j = 0;
+    R.wave = 0;
+    rect[j0 + k] = R;
+}
+
+void launch_plain_rect(const sa_job* jobs, uint32_t j0, uint32_t nb, uint64_t stride, Rect* rect,
+                       cudaStream_t st) {
+    if (!nb) return;
+    k_plain_rect<<<(nb + 255) / 256, 256, 0, st>>>(jobs, j0, nb, stride, rect);
+}
+
+// number of CIGAR ops of each job (soft clips included)
+__global__ void k_cigar_count(const sa_job* __restrict__ jobs, uint32_t n_jobs,
+                              const JobState* __restrict__ state, const TbOut* __restrict__ tb,
+                              int mode, int want_cigar, int32_t min_score,
+                              uint32_t* __restrict__ count) {
+    const uint32_t job = blockIdx.x * blockDim.x + threadIdx.x;
+    if (job >= n_jobs) return;
+    const JobState st = state[job];
+    uint32_t c = 0;
+    const bool tb_done = want_cigar && !(st.flags & kStEmpty) && st.best >= min_score;
+    if (tb_done) {
+        const TbOut t = tb[job];
+        c = (uint32_t)t.n_rev;
+        if (mode == SA_LOCAL) {
+            c += t.read_begin > 0 ? 1u : 0u;
+            c += (int)jobs[job].read_len > st.j_star ? 1u : 0u;
+        }
+    }
+    count[job] = c;
+}
+
+void launch_cigar_count(const sa_job* jobs, uint32_t n_jobs, const JobState* state, const TbOut* tb,
+                        int mode, int want_cigar, int32_t min_score, uint32_t* count,
+                        cudaStream_t st) {
+    if (!n_jobs) return;
+    k_cigar_count<<<(n_jobs + 255) / 256, 256, 0, st>>>(jobs, n_jobs, state, tb, mode, want_cigar,
+                                                         min_score, count);
+}
+
+__global__ void k_finalize(const sa_job* __restrict__ jobs, uint32_t n_jobs,
+                           const JobState* __restrict__ state, const TbOut* __restrict__ tb,
+                           const uint32_t* __restrict__ count, const uint64_t* __restrict__ coff,
+                           const uint32_t* __restrict__ tmp_ops, uint32_t tmp_stride, int mode,
+                           int want_cigar, int32_t min_score, sa_result* __restrict__ out,
+                           uint32_t* __restrict__ cigar) {
+    const uint32_t job = blockIdx.x * blockDim.x + threadIdx.x;
+    if (job >= n_jobs) return;
+    const sa_job J = jobs[job];
+    const JobState st = state[job];
+    sa_result r;
+    r.score = st.best;
+    r.second = SA_NO_SCORE;
+    r.read_begin = -1;
+    r.read_end = -1;
+    r.ref_begin = -1;
+    r.ref_end = -1;
+    r.second_ref_end = -1;
+    r.cigar_off = (uint32_t)coff[job];
+    r.cigar_len = count[job];
+    r.flags = 0;
+    r._pad = 0;
+    if (st.best < min_score) r.flags |= SA_RES_BELOW_MIN;
+    if (st.flags & kStEmpty) {
+        r.flags |= SA_RES_EMPTY;
+        r.score = 0;
+    } else {
+        r.second = st.second;
+        r.second_ref_end = st.second_i ? (int64_t)J.ref_pos + st.second_i : -1;
+        r.read_end = st.j_star;
+        r.ref_end = (int64_t)J.ref_pos + st.i_star;
+        const bool tb_done = want_cigar && st.best >= min_score;
+        if (tb_done) {
+            const TbOut t = tb[job];
+            r.read_begin = t.read_begin;
+            r.ref_begin = (int64_t)J.ref_pos + t.ref_begin_rel;
+            uint32_t* o = cigar + coff[job];
+            int k = 0;
+            if (mode == SA_LOCAL && t.read_begin > 0) o[k++] = ((uint32_t)t.read_begin << 4) | 4u;
+            const uint32_t* src = tmp_ops + (uint64_t)job * tmp_stride;
+            for (int q = t.n_rev - 1; q >= 0; q--) o[k++] = src[q];
+            if (mode == SA_LOCAL && (int)J.read_len > st.j_star)
+                o[k++] = ((uint32_t)(J.read_len - st.j_star) << 4) | 4u;
+        }
+    }
+    out[job] = r;
+}
+
+void launch_finalize(const sa_job* jobs, uint32_t n_jobs, const JobState* state, const TbOut* tb,
+                     const uint32_t* count, const uint64_t* coff, const uint32_t* tmp_ops,
+                     uint32_t tmp_stride, int mode, int want_cigar, int32_t min_score,
+                     sa_result* out, uint32_t* cigar, cudaStream_t st) {
+    if (!n_jobs) return;
+    k_finalize<<<(n_jobs + 255) / 256, 256, 0, st>>>(jobs, n_jobs, state, tb, count, coff, tmp_ops,
+                                                      tmp_stride, mode, want_cigar, min_score, out,
+                                                      cigar);
+}
+
+}  // namespace sa

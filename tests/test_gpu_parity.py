@@ -1,0 +1,210 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle,
+field by field and bit-exact (score, ends, begins, second best and its end,
+flags, CIGAR), on seeded synthetic inputs."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from oracle.compare import compare
+
+pytestmark = pytest.mark.gpu
+
+SCHEMES = [(1, 2, 2, 1), (1, 4, 6, 1), (2, 3, 5, 2), (1, 3, 1, 0), (3, 1, 0, 1), (1, 10, 0, 1)]
+
+
+@pytest.fixture(scope="module")
+def sa():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1302_5507_gb300 as sa
+    return sa
+
+
+def run_pair(sa, ref, wl, *, scoring=(1, 2, 2, 1), mode=0, form=0, width=0, want_cigar=True,
+             min_score=oracle.NO_SCORE):
+    jobs = sa.jobs_array(wl.read_off, wl.read_len, wl.flags, wl.ref_pos, wl.win_len)
+    p = sa.make_params(scoring=scoring, mode=mode, form=form, width=width, want_cigar=want_cigar,
+                       min_score=min_score)
+    res, cig = ref.align(jobs, wl.reads, p)
+    ores, oops = oracle.align(wl, scoring=scoring, mode=mode, want_cigar=want_cigar,
+                              min_score=min_score)
+    return res, cig, ores, oops
+
+
+def assert_parity(sa, ref, wl, **kw):
+    res, cig, ores, oops = run_pair(sa, ref, wl, **kw)
+    bad = compare(res, cig, ores, oops if kw.get("want_cigar", True) else None)
+    assert not bad, f"{wl.name} {kw}: " + "\n".join(bad)
+    return res, ores
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("scoring", SCHEMES)
+def test_small_random(sa, mode, form, scoring):
+    for seed, alpha in ((1, 4), (2, 2)):
+        wl = workloads.small(seed * 100 + sum(scoring), 1500, n_range=(1, 70), m_range=(1, 160),
+                             alphabet=alpha)
+        with sa.Reference(wl.ref) as ref:
+            assert_parity(sa, ref, wl, scoring=scoring, mode=mode, form=form)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_long_reads_wide_groups(sa, mode):
+    """Reads of 257..1024 bases use the 32-lane configurations."""
+    wl = workloads.small(5, 60, n_range=(200, 1024), m_range=(1, 2500))
+    with sa.Reference(wl.ref) as ref:
+        assert_parity(sa, ref, wl, mode=mode)
+        assert_parity(sa, ref, wl, mode=mode, form=1)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_plain_workload_full(sa, mode):
+    """10,000 jobs of 100 bp reads in 400 bp windows (every job)."""
+    wl = workloads.plain(seed=1)
+    with sa.Reference(wl.ref) as ref:
+        assert_parity(sa, ref, wl, mode=mode)
+        assert_parity(sa, ref, wl, mode=mode, form=1)
+
+
+def test_mate_rescue_subset(sa):
+    wl = workloads.mate_rescue(seed=1, n_pairs=20_000)
+    with sa.Reference(wl.ref) as ref:
+        res, ores = assert_parity(sa, ref, wl)
+        assert_parity(sa, ref, wl, mode=1)
+    # mates come from the window: most align (almost) end to end
+    assert np.median(res["score"]) >= 140
+
+
+def test_uneven_subset(sa):
+    wl = workloads.uneven(seed=1, n_jobs=20_000)
+    with sa.Reference(wl.ref) as ref:
+        assert_parity(sa, ref, wl)
+        assert_parity(sa, ref, wl, form=1)
+
+
+def test_low_similarity_subset(sa):
+    wl = workloads.lowsim(seed=1, n_jobs=3_000)
+    with sa.Reference(wl.ref) as ref:
+        assert_parity(sa, ref, wl)
+        assert_parity(sa, ref, wl, want_cigar=False)
+        assert_parity(sa, ref, wl, mode=1)
+
+
+def _wl_from_pairs(pairs, flags=None):
+    ref = "".join(w for w, _ in pairs)
+    reads = "".join(r for _, r in pairs)
+    n = np.array([len(r) for _, r in pairs], np.uint32)
+    m = np.array([len(w) for w, _ in pairs], np.uint32)
+    off = np.concatenate([[0], np.cumsum(n[:-1])]).astype(np.uint64)
+    pos = np.concatenate([[0], np.cumsum(m[:-1])]).astype(np.uint64)
+    fl = np.zeros(len(pairs), np.uint32) if flags is None else np.asarray(flags, np.uint32)
+    return workloads.Workload("edge", np.frombuffer(ref.encode(), np.uint8).copy(),
+                              np.frombuffer(reads.encode(), np.uint8).copy(), off, n, fl, pos, m,
+                              pos.copy())
+
+
+def test_edge_cases(sa):
+    pairs = [("A", "A"), ("C", "A"), ("ACGT", "ACGTACGT"), ("AAAAAAAAAA", "AAA"), ("CCCCCCCC", "AAAA"),
+             ("ACGTTTACGT", "ACGTACGT"), ("AC", "AAC"), ("ACGT", "AGT"), ("T" * 300, "T" * 256),
+             ("ACGT" * 50, "TGCA" * 10), ("G", "GGGGGGGGGGGGGGGGGGGGGGGGGGGGGGGGGG")]
+    wl = _wl_from_pairs(pairs, flags=[0, 1] * 5 + [0])
+    with sa.Reference(wl.ref) as ref:
+        for mode in (0, 1):
+            for form in (0, 1):
+                for scoring in SCHEMES:
+                    assert_parity(sa, ref, wl, mode=mode, form=form, scoring=scoring)
+
+
+def test_min_score_and_score_only(sa):
+    wl = workloads.small(9, 800, n_range=(5, 60), m_range=(5, 120))
+    with sa.Reference(wl.ref) as ref:
+        for mode in (0, 1):
+            assert_parity(sa, ref, wl, mode=mode, min_score=20)
+            assert_parity(sa, ref, wl, mode=mode, want_cigar=False)
+
+
+def test_invalid_inputs(sa):
+    wl = workloads.small(3, 10, n_range=(5, 20), m_range=(30, 60))
+    jobs = sa.jobs_array(wl.read_off, wl.read_len, wl.flags, wl.ref_pos, wl.win_len)
+    with sa.Reference(wl.ref) as ref:
+        bad_reads = wl.reads.copy()
+        bad_reads[3] = ord("N")
+        with pytest.raises(sa.SAError) as e:
+            ref.align(jobs, bad_reads)
+        assert e.value.code == sa.SA_EINVAL
+        past = jobs.copy()
+        past["ref_pos"][2] = len(wl.ref) - 5
+        with pytest.raises(sa.SAError) as e:
+            ref.align(past, wl.reads)
+        assert e.value.code == sa.SA_EINVAL
+        zero = jobs.copy()
+        zero["read_len"][0] = 0
+        with pytest.raises(sa.SAError):
+            ref.align(zero, wl.reads)
+        long_ = jobs.copy()
+        long_["read_len"][0] = sa.SA_MAX_READ + 1
+        with pytest.raises(sa.SAError):
+            ref.align(long_, wl.reads)
+        # an empty batch is fine
+        out, cig = ref.align(jobs[:0], wl.reads)
+        assert len(out) == 0 and len(cig) == 0
+        # a too-small CIGAR buffer reports the size it needs
+        with pytest.raises(sa.SAError) as e:
+            ref.align(jobs, wl.reads, cigar=np.zeros(1, np.uint32))
+        assert e.value.code == sa.SA_EOVERFLOW
+        # and the reference itself is validated
+        with pytest.raises(sa.SAError):
+            sa.Reference(b"ACGTNACGT")
+        # after the errors the same reference still computes correctly
+        assert_parity(sa, ref, wl)
+
+
+def test_device_buffers_match_host_buffers(sa):
+    import torch
+    wl = workloads.mate_rescue(seed=2, n_pairs=5_000)
+    jobs = sa.jobs_array(wl.read_off, wl.read_len, wl.flags, wl.ref_pos, wl.win_len)
+    with sa.Reference(wl.ref) as ref:
+        h_res, h_cig = ref.align(jobs, wl.reads)
+        dev = torch.device("cuda:0")
+        d_jobs = torch.from_numpy(jobs.view(np.uint8)).to(dev)
+        d_reads = torch.from_numpy(wl.reads).to(dev)
+        d_out = torch.zeros(len(jobs) * 56, dtype=torch.uint8, device=dev)
+        cap = sa.cigar_max_ops(wl.read_len)
+        d_cig = torch.zeros(cap, dtype=torch.int32, device=dev)
+        stream = torch.cuda.Stream()
+        used = ref.align_dev(d_jobs, d_reads, d_out, d_cig, stream=stream)
+        torch.cuda.synchronize()
+        res = d_out.cpu().numpy().view(sa.RESULT_DTYPE)
+        cig = d_cig[:used].cpu().numpy().view(np.uint32)
+        assert (res == h_res).all()
+        assert np.array_equal(cig, h_cig)
+
+
+def test_full_size_mate_rescue_sampled(sa):
+    """The benchmark's workload (1M mate-rescue jobs) in one call; a seeded sample
+    of jobs is recomputed by the oracle one by one."""
+    wl = workloads.mate_rescue(seed=1)
+    jobs = sa.jobs_array(wl.read_off, wl.read_len, wl.flags, wl.ref_pos, wl.win_len)
+    with sa.Reference(wl.ref) as ref:
+        res, cig = ref.align(jobs, wl.reads)
+    rng = np.random.default_rng(123)
+    idx = np.sort(rng.choice(wl.n_jobs, 3000, replace=False))
+    sub = wl.subset(idx)
+    ores, oops = oracle.align(sub)
+    sres = res[idx].copy()
+    # re-base the CIGAR offsets of the sample onto a compacted copy
+    parts, off = [], 0
+    for k, j in enumerate(idx):
+        L = int(res["cigar_len"][j])
+        parts.append(cig[int(res["cigar_off"][j]):int(res["cigar_off"][j]) + L])
+        sres["cigar_off"][k] = off
+        off += L
+    scig = np.concatenate(parts) if parts else np.zeros(0, np.uint32)
+    bad = compare(sres, scig, ores, oops)
+    assert not bad, "\n".join(bad)
+    # the CIGAR buffer is compact and in job order
+    assert (np.diff(res["cigar_off"].astype(np.int64)) == res["cigar_len"][:-1]).all()
