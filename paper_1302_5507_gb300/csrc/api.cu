@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstddef>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -188,6 +189,23 @@ struct Timer {
 };
 
 constexpr uint32_t kPlainBatch = 65536;     // jobs per launch of the plain form
+
+// SA_TRACE=1 in the environment: synchronise after each phase and log it to
+// stderr with its host time (debugging aid; off by default).
+struct Trace {
+    bool on;
+    cudaStream_t st;
+    std::chrono::steady_clock::time_point t0;
+    explicit Trace(cudaStream_t s) : on(getenv("SA_TRACE") != nullptr), st(s),
+                                     t0(std::chrono::steady_clock::now()) {}
+    void operator()(const char* what) {
+        if (!on) return;
+        const cudaError_t e = cudaStreamSynchronize(st);
+        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        fprintf(stderr, "[sa] %9.3f ms  %s  (%s)\n", ms, what, cudaGetErrorString(e));
+        fflush(stderr);
+    }
+};
 constexpr int kBlock = 128;
 
 int check_bad_read(PlanBlock* dp, PlanBlock* hp, cudaStream_t st) {
@@ -217,6 +235,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
     const int32_t min_score = P->min_score;
     if (P->profile) TRY(ensure_events(ws));
     Timer tm(ws, st, P->profile != 0);
+    Trace trace(st);
     const int t0 = tm.mark();
     uint32_t launches = 0;
 
@@ -227,6 +246,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
     PlanBlock* hp = ws.h_plan;
     CU(cudaMemsetAsync(dp, 0, sizeof(PlanBlock), st));
     CU(cudaMemsetAsync(&dp->st.bad_job, 0xff, sizeof(uint32_t) * 2, st));
+    CU(cudaMemsetAsync(&dp->st.bad_walk, 0xff, sizeof(uint32_t), st));
     TRY(ws.key.ensure((size_t)n_jobs * sizeof(uint16_t), "keys"));
     TRY(ws.counters.ensure(256 * sizeof(uint32_t), "counters"));
     CU(cudaMemsetAsync(ws.counters.p, 0, 256 * sizeof(uint32_t), st));
@@ -234,6 +254,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
     launch_plan(d_jobs, n_jobs, reads_len, (int64_t)X.len, ws.key.as<uint16_t>(), dp->hist, &dp->st, st);
     launches++;
     CU(cudaGetLastError());
+    trace("plan");
     CU(cudaMemcpyAsync(hp, dp, offsetof(PlanBlock, key_off), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
     if (hp->st.bad_job != 0xffffffffu)
@@ -299,6 +320,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
                       ws.rpack.as<uint32_t>(), rw, &dp->st.bad_read, st);
     launches++;
     CU(cudaGetLastError());
+    trace("order + pack reads");
     const int t1 = tm.mark();
 
     FillArgs base{};
@@ -336,6 +358,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             launch_fill_cfg(c, fl);
             stats.fill_launches++;
             launches++;
+            if (trace.on) { char b[64]; snprintf(b, sizeof b, "score pass cfg %d (%u jobs)", c, cfg_count[c]); trace(b); }
         }
         CU(cudaGetLastError());
         tfill1 = tm.mark();
@@ -348,6 +371,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
                             ws.bsum.as<uint64_t>(), &dp->totals[0], st);
             launches += 4;
             CU(cudaGetLastError());
+            trace("rect plan + scan");
             CU(cudaMemcpyAsync(&hp->totals[0], &dp->totals[0], 8, cudaMemcpyDeviceToHost, st));
             TRY(check_bad_read(dp, hp, st));
             const uint64_t total_words = hp->totals[0];
@@ -391,13 +415,15 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
                     fl.stream = st;
                     launch_fill_cfg(c, fl);
                     launches++;
+                    if (trace.on) { char b[64]; snprintf(b, sizeof b, "rect pass cfg %d wave %u", c, wv); trace(b); }
                 }
                 if (wv == 0) trect1 = tm.mark();
                 launch_traceback(d_jobs, 0, n_jobs, ws.state.as<JobState>(), ws.rect.as<Rect>(),
                                  ws.arena.as<uint32_t>(), (int)wv, mode, 0, -1, min_score,
-                                 ws.tmp_ops.as<uint32_t>(), tmp_stride, ws.tb.as<TbOut>(), st);
+                                 ws.tmp_ops.as<uint32_t>(), tmp_stride, ws.tb.as<TbOut>(), &dp->st.bad_walk, st);
                 launches++;
                 CU(cudaGetLastError());
+                trace("traceback");
             }
             ttb1 = tm.mark();
         } else {
@@ -433,7 +459,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             if (want_cigar) {
                 launch_traceback(d_jobs, j0, nb, ws.state.as<JobState>(), ws.rect.as<Rect>(),
                                  ws.arena.as<uint32_t>(), 0, mode, 1, c, min_score,
-                                 ws.tmp_ops.as<uint32_t>(), tmp_stride, ws.tb.as<TbOut>(), st);
+                                 ws.tmp_ops.as<uint32_t>(), tmp_stride, ws.tb.as<TbOut>(), &dp->st.bad_walk, st);
                 launches++;
             }
             CU(cudaGetLastError());
@@ -450,8 +476,13 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
                     &dp->totals[1], st);
     launches += 4;
     CU(cudaGetLastError());
+    trace("cigar count + scan");
     CU(cudaMemcpyAsync(&hp->totals[1], &dp->totals[1], 8, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(&hp->st.bad_walk, &dp->st.bad_walk, 4, cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
+    if (hp->st.bad_walk != 0xffffffffu)
+        return fail(SA_ECUDA, "internal error: the traceback of job %u left its direction-bit rectangle",
+                    hp->st.bad_walk);
     const uint64_t ops_total = hp->totals[1];
     if (cigar_used) *cigar_used = ops_total;
     if (ops_total > cigar_cap)
@@ -471,6 +502,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
                     tmp_stride, mode, want_cigar ? 1 : 0, min_score, d_out, dst, st);
     launches++;
     CU(cudaGetLastError());
+    trace("finalize");
     const int tfin1 = tm.mark();
     CU(cudaStreamSynchronize(st));
     stats.kernel_launches = launches;

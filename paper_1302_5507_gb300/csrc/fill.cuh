@@ -268,21 +268,22 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
                 istar = vi;
                 jstar = rows;
             }
+            // second best; the shuffles stay outside any per-group branch (every
+            // lane of the warp must reach them)
             int32_t sv = SA_NO_SCORE;
             int si = 0;
-            if (!empty) {
-                for (int ii = g + 1; ii <= w; ii += L) {
-                    const int dd = ii > istar ? ii - istar : istar - ii;
-                    if (dd < n) continue;
-                    const int32_t x = cb[ii - 1];
-                    if (si == 0 || x > sv) { sv = x; si = ii; }
-                }
+            const int wsec = empty ? 0 : w;
+            for (int ii = g + 1; ii <= wsec; ii += L) {
+                const int dd = ii > istar ? ii - istar : istar - ii;
+                if (dd < n) continue;
+                const int32_t x = cb[ii - 1];
+                if (si == 0 || x > sv) { sv = x; si = ii; }
+            }
 #pragma unroll
-                for (int o = 1; o < L; o <<= 1) {
-                    const int32_t ov = __shfl_xor_sync(FULL, sv, o, L);
-                    const int oi = __shfl_xor_sync(FULL, si, o, L);
-                    if (oi != 0 && (si == 0 || ov > sv || (ov == sv && oi < si))) { sv = ov; si = oi; }
-                }
+            for (int o = 1; o < L; o <<= 1) {
+                const int32_t ov = __shfl_xor_sync(FULL, sv, o, L);
+                const int oi = __shfl_xor_sync(FULL, si, o, L);
+                if (oi != 0 && (si == 0 || ov > sv || (ov == sv && oi < si))) { sv = ov; si = oi; }
             }
             if (g == 0 && has) {
                 JobState st;

@@ -11,7 +11,7 @@ struct PlanStats {                 // filled by the plan kernel (device)
     uint32_t bad_job;              // first invalid job (UINT32_MAX: none)
     uint32_t bad_read;             // first job with a non-ACGT base (UINT32_MAX: none)
     uint32_t max_wave;             // last direction-arena wave with work
-    uint32_t _pad;
+    uint32_t bad_walk;             // first job whose traceback left its rectangle (internal error)
     unsigned long long bad_ref_pos;
 };
 
@@ -44,7 +44,7 @@ void launch_scan_u32(const uint32_t* in, uint64_t n, uint64_t* out, uint64_t* bs
 void launch_traceback(const sa_job* jobs, uint32_t job_begin, uint32_t n_jobs, const JobState* state,
                       const Rect* rect, const uint32_t* arena, int wave, int mode, int plain,
                       int cfg_force, int32_t min_score, uint32_t* tmp_ops, uint32_t tmp_stride,
-                      TbOut* tb, cudaStream_t st);
+                      TbOut* tb, unsigned* err_job, cudaStream_t st);
 void launch_iota(uint32_t* p, uint32_t n, cudaStream_t st);
 void launch_cigar_count(const sa_job* jobs, uint32_t n_jobs, const JobState* state, const TbOut* tb,
                         int mode, int want_cigar, int32_t min_score, uint32_t* count,

@@ -381,7 +381,7 @@ __global__ void k_traceback(const sa_job* __restrict__ jobs, uint32_t job_begin,
                             const JobState* __restrict__ state, const Rect* __restrict__ rect,
                             const uint32_t* __restrict__ arena, int wave, int mode, int plain,
                             int cfg_force, int32_t min_score, uint32_t* __restrict__ tmp_ops,
-                            uint32_t tmp_stride, TbOut* __restrict__ tb) {
+                            uint32_t tmp_stride, TbOut* __restrict__ tb, unsigned* err_job) {
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= n_jobs) return;
     const uint32_t job = job_begin + tid;
@@ -415,7 +415,12 @@ __global__ void k_traceback(const sa_job* __restrict__ jobs, uint32_t job_begin,
     int i = si, j = sj;
     int state_ = 0;   // 0 H, 1 E (insertion), 2 F (deletion)
     const uint64_t off = R.off;
-    for (;;) {
+    // a valid walk emits at most w + rows ops and enters at most as many gap
+    // runs (one extra iteration each); anything longer is an internal error
+    int budget = 2 * (R.w + R.rows) + 4;
+    bool bad = (i < 0 || j < 0 || i > R.w || j > R.rows);
+    while (!bad) {
+        if (--budget < 0) { bad = true; break; }
         if (state_ == 0) {
             if (i == 0 || j == 0) break;
             const uint32_t nib = nibble_at(arena, off, L, K, pad, i, j);
@@ -425,16 +430,27 @@ __global__ void k_traceback(const sa_job* __restrict__ jobs, uint32_t job_begin,
             else if (src == 2u) state_ = 2;
             else state_ = 1;
         } else if (state_ == 2) {
+            if (i < 1 || j < 1) { bad = true; break; }
             const uint32_t nib = nibble_at(arena, off, L, K, pad, i, j);
             emit(2u, 1u);
             i--;
             state_ = (nib & 8u) ? 2 : 0;
         } else {
+            if (i < 1 || j < 1) { bad = true; break; }
             const uint32_t nib = nibble_at(arena, off, L, K, pad, i, j);
             emit(1u, 1u);
             j--;
             state_ = (nib & 4u) ? 1 : 0;
         }
+        if (nrev >= (int)tmp_stride - 1) { bad = true; break; }
+    }
+    if (bad) {
+        atomicMin(err_job, job);
+        out.n_rev = 0;
+        out.read_begin = 0;
+        out.ref_begin_rel = 0;
+        tb[job] = out;
+        return;
     }
     if (mode == SA_GLOCAL && j > 0) { emit(1u, (uint32_t)j); j = 0; }
     if (cur_len) ops[nrev++] = (cur_len << 4) | cur_op;
@@ -447,11 +463,11 @@ __global__ void k_traceback(const sa_job* __restrict__ jobs, uint32_t job_begin,
 void launch_traceback(const sa_job* jobs, uint32_t job_begin, uint32_t n_jobs, const JobState* state,
                       const Rect* rect, const uint32_t* arena, int wave, int mode, int plain,
                       int cfg_force, int32_t min_score, uint32_t* tmp_ops, uint32_t tmp_stride,
-                      TbOut* tb, cudaStream_t st) {
+                      TbOut* tb, unsigned* err_job, cudaStream_t st) {
     if (!n_jobs) return;
     k_traceback<<<(n_jobs + 127) / 128, 128, 0, st>>>(jobs, job_begin, n_jobs, state, rect, arena,
                                                        wave, mode, plain, cfg_force, min_score,
-                                                       tmp_ops, tmp_stride, tb);
+                                                       tmp_ops, tmp_stride, tb, err_job);
 }
 
 __global__ void k_iota(uint32_t* __restrict__ p, uint32_t n) {
