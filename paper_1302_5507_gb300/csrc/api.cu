@@ -509,7 +509,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
     if (P->profile) {
         stats.ms_stage = tm.ms(t0, t1);
         stats.ms_fill = tm.ms(t1, tfill1);
-        stats.ms_rect = tm.ms(trect0, trect1);
+        stats.ms_rect = tm.ms(tfill1, trect1);   // rectangle planning + direction pass
         stats.ms_traceback = tm.ms(trect1, ttb1);
         stats.ms_finalize = tm.ms(tfin0, tfin1);
         stats.ms_total = tm.ms(t0, tfin1);
