@@ -167,6 +167,35 @@ int sa_align_batch_dev(sa_reference* ref, const sa_params* params, const sa_job*
                        uint32_t* d_cigar, uint64_t cigar_cap, uint64_t* cigar_used,
                        void* cuda_stream);
 
+/* Allocation-free score pass.  This entry point has no counterpart in the
+ * paper; it exists for callers that cannot let a library allocate device
+ * memory: code inside a host framework that owns all device memory through its
+ * own allocator, and latency-sensitive callers that cannot afford the
+ * device-wide synchronisation cudaMalloc / cudaFree may imply.
+ *
+ * It computes what sa_align_batch_dev computes with want_cigar = 0 (score,
+ * read/reference ends, second best and its end, flags; begins -1, no CIGAR;
+ * params->want_cigar, width and form are ignored) on device buffers d_jobs,
+ * d_reads and d_out of the reference's device, and calls no cudaMalloc,
+ * cudaFree or allocating library routine.  Its intermediate arrays live in one
+ * file-scope device array of SA_NOALLOC_SCRATCH_BYTES that every device which
+ * loads the library holds until the process exits.  A batch whose
+ * intermediate arrays do not fit (about 30 + 4*ceil(max_n/16) bytes per job
+ * plus 4*max_m bytes per resident lane group) is rejected with SA_EINVAL and a
+ * message giving the size needed: split it.
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the array and it keeps the previous call's
+ * contents (the call clears what must start at zero), so calls whose work
+ * overlaps on the GPU -- on different streams or from different host threads
+ * -- race on it and must not be issued.  The work runs on cuda_stream (NULL:
+ * the reference's own stream) and the call returns when it has completed. */
+#define SA_NOALLOC_SCRATCH_BYTES (32u << 20)
+int sa_align_batch_noalloc(sa_reference* ref, const sa_params* params, const sa_job* d_jobs,
+                           uint32_t n_jobs, const char* d_reads, uint64_t reads_len,
+                           sa_result* d_out, void* cuda_stream);
+
 /* Statistics of the last sa_align_batch / sa_align_batch_dev call on ref. */
 int sa_last_stats(const sa_reference* ref, sa_stats* out);
 

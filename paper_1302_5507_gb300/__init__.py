@@ -84,6 +84,7 @@ def lib():
         L.sa_align_batch.argtypes = [_VP, ctypes.POINTER(sa_params), _VP, _U32, _VP, _U64, _VP, _VP,
                                      _U64, ctypes.POINTER(_U64), _VP]
         L.sa_align_batch_dev.argtypes = L.sa_align_batch.argtypes
+        L.sa_align_batch_noalloc.argtypes = [_VP, ctypes.POINTER(sa_params), _VP, _U32, _VP, _U64, _VP, _VP]
         L.sa_last_stats.argtypes = [_VP, ctypes.POINTER(sa_stats)]
         L.sa_server_create.argtypes = [_VP, ctypes.POINTER(sa_params), _U64, _U32, ctypes.POINTER(_VP)]
         L.sa_submit.argtypes = [_VP, _VP, _U32, _VP, _U64, ctypes.POINTER(_U64)]
@@ -91,7 +92,8 @@ def lib():
         L.sa_server_destroy.argtypes = [_VP]
         L.sa_last_error.restype = ctypes.c_char_p
         for name in ("sa_create_reference", "sa_destroy_reference", "sa_align_batch",
-                     "sa_align_batch_dev", "sa_last_stats", "sa_server_create", "sa_submit",
+                     "sa_align_batch_dev", "sa_align_batch_noalloc", "sa_last_stats",
+                     "sa_server_create", "sa_submit",
                      "sa_poll", "sa_server_destroy"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -148,6 +150,12 @@ def sa_align_batch_dev(h, params, jobs_ptr, n_jobs, reads_ptr, reads_len, out_pt
     rc = lib().sa_align_batch_dev(h, ctypes.byref(params), jobs_ptr, n_jobs, reads_ptr, reads_len,
                                   out_ptr, cigar_ptr, cigar_cap, ctypes.byref(used), stream)
     return rc, used.value
+
+
+def sa_align_batch_noalloc(h, params, jobs_ptr, n_jobs, reads_ptr, reads_len, out_ptr, stream=None):
+    """Allocation-free score pass (see sa.h); returns the status code."""
+    return lib().sa_align_batch_noalloc(h, ctypes.byref(params), jobs_ptr, n_jobs, reads_ptr, reads_len,
+                                        out_ptr, stream)
 
 
 def sa_last_stats(h) -> sa_stats:

@@ -928,3 +928,18 @@ int sa_server_destroy(sa_server* S) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// read-only view of a reference handle for the other translation units
+
+namespace sa {
+RefView ref_view(const sa_reference* R) {
+    return RefView{R->d_words, R->len, R->device, R->num_sms, R->own};
+}
+
+// the calling thread's sa_last_error() message, for the other translation units
+int set_error(int code, const char* msg) {
+    snprintf(g_err, sizeof(g_err), "%s", msg);
+    return code;
+}
+}  // namespace sa

@@ -58,6 +58,17 @@ void launch_finalize(const sa_job* jobs, uint32_t n_jobs, const JobState* state,
 void launch_fill_cfg(int cfg, const FillLaunch& fl);
 int fill_max_blocks_per_sm(int cfg, int kind, int mode);
 
+// what other translation units may read of a reference handle (api.cu)
+struct RefView {
+    const uint32_t* d_words;       // padded packed reference
+    uint64_t len;                  // bases
+    int device;
+    int num_sms;
+    cudaStream_t own;              // the reference's own stream
+};
+RefView ref_view(const sa_reference* R);
+int set_error(int code, const char* msg);   // sets sa_last_error() for the calling thread
+
 // scan scratch: number of uint64 block sums needed for n elements
 inline uint64_t scan_bsum_len(uint64_t n) { return (n + 1023) / 1024 + 1; }
 
