@@ -29,6 +29,17 @@ __device__ __forceinline__ int32_t addmax(int32_t a, int32_t b, int32_t c) {
     return __viaddmax_s32(a, b, c);   // max(a + b, c)
 }
 
+// x + y issued as an integer multiply-add (x * one + y) with a `one` the compiler
+// cannot see, so the add runs on the FMA pipe and leaves the ALU pipe (where the
+// max operations of the recurrence run) to the maxima
+__device__ __forceinline__ int32_t add_fma(int32_t x, int32_t y, int32_t one) { return x * one + y; }
+
+// Shared-memory words of the score pass's per-lane profile: for each window base
+// t and read row r of the lane, the diagonal term (a or b) minus S_GO, rows
+// padded to a multiple of 4 so that one 16-byte load serves four rows.
+template <int K>
+constexpr int prof_words_per_warp() { return 4 * ((K + 3) / 4) * 4 * 32; }
+
 template <int L, int K>
 __device__ __forceinline__ uint32_t load_window16(const FillArgs& A, int64_t wstart, int b, int g) {
     // 8 bases for columns of block b of lane g: positions wstart + 8b - g .. +7
@@ -55,6 +66,13 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
     int32_t* cb = BEST ? A.colbest + (size_t)(gwarp * G + grp) * A.cb_stride : nullptr;
     const Score S = A.sc;
     const uint32_t count = A.count_ptr ? *A.count_ptr : A.pos_count;
+    // the score pass takes the match/mismatch term from a shared-memory profile
+    constexpr bool PROF = BEST && !DIR;
+    constexpr int K4 = (K + 3) / 4;
+    extern __shared__ __align__(16) int32_t s_prof[];
+    int32_t* prof = s_prof + (threadIdx.x >> 5) * prof_words_per_warp<K>();
+    // 1 at run time (every launch uses 128-thread blocks), unknown to the compiler
+    const int32_t one = (int32_t)(blockDim.x >> 7);
 
     for (;;) {
         uint32_t item = 0;
@@ -95,7 +113,21 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
         const int pad = LOCAL ? (L * K - rows) : 0;
         // match masks: bit r of mX is set when the lane's row r holds base X
         uint32_t mA = 0, mC = 0, mG = 0, mT = 0;
-        {
+        if (PROF) {
+            // profile: word ((t*K4 + r/4)*32 + lane)*4 + r%4 holds the diagonal term of
+            // row r against window base t (rows that are padding never match)
+            const uint32_t* rp = A.rpack + (size_t)job * A.rw;
+#pragma unroll
+            for (int r = 0; r < 4 * K4; r++) {
+                const int j = g * K + r + 1 - pad;
+                int code = -1;
+                if (r < K && w > 0 && j >= 1 && j <= rows)
+                    code = (int)((__ldg(rp + ((j - 1) >> 4)) >> (2 * ((j - 1) & 15))) & 3u);
+#pragma unroll
+                for (int t = 0; t < 4; t++)
+                    prof[((t * K4 + r / 4) * 32 + lane) * 4 + (r & 3)] = code == t ? S.dm : S.dx;
+            }
+        } else {
             const uint32_t* rp = A.rpack + (size_t)job * A.rw;
 #pragma unroll
             for (int r = 0; r < K; r++) {
@@ -154,13 +186,22 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
                 int32_t diag = h_up_prev;
                 h_up_prev = hg_up;
                 const uint32_t t = (wb >> (2 * u)) & 3u;
-                const uint32_t mk = t == 0 ? mA : (t == 1 ? mC : (t == 2 ? mG : mT));
+                const uint32_t mk = PROF ? 0u : (t == 0 ? mA : (t == 1 ? mC : (t == 2 ? mG : mT)));
+                const int4* pt = reinterpret_cast<const int4*>(prof) + (t * K4) * 32 + lane;
+                int4 dq = make_int4(0, 0, 0, 0);
                 int32_t e = e_up, hga = hg_up;
-                int32_t lm = 0;
+                int32_t lm = 0, hpair = 0;
 #pragma unroll
                 for (int r = 0; r < K; r++) {
-                    const int32_t d = ((mk >> r) & 1u) ? S.dm : S.dx;
-                    const int32_t gv = diag + d;          // H(i-1,j-1) + delta
+                    int32_t d;
+                    if (PROF) {
+                        if ((r & 3) == 0) dq = pt[(r / 4) * 32];
+                        d = (r & 3) == 0 ? dq.x : (r & 3) == 1 ? dq.y : (r & 3) == 2 ? dq.z : dq.w;
+                    } else {
+                        d = ((mk >> r) & 1u) ? S.dm : S.dx;
+                    }
+                    // H(i-1,j-1) + delta
+                    const int32_t gv = PROF ? add_fma(d, diag, one) : diag + d;
                     diag = HG[r];
                     int32_t f, h;
                     if (!DIR) {
@@ -185,9 +226,18 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
                         dw[q >> 3] |= nib << (4 * (q & 7));
                     }
                     F[r] = f;
-                    HG[r] = h + S.GO;
+                    HG[r] = PROF ? add_fma(h, S.GO, one) : h + S.GO;
                     hga = HG[r];
-                    if (BEST && LOCAL) lm = max(lm, h);
+                    if (BEST && LOCAL) {
+                        // column maximum, two rows per 3-input max
+                        if (PROF) {
+                            if ((r & 1) == 1) lm = __vimax3_s32(lm, hpair, h);
+                            else if (r == K - 1) lm = max(lm, h);
+                            else hpair = h;
+                        } else {
+                            lm = max(lm, h);
+                        }
+                    }
                 }
                 hg_bot = HG[K - 1];
                 e_bot = e;

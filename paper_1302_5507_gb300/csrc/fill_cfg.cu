@@ -13,15 +13,32 @@ namespace {
 constexpr int kL = kCfgs[SA_CFG].L;
 constexpr int kK = kCfgs[SA_CFG].K;
 
+// dynamic shared memory of a 128-thread block: the score pass's profile
+template <bool DIR, bool BEST>
+constexpr size_t smem_bytes() { return (BEST && !DIR) ? 4 * prof_words_per_warp<kK>() * sizeof(int32_t) : 0; }
+
+template <int MODE, bool DIR, bool BEST>
+void prepare() {
+    static bool done = false;   // attribute set once per process (same on every device)
+    if (!done) {
+        cudaFuncSetAttribute(k_fill32<kL, kK, MODE, DIR, BEST>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<DIR, BEST>());
+        done = true;
+    }
+}
+
 template <int MODE, bool DIR, bool BEST>
 void launch_one(const FillLaunch& fl) {
-    k_fill32<kL, kK, MODE, DIR, BEST><<<fl.grid, fl.block, 0, fl.stream>>>(fl.args);
+    prepare<MODE, DIR, BEST>();
+    k_fill32<kL, kK, MODE, DIR, BEST><<<fl.grid, fl.block, smem_bytes<DIR, BEST>(), fl.stream>>>(fl.args);
 }
 
 template <int MODE, bool DIR, bool BEST>
 int blocks_per_sm() {
+    prepare<MODE, DIR, BEST>();
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fill32<kL, kK, MODE, DIR, BEST>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fill32<kL, kK, MODE, DIR, BEST>, 128,
+                                                  smem_bytes<DIR, BEST>());
     return nb;
 }
 }  // namespace
