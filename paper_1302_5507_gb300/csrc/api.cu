@@ -90,20 +90,21 @@ struct PlanBlock {
     uint32_t cfg_begin[kNumCfg + 1];
     uint32_t _pad;
     uint64_t totals[4];
+    uint32_t cls_count[4];         // direction-pass classes (none, band 16, band 32, rectangle)
 };
 
 // Device buffers of one computation at a time (grown on demand, reused).
 struct Workspace {
     DevBuf jobs, reads, out, cigar;          // inputs/outputs of the host-buffer entry points
     DevBuf key, order, rpack, state, rect, tb, count, coff, sizes, offs, bsum;
-    DevBuf colbest, tmp_ops, arena, plan, counters;
+    DevBuf colbest, tmp_ops, arena, plan, counters, list16, list32, band;
     PlanBlock* h_plan = nullptr;             // pinned mirror of the plan block
     cudaEvent_t ev[16] = {};
     bool ev_ok = false;
     void release() {
         DevBuf* all[] = {&jobs, &reads, &out, &cigar, &key, &order, &rpack, &state, &rect, &tb,
                          &count, &coff, &sizes, &offs, &bsum, &colbest, &tmp_ops, &arena,
-                         &plan, &counters};
+                         &plan, &counters, &list16, &list32, &band};
         for (DevBuf* b : all) b->release();
         if (h_plan) cudaFreeHost(h_plan);
         h_plan = nullptr;
@@ -339,7 +340,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
     uint32_t* counters = ws.counters.as<uint32_t>();
     auto next_counter = [&]() { return counters + (counter_next++ % 256); };
 
-    int tfill1 = -1, trect0 = -1, trect1 = -1, ttb1 = -1;
+    int tfill1 = -1, trect1 = -1, ttb1 = -1;
     if (!plain) {
         // --- score pass: one persistent launch per non-empty length bucket
         for (int c = 0; c < kNumCfg; c++) {
@@ -364,17 +365,53 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
         tfill1 = tm.mark();
 
         if (want_cigar) {
-            // --- reduced traceback: rectangles, arena waves, direction pass, walk
+            // --- reduced traceback: banded direction pass for most jobs, the
+            // wavefront rectangle pass (in arena waves) for wide bands, then the walk
+            TRY(ws.list16.ensure((size_t)n_jobs * 4, "band lists"));
+            TRY(ws.list32.ensure((size_t)n_jobs * 4, "band lists"));
             launch_rect_plan(d_jobs, ws.order.as<uint32_t>(), n_jobs, ws.state.as<JobState>(), sc,
-                             min_score, 0, ws.rect.as<Rect>(), ws.sizes.as<uint64_t>(), st);
+                             min_score, 1, ws.rect.as<Rect>(), ws.sizes.as<uint64_t>(),
+                             ws.list16.as<uint32_t>(), ws.list32.as<uint32_t>(), dp->cls_count, st);
             launch_scan_u64(ws.sizes.as<uint64_t>(), n_jobs, ws.offs.as<uint64_t>(),
                             ws.bsum.as<uint64_t>(), &dp->totals[0], st);
             launches += 4;
             CU(cudaGetLastError());
             trace("rect plan + scan");
             CU(cudaMemcpyAsync(&hp->totals[0], &dp->totals[0], 8, cudaMemcpyDeviceToHost, st));
+            CU(cudaMemcpyAsync(hp->cls_count, dp->cls_count, sizeof(hp->cls_count), cudaMemcpyDeviceToHost, st));
             TRY(check_bad_read(dp, hp, st));
             const uint64_t total_words = hp->totals[0];
+            const uint32_t n16 = hp->cls_count[kClsBand16], n32 = hp->cls_count[kClsBand32];
+            // band regions: 32 jobs of a class share a region of max_n rows x B/8 words x 32 lanes
+            BandLayout bl{};
+            bl.warp_stride[0] = (uint64_t)max_n * 2 * 32;
+            bl.warp_stride[1] = (uint64_t)max_n * 4 * 32;
+            bl.base[0] = 0;
+            bl.base[1] = (uint64_t)((n16 + 31) / 32) * bl.warp_stride[0];
+            const uint64_t band_words = bl.base[1] + (uint64_t)((n32 + 31) / 32) * bl.warp_stride[1];
+            TRY(ws.band.ensure(std::max<uint64_t>(band_words, 1) * 4, "band arena"));
+            bl.arena = ws.band.as<uint32_t>();
+
+            for (int k = 0; k < 2; k++) {
+                BandArgs ba{};
+                ba.ref = X.d_words;
+                ba.ref_len = (int64_t)X.len;
+                ba.jobs = d_jobs;
+                ba.rpack = ws.rpack.as<uint32_t>();
+                ba.rw = rw;
+                ba.rect = ws.rect.as<Rect>();
+                ba.list = k == 0 ? ws.list16.as<uint32_t>() : ws.list32.as<uint32_t>();
+                ba.count = k == 0 ? n16 : n32;
+                ba.arena = ws.band.as<uint32_t>() + bl.base[k];
+                ba.warp_stride = bl.warp_stride[k];
+                ba.sc = sc;
+                if (ba.count) {
+                    launch_band(k == 0 ? kClsBand16 : kClsBand32, ba, st);
+                    launches++;
+                }
+            }
+            CU(cudaGetLastError());
+            trace("band passes");
             // largest item: G jobs of the largest rectangle (bounded by the whole window)
             uint64_t item_max = 0;
             for (int c = 0; c < kNumCfg; c++)
@@ -395,10 +432,9 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
                                wave_words, ws.rect.as<Rect>(), &dp->st.max_wave, st);
             launches++;
             const uint32_t waves = wave_words ? (uint32_t)((total_words + wave_words - 1) / wave_words) : 1;
-            stats.waves = waves;
-            trect0 = tm.mark();
+            stats.waves = total_words ? waves : 0;
             for (uint32_t wv = 0; wv < waves; wv++) {
-                for (int c = 0; c < kNumCfg; c++) {
+                for (int c = 0; c < kNumCfg && total_words; c++) {
                     if (!cfg_count[c]) continue;
                     FillLaunch fl{};
                     fl.args = base;
@@ -419,7 +455,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
                 }
                 if (wv == 0) trect1 = tm.mark();
                 launch_traceback(d_jobs, 0, n_jobs, ws.state.as<JobState>(), ws.rect.as<Rect>(),
-                                 ws.arena.as<uint32_t>(), (int)wv, mode, 0, -1, min_score,
+                                 ws.arena.as<uint32_t>(), bl, (int)wv, mode, 0, -1, min_score,
                                  ws.tmp_ops.as<uint32_t>(), tmp_stride, ws.tb.as<TbOut>(), &dp->st.bad_walk, st);
                 launches++;
                 CU(cudaGetLastError());
@@ -458,7 +494,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             launches += 2;
             if (want_cigar) {
                 launch_traceback(d_jobs, j0, nb, ws.state.as<JobState>(), ws.rect.as<Rect>(),
-                                 ws.arena.as<uint32_t>(), 0, mode, 1, c, min_score,
+                                 ws.arena.as<uint32_t>(), BandLayout{}, 0, mode, 1, c, min_score,
                                  ws.tmp_ops.as<uint32_t>(), tmp_stride, ws.tb.as<TbOut>(), &dp->st.bad_walk, st);
                 launches++;
             }

@@ -1,0 +1,124 @@
+// Banded direction pass: one thread per job, direction nibbles of the cells on
+// the diagonals that can hold an optimal path ending at the best cell.
+//
+// Every optimal path ending at (i*, j*) with score `best` consumes at most j*
+// read bases, and each insertion costs at least a + e (the match it displaces
+// plus its own extension), each deletion at least e.  With S = a*j* - best this
+// gives #I <= S/(a+e) and #D <= S/e, so the path stays on the diagonals
+// d = i - j in [d* - S/e, d* + S/(a+e)] (d* = i* - j*).  The DP restricted to
+// those diagonals (everything else -inf; row 0 and column 0 keep their border
+// values) reproduces every value on such paths and every comparison the
+// traceback makes, so walking its nibbles from (i*, j*) gives the same CIGAR
+// as the full matrix (SOAP3-dp Methods section 3 backtracks from the full D and
+// M tables; this stores 4 bits for band-width cells per row instead).
+//
+// Row j is computed left to right over the band slots k = i - j - d_lo; the
+// previous row stays in registers in place: slot k holds H(i-1, j-1) for the
+// diagonal move and slot k+1 holds H(i, j-1), E(i, j-1) for the vertical one.
+// Nibble words are stored interleaved by lane (word w of row j of the job in
+// lane t at ((j-1)*W + w)*32 + t of its warp's region), so the stores of a warp
+// are coalesced.
+#include "kernels.h"
+
+namespace sa {
+
+namespace {
+
+template <int B, int MODE>
+__global__ void __launch_bounds__(128) k_band(BandArgs A) {
+    constexpr bool LOCAL = (MODE == SA_LOCAL);
+    constexpr int W = B / 8;
+    static_assert(B == 16 || B == 32, "band widths 16 and 32");
+    const uint32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= A.count) return;
+    const uint32_t job = A.list[pos];
+    const sa_job J = A.jobs[job];
+    const Rect R = A.rect[job];
+    const int rows = R.rows;
+    const int dlo = R.d_lo;
+    const Score S = A.sc;
+    uint32_t* out = A.arena + (uint64_t)(pos >> 5) * A.warp_stride + (pos & 31);
+    const uint32_t* rp = A.rpack + (size_t)job * A.rw;
+    const uint32_t* refw = A.ref + kRefFrontPad;
+
+    int32_t Hs[B + 1], Es[B + 1];
+#pragma unroll
+    for (int k = 0; k <= B; k++) {            // row 0: H(i,0) = 0 for i >= 0, E = -inf
+        Hs[k] = (k < B && dlo + k >= 0) ? 0 : kNeg32;
+        Es[k] = kNeg32;
+    }
+    for (int j = 1; j <= rows; j++) {
+        const int i0 = j + dlo;               // window column of slot 0
+        // window bases of slots 0..B-1 (reference positions ref_pos + i0 - 1 + k);
+        // positions before the window start only feed masked slots
+        const int64_t p0 = (int64_t)J.ref_pos + i0 - 1;
+        int64_t q0 = p0 < (int64_t)J.ref_pos ? (int64_t)J.ref_pos : p0;
+        if (q0 > A.ref_len) q0 = A.ref_len;
+        const int64_t wi = q0 >> 4;
+        const uint32_t sh = (uint32_t)(q0 & 15) * 2u;
+        const uint64_t lo = ((uint64_t)__ldg(refw + wi + 1) << 32) | (uint64_t)__ldg(refw + wi);
+        const uint64_t hi = (uint64_t)__ldg(refw + wi + 2);
+        uint64_t wb = sh ? ((lo >> sh) | (hi << (64 - sh))) : lo;
+        const int64_t lead = q0 - p0;         // slots before the clamped start
+        wb = lead >= 32 ? 0ull : (wb << (2 * lead));
+        const uint64_t rb = (uint64_t)((__ldg(rp + ((j - 1) >> 4)) >> (2 * ((j - 1) & 15))) & 3u);
+        const uint64_t x = wb ^ (rb * 0x5555555555555555ull);
+        const uint64_t mm = ~(x | (x >> 1)) & 0x5555555555555555ull;   // bit 2k: slot k matches
+        const int32_t border = (!LOCAL) ? S.GO + (j - 1) * S.GE : 0;  // H(0, j)
+        const bool edge = i0 < 1;
+        int32_t hleft = kNeg32, fleft = kNeg32;
+        uint32_t words[W];
+#pragma unroll
+        for (int w = 0; w < W; w++) words[w] = 0u;
+#pragma unroll
+        for (int k = 0; k < B; k++) {
+            int32_t hn, en, fn;
+            uint32_t nib = 0u;
+            const int i = i0 + k;
+            if (edge && i <= 0) {
+                hn = (i == 0) ? border : kNeg32;
+                en = kNeg32;
+                fn = kNeg32;
+            } else {
+                const int32_t diag = Hs[k], up = Hs[k + 1], eup = Es[k + 1];
+                const int32_t ee = eup + S.GE, eo = up + S.GO;
+                const bool eopen = eo >= ee;
+                en = eopen ? eo : ee;
+                const int32_t fe = fleft + S.GE, fo = hleft + S.GO;
+                const bool fopen = fo >= fe;
+                fn = fopen ? fo : fe;
+                const int32_t g = diag + (((mm >> (2 * k)) & 1ull) ? S.a : S.b);
+                const bool pF = fn >= en;
+                const int32_t ef = pF ? fn : en;
+                const bool pG = g >= ef;
+                int32_t h = pG ? g : ef;
+                uint32_t src = pG ? 1u : (pF ? 2u : 3u);
+                if (LOCAL && h <= 0) { h = 0; src = 0u; }
+                nib = src | (eopen ? 0u : 4u) | (fopen ? 0u : 8u);
+                hn = h;
+            }
+            Hs[k] = hn;
+            Es[k] = en;
+            hleft = hn;
+            fleft = fn;
+            words[k >> 3] |= nib << (4 * (k & 7));
+        }
+#pragma unroll
+        for (int w = 0; w < W; w++) out[((uint64_t)(j - 1) * W + w) * 32] = words[w];
+    }
+}
+
+}  // namespace
+
+void launch_band(int cls, const BandArgs& a, cudaStream_t st) {
+    if (!a.count) return;
+    const unsigned grid = (a.count + 127) / 128;
+    const bool local = a.sc.mode == SA_LOCAL;
+    if (cls == kClsBand16) {
+        local ? k_band<16, SA_LOCAL><<<grid, 128, 0, st>>>(a) : k_band<16, SA_GLOCAL><<<grid, 128, 0, st>>>(a);
+    } else {
+        local ? k_band<32, SA_LOCAL><<<grid, 128, 0, st>>>(a) : k_band<32, SA_GLOCAL><<<grid, 128, 0, st>>>(a);
+    }
+}
+
+}  // namespace sa

@@ -15,6 +15,26 @@ struct PlanStats {                 // filled by the plan kernel (device)
     unsigned long long bad_ref_pos;
 };
 
+struct BandArgs {                  // banded direction pass of one class
+    const uint32_t* ref;
+    int64_t ref_len;
+    const sa_job* jobs;
+    const uint32_t* rpack;
+    uint32_t rw;
+    const Rect* rect;
+    const uint32_t* list;          // job ids of this class
+    uint32_t count;
+    uint32_t* arena;               // this class's region
+    uint64_t warp_stride;          // words per 32 list entries (max_n * B/8 * 32)
+    Score sc;
+};
+
+struct BandLayout {                // where the traceback finds band nibbles
+    const uint32_t* arena;
+    uint64_t base[2];              // word offset of the class 16 / class 32 regions
+    uint64_t warp_stride[2];
+};
+
 struct TbOut {                     // traceback result of one job
     int32_t n_rev;                 // ops written (reverse order) to the temporary slot
     int32_t read_begin;            // 0-based
@@ -30,8 +50,10 @@ void launch_plan_order(const uint16_t* key, uint32_t n_jobs, const uint32_t* his
 void launch_pack_reads(const sa_job* jobs, uint32_t n_jobs, const uint8_t* reads, uint32_t* rpack,
                        uint32_t rw, unsigned* bad_job, cudaStream_t st);
 void launch_rect_plan(const sa_job* jobs, const uint32_t* order, uint32_t n_pos,
-                      const JobState* state, const Score& sc, int32_t min_score, int plain,
-                      Rect* rect, uint64_t* sizes, cudaStream_t st);
+                      const JobState* state, const Score& sc, int32_t min_score, int allow_band,
+                      Rect* rect, uint64_t* sizes, uint32_t* list16, uint32_t* list32,
+                      uint32_t* cls_count, cudaStream_t st);
+void launch_band(int cls, const BandArgs& a, cudaStream_t st);
 void launch_rect_assign(const uint32_t* order, uint32_t n_pos, const uint64_t* offs,
                         const uint32_t* cfg_begin, uint64_t wave_words, Rect* rect,
                         uint32_t* max_wave, cudaStream_t st);
@@ -42,9 +64,9 @@ void launch_scan_u64(const uint64_t* in, uint64_t n, uint64_t* out, uint64_t* bs
 void launch_scan_u32(const uint32_t* in, uint64_t n, uint64_t* out, uint64_t* bsum, uint64_t* total,
                      cudaStream_t st);
 void launch_traceback(const sa_job* jobs, uint32_t job_begin, uint32_t n_jobs, const JobState* state,
-                      const Rect* rect, const uint32_t* arena, int wave, int mode, int plain,
-                      int cfg_force, int32_t min_score, uint32_t* tmp_ops, uint32_t tmp_stride,
-                      TbOut* tb, unsigned* err_job, cudaStream_t st);
+                      const Rect* rect, const uint32_t* arena, const BandLayout& band, int wave,
+                      int mode, int plain, int cfg_force, int32_t min_score, uint32_t* tmp_ops,
+                      uint32_t tmp_stride, TbOut* tb, unsigned* err_job, cudaStream_t st);
 void launch_iota(uint32_t* p, uint32_t n, cudaStream_t st);
 void launch_cigar_count(const sa_job* jobs, uint32_t n_jobs, const JobState* state, const TbOut* tb,
                         int mode, int want_cigar, int32_t min_score, uint32_t* count,

@@ -93,7 +93,13 @@ struct Rect {
     int32_t start_i;    // traceback start cell in rect coordinates
     int32_t start_j;
     int32_t wave;
+    // banded form (cls 1, 2): diagonals d = i - j in [d_lo, d_lo + band width)
+    int32_t cls;        // 0 none, 1 band of 16, 2 band of 32, 3 wavefront rectangle
+    int32_t d_lo;
+    uint32_t lpos;      // position in its class list
+    int32_t _pad;
 };
+enum { kClsNone = 0, kClsBand16 = 1, kClsBand32 = 2, kClsRect = 3 };
 
 // Arguments of the wavefront kernels.
 struct FillArgs {

@@ -187,13 +187,13 @@ void launch_pack_reads(const sa_job* jobs, uint32_t n_jobs, const uint8_t* reads
 
 __global__ void k_rect_plan(const sa_job* __restrict__ jobs, const uint32_t* __restrict__ order,
                             uint32_t n_pos, const JobState* __restrict__ state, Score sc,
-                            int32_t min_score, int plain, Rect* __restrict__ rect,
-                            uint64_t* __restrict__ sizes) {
+                            int32_t min_score, int allow_band, Rect* __restrict__ rect,
+                            uint64_t* __restrict__ sizes, uint32_t* __restrict__ list16,
+                            uint32_t* __restrict__ list32, uint32_t* cls_count) {
+    // no early return: the class lists are appended with warp-wide ballots
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n_pos) return;
-    const uint32_t job = order[p];
-    const sa_job J = jobs[job];
-    const JobState st = state[job];
+    const bool valid = p < n_pos;
+    const uint32_t job = valid ? order[p] : 0u;
     Rect R;
     R.off = 0;
     R.wave = 0;
@@ -202,40 +202,69 @@ __global__ void k_rect_plan(const sa_job* __restrict__ jobs, const uint32_t* __r
     R.rows = 0;
     R.start_i = 0;
     R.start_j = 0;
-    const int c = cfg_for_rows((int)J.read_len);
-    const bool tb = !(st.flags & kStEmpty) && st.best >= min_score;
-    if (plain) {
-        // direction bits over the whole window for every job (the best cell is
-        // only known after the fill, so the start cell is set by the traceback)
-        R.i_lo = 1;
-        R.w = (int)J.win_len;
-        R.rows = (int)J.read_len;
-    } else if (tb) {
-        const int istar = st.i_star, jstar = st.j_star;
-        int64_t span = istar;
-        const int32_t e = -sc.GE;
-        if (e > 0) {
-            const int64_t slack = (int64_t)sc.a * jstar - st.best;
-            span = (int64_t)jstar + (slack > 0 ? slack / e : 0);
+    R.cls = kClsNone;
+    R.d_lo = 0;
+    R.lpos = 0;
+    R._pad = 0;
+    int c = 0;
+    if (valid) {
+        const sa_job J = jobs[job];
+        const JobState st = state[job];
+        c = cfg_for_rows((int)J.read_len);
+        if (!(st.flags & kStEmpty) && st.best >= min_score) {
+            const int istar = st.i_star, jstar = st.j_star;
+            const int64_t slack = (int64_t)sc.a * jstar - st.best;     // S = a*j* - best >= 0
+            const int32_t e = -sc.GE;
+            int64_t span = istar;
+            R.cls = kClsRect;
+            if (e > 0) {
+                const int64_t dmax = slack / e, imax = slack / (sc.a + e);
+                const int64_t width = dmax + imax + 1;
+                R.d_lo = (int)((int64_t)(istar - jstar) - dmax);
+                if (allow_band) R.cls = width <= 16 ? kClsBand16 : (width <= 32 ? kClsBand32 : kClsRect);
+                span = (int64_t)jstar + dmax;
+            }
+            R.rows = jstar;
+            if (R.cls == kClsRect) {
+                int64_t ilo = (int64_t)istar - span + 1;
+                if (ilo < 1) ilo = 1;
+                R.i_lo = (int)ilo;
+                R.w = istar - (int)ilo + 1;
+                R.start_i = R.w;
+                R.start_j = jstar;
+            }
         }
-        int64_t ilo = (int64_t)istar - span + 1;
-        if (ilo < 1) ilo = 1;
-        R.i_lo = (int)ilo;
-        R.w = istar - (int)ilo + 1;
-        R.rows = jstar;
-        R.start_i = R.w;
-        R.start_j = jstar;
     }
-    rect[job] = R;
-    sizes[p] = R.w > 0 ? dir_words(cfg_L(c), cfg_K(c), R.w) : 0;
+    const unsigned lane = threadIdx.x & 31u;
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const int cls = k == 0 ? kClsBand16 : kClsBand32;
+        const unsigned mask = __ballot_sync(0xffffffffu, valid && R.cls == cls);
+        if (mask) {
+            const int leader = __ffs(mask) - 1;
+            uint32_t base = 0;
+            if ((int)lane == leader) base = atomicAdd(&cls_count[cls], (uint32_t)__popc(mask));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (valid && R.cls == cls) {
+                R.lpos = base + (uint32_t)__popc(mask & ((1u << lane) - 1u));
+                (k == 0 ? list16 : list32)[R.lpos] = job;
+            }
+        }
+    }
+    if (valid) {
+        rect[job] = R;
+        sizes[p] = R.w > 0 ? dir_words(cfg_L(c), cfg_K(c), R.w) : 0;
+    }
 }
 
 void launch_rect_plan(const sa_job* jobs, const uint32_t* order, uint32_t n_pos,
-                      const JobState* state, const Score& sc, int32_t min_score, int plain,
-                      Rect* rect, uint64_t* sizes, cudaStream_t st) {
+                      const JobState* state, const Score& sc, int32_t min_score, int allow_band,
+                      Rect* rect, uint64_t* sizes, uint32_t* list16, uint32_t* list32,
+                      uint32_t* cls_count, cudaStream_t st) {
     if (!n_pos) return;
-    k_rect_plan<<<(n_pos + 255) / 256, 256, 0, st>>>(jobs, order, n_pos, state, sc, min_score, plain,
-                                                      rect, sizes);
+    k_rect_plan<<<(n_pos + 255) / 256, 256, 0, st>>>(jobs, order, n_pos, state, sc, min_score,
+                                                      allow_band, rect, sizes, list16, list32,
+                                                      cls_count);
 }
 
 // wave assignment: an item (the G jobs a warp takes at once) belongs to the wave
@@ -377,16 +406,24 @@ __device__ __forceinline__ uint32_t nibble_at(const uint32_t* __restrict__ arena
     return (word >> (4 * (q & 7))) & 15u;
 }
 
+__device__ __forceinline__ uint32_t band_nibble(const uint32_t* __restrict__ arena, uint64_t base,
+                                                int W, int k, int j) {
+    const uint32_t word = arena[base + ((uint64_t)(j - 1) * W + (k >> 3)) * 32];
+    return (word >> (4 * (k & 7))) & 15u;
+}
+
 __global__ void k_traceback(const sa_job* __restrict__ jobs, uint32_t job_begin, uint32_t n_jobs,
                             const JobState* __restrict__ state, const Rect* __restrict__ rect,
-                            const uint32_t* __restrict__ arena, int wave, int mode, int plain,
+                            const uint32_t* __restrict__ arena, BandLayout band, int wave, int mode,
+                            int plain,
                             int cfg_force, int32_t min_score, uint32_t* __restrict__ tmp_ops,
                             uint32_t tmp_stride, TbOut* __restrict__ tb, unsigned* err_job) {
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= n_jobs) return;
     const uint32_t job = job_begin + tid;
     const Rect R = rect[job];
-    if (R.w <= 0 || R.wave != wave) return;
+    const bool banded = R.cls == kClsBand16 || R.cls == kClsBand32;
+    if (banded ? wave != 0 : (R.w <= 0 || R.wave != wave)) return;
     const sa_job J = jobs[job];
     const JobState st = state[job];
     TbOut out;
@@ -403,6 +440,17 @@ __global__ void k_traceback(const sa_job* __restrict__ jobs, uint32_t job_begin,
     const int c = cfg_force >= 0 ? cfg_force : cfg_for_rows((int)J.read_len);
     const int L = cfg_L(c), K = cfg_K(c);
     const int pad = (mode == SA_LOCAL) ? L * K - R.rows : 0;
+    // banded jobs walk in window coordinates (start at the best cell, border at
+    // column 0); rectangle jobs in rectangle coordinates (border at column 0 of
+    // the rectangle, window column i_lo - 1)
+    const int bw = R.cls == kClsBand16 ? 16 : 32;
+    const int bc = R.cls == kClsBand16 ? 0 : 1;
+    const uint64_t bbase = banded ? band.base[bc] + (uint64_t)(R.lpos >> 5) * band.warp_stride[bc] + (R.lpos & 31u) : 0;
+    if (banded) {
+        si = st.i_star;
+        sj = st.j_star;
+    }
+    const int imax_walk = banded ? st.i_star : R.w;
     uint32_t* ops = tmp_ops + (uint64_t)job * tmp_stride;
     int nrev = 0;
     uint32_t cur_op = 15u, cur_len = 0;
@@ -417,13 +465,22 @@ __global__ void k_traceback(const sa_job* __restrict__ jobs, uint32_t job_begin,
     const uint64_t off = R.off;
     // a valid walk emits at most w + rows ops and enters at most as many gap
     // runs (one extra iteration each); anything longer is an internal error
-    int budget = 2 * (R.w + R.rows) + 4;
-    bool bad = (i < 0 || j < 0 || i > R.w || j > R.rows);
+    int budget = 2 * (imax_walk + R.rows) + 4;
+    bool bad = (i < 0 || j < 0 || i > imax_walk || j > R.rows);
+    auto nib_at = [&](int ii, int jj, bool* out_bad) -> uint32_t {
+        if (banded) {
+            const int k = ii - jj - R.d_lo;
+            if (k < 0 || k >= bw) { *out_bad = true; return 0u; }
+            return band_nibble(band.arena, bbase, bw / 8, k, jj);
+        }
+        return nibble_at(arena, off, L, K, pad, ii, jj);
+    };
     while (!bad) {
         if (--budget < 0) { bad = true; break; }
         if (state_ == 0) {
             if (i == 0 || j == 0) break;
-            const uint32_t nib = nibble_at(arena, off, L, K, pad, i, j);
+            const uint32_t nib = nib_at(i, j, &bad);
+            if (bad) break;
             const uint32_t src = nib & 3u;
             if (src == 0u) break;
             if (src == 1u) { emit(0u, 1u); i--; j--; }
@@ -431,13 +488,15 @@ __global__ void k_traceback(const sa_job* __restrict__ jobs, uint32_t job_begin,
             else state_ = 1;
         } else if (state_ == 2) {
             if (i < 1 || j < 1) { bad = true; break; }
-            const uint32_t nib = nibble_at(arena, off, L, K, pad, i, j);
+            const uint32_t nib = nib_at(i, j, &bad);
+            if (bad) break;
             emit(2u, 1u);
             i--;
             state_ = (nib & 8u) ? 2 : 0;
         } else {
             if (i < 1 || j < 1) { bad = true; break; }
-            const uint32_t nib = nibble_at(arena, off, L, K, pad, i, j);
+            const uint32_t nib = nib_at(i, j, &bad);
+            if (bad) break;
             emit(1u, 1u);
             j--;
             state_ = (nib & 4u) ? 1 : 0;
@@ -456,17 +515,17 @@ __global__ void k_traceback(const sa_job* __restrict__ jobs, uint32_t job_begin,
     if (cur_len) ops[nrev++] = (cur_len << 4) | cur_op;
     out.n_rev = nrev;
     out.read_begin = j;
-    out.ref_begin_rel = (R.i_lo - 1) + i;
+    out.ref_begin_rel = banded ? i : (R.i_lo - 1) + i;
     tb[job] = out;
 }
 
 void launch_traceback(const sa_job* jobs, uint32_t job_begin, uint32_t n_jobs, const JobState* state,
-                      const Rect* rect, const uint32_t* arena, int wave, int mode, int plain,
-                      int cfg_force, int32_t min_score, uint32_t* tmp_ops, uint32_t tmp_stride,
-                      TbOut* tb, unsigned* err_job, cudaStream_t st) {
+                      const Rect* rect, const uint32_t* arena, const BandLayout& band, int wave,
+                      int mode, int plain, int cfg_force, int32_t min_score, uint32_t* tmp_ops,
+                      uint32_t tmp_stride, TbOut* tb, unsigned* err_job, cudaStream_t st) {
     if (!n_jobs) return;
     k_traceback<<<(n_jobs + 127) / 128, 128, 0, st>>>(jobs, job_begin, n_jobs, state, rect, arena,
-                                                       wave, mode, plain, cfg_force, min_score,
+                                                       band, wave, mode, plain, cfg_force, min_score,
                                                        tmp_ops, tmp_stride, tb, err_job);
 }
 
@@ -494,6 +553,10 @@ __global__ void k_plain_rect(const sa_job* __restrict__ jobs, uint32_t j0, uint3
     R.start_i = 0;
     R.start_j = 0;
     R.wave = 0;
+    R.cls = kClsRect;
+    R.d_lo = 0;
+    R.lpos = 0;
+    R._pad = 0;
     rect[j0 + k] = R;
 }
 
