@@ -49,7 +49,9 @@ class sa_stats(ctypes.Structure):
                 ("fill_launches", ctypes.c_uint32), ("kernel_launches", ctypes.c_uint32),
                 ("ms_stage", ctypes.c_float), ("ms_fill", ctypes.c_float), ("ms_rerun", ctypes.c_float),
                 ("ms_rect", ctypes.c_float), ("ms_traceback", ctypes.c_float),
-                ("ms_finalize", ctypes.c_float), ("ms_total", ctypes.c_float)]
+                ("ms_finalize", ctypes.c_float), ("ms_total", ctypes.c_float),
+                ("band16_jobs", ctypes.c_uint32), ("band_wide_jobs", ctypes.c_uint32),
+                ("rect_jobs", ctypes.c_uint32), ("_pad", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -90,21 +90,21 @@ struct PlanBlock {
     uint32_t cfg_begin[kNumCfg + 1];
     uint32_t _pad;
     uint64_t totals[4];
-    uint32_t cls_count[4];         // direction-pass classes (none, band 16, band 32, rectangle)
+    uint32_t cls_count[5];         // direction-pass classes (none, band 16, band 32, rectangle, band 64)
 };
 
 // Device buffers of one computation at a time (grown on demand, reused).
 struct Workspace {
     DevBuf jobs, reads, out, cigar;          // inputs/outputs of the host-buffer entry points
     DevBuf key, order, rpack, state, rect, tb, count, coff, sizes, offs, bsum;
-    DevBuf colbest, tmp_ops, arena, plan, counters, list16, list32, band;
+    DevBuf colbest, tmp_ops, arena, plan, counters, list16, list32, list64, band;
     PlanBlock* h_plan = nullptr;             // pinned mirror of the plan block
     cudaEvent_t ev[16] = {};
     bool ev_ok = false;
     void release() {
         DevBuf* all[] = {&jobs, &reads, &out, &cigar, &key, &order, &rpack, &state, &rect, &tb,
                          &count, &coff, &sizes, &offs, &bsum, &colbest, &tmp_ops, &arena,
-                         &plan, &counters, &list16, &list32, &band};
+                         &plan, &counters, &list16, &list32, &list64, &band};
         for (DevBuf* b : all) b->release();
         if (h_plan) cudaFreeHost(h_plan);
         h_plan = nullptr;
@@ -369,9 +369,12 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             // wavefront rectangle pass (in arena waves) for wide bands, then the walk
             TRY(ws.list16.ensure((size_t)n_jobs * 4, "band lists"));
             TRY(ws.list32.ensure((size_t)n_jobs * 4, "band lists"));
+            TRY(ws.list64.ensure((size_t)n_jobs * 4, "band lists"));
+            uint32_t* lists[kNumBand] = {ws.list16.as<uint32_t>(), ws.list32.as<uint32_t>(),
+                                         ws.list64.as<uint32_t>()};
             launch_rect_plan(d_jobs, ws.order.as<uint32_t>(), n_jobs, ws.state.as<JobState>(), sc,
-                             min_score, 1, ws.rect.as<Rect>(), ws.sizes.as<uint64_t>(),
-                             ws.list16.as<uint32_t>(), ws.list32.as<uint32_t>(), dp->cls_count, st);
+                             min_score, 1, ws.rect.as<Rect>(), ws.sizes.as<uint64_t>(), lists,
+                             dp->cls_count, st);
             launch_scan_u64(ws.sizes.as<uint64_t>(), n_jobs, ws.offs.as<uint64_t>(),
                             ws.bsum.as<uint64_t>(), &dp->totals[0], st);
             launches += 4;
@@ -381,18 +384,22 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             CU(cudaMemcpyAsync(hp->cls_count, dp->cls_count, sizeof(hp->cls_count), cudaMemcpyDeviceToHost, st));
             TRY(check_bad_read(dp, hp, st));
             const uint64_t total_words = hp->totals[0];
-            const uint32_t n16 = hp->cls_count[kClsBand16], n32 = hp->cls_count[kClsBand32];
+            uint32_t nb[kNumBand];
+            for (int k = 0; k < kNumBand; k++) nb[k] = hp->cls_count[band_cls(k)];
+            stats.band16_jobs = nb[0];
+            stats.band_wide_jobs = nb[1] + nb[2];
+            stats.rect_jobs = hp->cls_count[kClsRect];
             // band regions: 32 jobs of a class share a region of max_n rows x B/8 words x 32 lanes
             BandLayout bl{};
-            bl.warp_stride[0] = (uint64_t)max_n * 2 * 32;
-            bl.warp_stride[1] = (uint64_t)max_n * 4 * 32;
-            bl.base[0] = 0;
-            bl.base[1] = (uint64_t)((n16 + 31) / 32) * bl.warp_stride[0];
-            const uint64_t band_words = bl.base[1] + (uint64_t)((n32 + 31) / 32) * bl.warp_stride[1];
+            uint64_t band_words = 0;
+            for (int k = 0; k < kNumBand; k++) {
+                bl.warp_stride[k] = (uint64_t)max_n * (band_width_of(k) / 8) * 32;
+                bl.base[k] = band_words;
+                band_words += (uint64_t)((nb[k] + 31) / 32) * bl.warp_stride[k];
+            }
             TRY(ws.band.ensure(std::max<uint64_t>(band_words, 1) * 4, "band arena"));
             bl.arena = ws.band.as<uint32_t>();
-
-            for (int k = 0; k < 2; k++) {
+            for (int k = 0; k < kNumBand; k++) {
                 BandArgs ba{};
                 ba.ref = X.d_words;
                 ba.ref_len = (int64_t)X.len;
@@ -400,13 +407,13 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
                 ba.rpack = ws.rpack.as<uint32_t>();
                 ba.rw = rw;
                 ba.rect = ws.rect.as<Rect>();
-                ba.list = k == 0 ? ws.list16.as<uint32_t>() : ws.list32.as<uint32_t>();
-                ba.count = k == 0 ? n16 : n32;
+                ba.list = lists[k];
+                ba.count = nb[k];
                 ba.arena = ws.band.as<uint32_t>() + bl.base[k];
                 ba.warp_stride = bl.warp_stride[k];
                 ba.sc = sc;
                 if (ba.count) {
-                    launch_band(k == 0 ? kClsBand16 : kClsBand32, ba, st);
+                    launch_band(band_cls(k), ba, st);
                     launches++;
                 }
             }

@@ -28,7 +28,7 @@ template <int B, int MODE>
 __global__ void __launch_bounds__(128) k_band(BandArgs A) {
     constexpr bool LOCAL = (MODE == SA_LOCAL);
     constexpr int W = B / 8;
-    static_assert(B == 16 || B == 32, "band widths 16 and 32");
+    static_assert(B == 16 || B == 32 || B == 64, "band widths 16, 32 and 64");
     const uint32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
     if (pos >= A.count) return;
     const uint32_t job = A.list[pos];
@@ -49,21 +49,27 @@ __global__ void __launch_bounds__(128) k_band(BandArgs A) {
     }
     for (int j = 1; j <= rows; j++) {
         const int i0 = j + dlo;               // window column of slot 0
-        // window bases of slots 0..B-1 (reference positions ref_pos + i0 - 1 + k);
-        // positions before the window start only feed masked slots
-        const int64_t p0 = (int64_t)J.ref_pos + i0 - 1;
-        int64_t q0 = p0 < (int64_t)J.ref_pos ? (int64_t)J.ref_pos : p0;
-        if (q0 > A.ref_len) q0 = A.ref_len;
-        const int64_t wi = q0 >> 4;
-        const uint32_t sh = (uint32_t)(q0 & 15) * 2u;
-        const uint64_t lo = ((uint64_t)__ldg(refw + wi + 1) << 32) | (uint64_t)__ldg(refw + wi);
-        const uint64_t hi = (uint64_t)__ldg(refw + wi + 2);
-        uint64_t wb = sh ? ((lo >> sh) | (hi << (64 - sh))) : lo;
-        const int64_t lead = q0 - p0;         // slots before the clamped start
-        wb = lead >= 32 ? 0ull : (wb << (2 * lead));
+        // match bits of slots 0..B-1 against read base j: window bases at reference
+        // positions ref_pos + i0 - 1 + k, 32 slots per 64-bit half; positions before
+        // the window start only feed masked slots (column <= 0)
         const uint64_t rb = (uint64_t)((__ldg(rp + ((j - 1) >> 4)) >> (2 * ((j - 1) & 15))) & 3u);
-        const uint64_t x = wb ^ (rb * 0x5555555555555555ull);
-        const uint64_t mm = ~(x | (x >> 1)) & 0x5555555555555555ull;   // bit 2k: slot k matches
+        constexpr int NH = B > 32 ? 2 : 1;
+        uint64_t mmh[NH];
+#pragma unroll
+        for (int hh = 0; hh < NH; hh++) {
+            const int64_t ph = (int64_t)J.ref_pos + i0 - 1 + 32 * hh;
+            int64_t qh = ph < (int64_t)J.ref_pos ? (int64_t)J.ref_pos : ph;
+            if (qh > A.ref_len) qh = A.ref_len;
+            const int64_t wi = qh >> 4;
+            const uint32_t sh = (uint32_t)(qh & 15) * 2u;
+            const uint64_t lo = ((uint64_t)__ldg(refw + wi + 1) << 32) | (uint64_t)__ldg(refw + wi);
+            const uint64_t hi = (uint64_t)__ldg(refw + wi + 2);
+            uint64_t wb = sh ? ((lo >> sh) | (hi << (64 - sh))) : lo;
+            const int64_t lead = qh - ph;     // >= 0
+            wb = lead >= 32 ? 0ull : (wb << (2 * lead));
+            const uint64_t x = wb ^ (rb * 0x5555555555555555ull);
+            mmh[hh] = ~(x | (x >> 1)) & 0x5555555555555555ull;   // bit 2k: slot 32hh+k matches
+        }
         const int32_t border = (!LOCAL) ? S.GO + (j - 1) * S.GE : 0;  // H(0, j)
         const bool edge = i0 < 1;
         int32_t hleft = kNeg32, fleft = kNeg32;
@@ -87,7 +93,7 @@ __global__ void __launch_bounds__(128) k_band(BandArgs A) {
                 const int32_t fe = fleft + S.GE, fo = hleft + S.GO;
                 const bool fopen = fo >= fe;
                 fn = fopen ? fo : fe;
-                const int32_t g = diag + (((mm >> (2 * k)) & 1ull) ? S.a : S.b);
+                const int32_t g = diag + (((mmh[k >> 5] >> (2 * (k & 31))) & 1ull) ? S.a : S.b);
                 const bool pF = fn >= en;
                 const int32_t ef = pF ? fn : en;
                 const bool pG = g >= ef;
@@ -116,8 +122,10 @@ void launch_band(int cls, const BandArgs& a, cudaStream_t st) {
     const bool local = a.sc.mode == SA_LOCAL;
     if (cls == kClsBand16) {
         local ? k_band<16, SA_LOCAL><<<grid, 128, 0, st>>>(a) : k_band<16, SA_GLOCAL><<<grid, 128, 0, st>>>(a);
-    } else {
+    } else if (cls == kClsBand32) {
         local ? k_band<32, SA_LOCAL><<<grid, 128, 0, st>>>(a) : k_band<32, SA_GLOCAL><<<grid, 128, 0, st>>>(a);
+    } else {
+        local ? k_band<64, SA_LOCAL><<<grid, 128, 0, st>>>(a) : k_band<64, SA_GLOCAL><<<grid, 128, 0, st>>>(a);
     }
 }
 

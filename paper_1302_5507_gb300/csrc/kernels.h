@@ -31,8 +31,8 @@ struct BandArgs {                  // banded direction pass of one class
 
 struct BandLayout {                // where the traceback finds band nibbles
     const uint32_t* arena;
-    uint64_t base[2];              // word offset of the class 16 / class 32 regions
-    uint64_t warp_stride[2];
+    uint64_t base[kNumBand];       // word offset of the band 16 / 32 / 64 regions
+    uint64_t warp_stride[kNumBand];
 };
 
 struct TbOut {                     // traceback result of one job
@@ -51,8 +51,8 @@ void launch_pack_reads(const sa_job* jobs, uint32_t n_jobs, const uint8_t* reads
                        uint32_t rw, unsigned* bad_job, cudaStream_t st);
 void launch_rect_plan(const sa_job* jobs, const uint32_t* order, uint32_t n_pos,
                       const JobState* state, const Score& sc, int32_t min_score, int allow_band,
-                      Rect* rect, uint64_t* sizes, uint32_t* list16, uint32_t* list32,
-                      uint32_t* cls_count, cudaStream_t st);
+                      Rect* rect, uint64_t* sizes, uint32_t* const* lists, uint32_t* cls_count,
+                      cudaStream_t st);
 void launch_band(int cls, const BandArgs& a, cudaStream_t st);
 void launch_rect_assign(const uint32_t* order, uint32_t n_pos, const uint64_t* offs,
                         const uint32_t* cfg_begin, uint64_t wave_words, Rect* rect,

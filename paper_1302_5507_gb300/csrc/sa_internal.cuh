@@ -94,12 +94,16 @@ struct Rect {
     int32_t start_j;
     int32_t wave;
     // banded form (cls 1, 2): diagonals d = i - j in [d_lo, d_lo + band width)
-    int32_t cls;        // 0 none, 1 band of 16, 2 band of 32, 3 wavefront rectangle
+    int32_t cls;        // 0 none, 1/2/4 band of 16/32/64, 3 wavefront rectangle
     int32_t d_lo;
     uint32_t lpos;      // position in its class list
     int32_t _pad;
 };
-enum { kClsNone = 0, kClsBand16 = 1, kClsBand32 = 2, kClsRect = 3 };
+enum { kClsNone = 0, kClsBand16 = 1, kClsBand32 = 2, kClsRect = 3, kClsBand64 = 4 };
+constexpr int kNumBand = 3;                       // band classes 16, 32, 64
+__host__ __device__ inline int band_cls(int b) { return b == 0 ? kClsBand16 : (b == 1 ? kClsBand32 : kClsBand64); }
+__host__ __device__ inline int band_index(int cls) { return cls == kClsBand16 ? 0 : (cls == kClsBand32 ? 1 : (cls == kClsBand64 ? 2 : -1)); }
+__host__ __device__ inline int band_width_of(int b) { return 16 << b; }
 
 // Arguments of the wavefront kernels.
 struct FillArgs {

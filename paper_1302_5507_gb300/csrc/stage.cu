@@ -173,6 +173,8 @@ void launch_pack_reads(const sa_job* jobs, uint32_t n_jobs, const uint8_t* reads
                                                                       bad_job);
 }
 
+struct BandLists { uint32_t* p[kNumBand]; };
+
 // ---------------------------------------------------------------------------
 // reduced traceback rectangle.
 //
@@ -188,8 +190,7 @@ void launch_pack_reads(const sa_job* jobs, uint32_t n_jobs, const uint8_t* reads
 __global__ void k_rect_plan(const sa_job* __restrict__ jobs, const uint32_t* __restrict__ order,
                             uint32_t n_pos, const JobState* __restrict__ state, Score sc,
                             int32_t min_score, int allow_band, Rect* __restrict__ rect,
-                            uint64_t* __restrict__ sizes, uint32_t* __restrict__ list16,
-                            uint32_t* __restrict__ list32, uint32_t* cls_count) {
+                            uint64_t* __restrict__ sizes, BandLists lists, uint32_t* cls_count) {
     // no early return: the class lists are appended with warp-wide ballots
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = p < n_pos;
@@ -221,7 +222,9 @@ __global__ void k_rect_plan(const sa_job* __restrict__ jobs, const uint32_t* __r
                 const int64_t dmax = slack / e, imax = slack / (sc.a + e);
                 const int64_t width = dmax + imax + 1;
                 R.d_lo = (int)((int64_t)(istar - jstar) - dmax);
-                if (allow_band) R.cls = width <= 16 ? kClsBand16 : (width <= 32 ? kClsBand32 : kClsRect);
+                if (allow_band)
+                    R.cls = width <= 16 ? kClsBand16
+                          : (width <= 32 ? kClsBand32 : (width <= 64 ? kClsBand64 : kClsRect));
                 span = (int64_t)jstar + dmax;
             }
             R.rows = jstar;
@@ -237,8 +240,8 @@ __global__ void k_rect_plan(const sa_job* __restrict__ jobs, const uint32_t* __r
     }
     const unsigned lane = threadIdx.x & 31u;
 #pragma unroll
-    for (int k = 0; k < 2; k++) {
-        const int cls = k == 0 ? kClsBand16 : kClsBand32;
+    for (int k = 0; k < kNumBand; k++) {
+        const int cls = band_cls(k);
         const unsigned mask = __ballot_sync(0xffffffffu, valid && R.cls == cls);
         if (mask) {
             const int leader = __ffs(mask) - 1;
@@ -247,9 +250,13 @@ __global__ void k_rect_plan(const sa_job* __restrict__ jobs, const uint32_t* __r
             base = __shfl_sync(0xffffffffu, base, leader);
             if (valid && R.cls == cls) {
                 R.lpos = base + (uint32_t)__popc(mask & ((1u << lane) - 1u));
-                (k == 0 ? list16 : list32)[R.lpos] = job;
+                lists.p[k][R.lpos] = job;
             }
         }
+    }
+    {
+        const unsigned mask = __ballot_sync(0xffffffffu, valid && R.cls == kClsRect);
+        if (mask && (int)lane == __ffs(mask) - 1) atomicAdd(&cls_count[kClsRect], (uint32_t)__popc(mask));
     }
     if (valid) {
         rect[job] = R;
@@ -259,12 +266,13 @@ __global__ void k_rect_plan(const sa_job* __restrict__ jobs, const uint32_t* __r
 
 void launch_rect_plan(const sa_job* jobs, const uint32_t* order, uint32_t n_pos,
                       const JobState* state, const Score& sc, int32_t min_score, int allow_band,
-                      Rect* rect, uint64_t* sizes, uint32_t* list16, uint32_t* list32,
-                      uint32_t* cls_count, cudaStream_t st) {
+                      Rect* rect, uint64_t* sizes, uint32_t* const* lists, uint32_t* cls_count,
+                      cudaStream_t st) {
     if (!n_pos) return;
+    BandLists bl;
+    for (int k = 0; k < kNumBand; k++) bl.p[k] = lists[k];
     k_rect_plan<<<(n_pos + 255) / 256, 256, 0, st>>>(jobs, order, n_pos, state, sc, min_score,
-                                                      allow_band, rect, sizes, list16, list32,
-                                                      cls_count);
+                                                      allow_band, rect, sizes, bl, cls_count);
 }
 
 // wave assignment: an item (the G jobs a warp takes at once) belongs to the wave
@@ -422,7 +430,8 @@ __global__ void k_traceback(const sa_job* __restrict__ jobs, uint32_t job_begin,
     if (tid >= n_jobs) return;
     const uint32_t job = job_begin + tid;
     const Rect R = rect[job];
-    const bool banded = R.cls == kClsBand16 || R.cls == kClsBand32;
+    const int bidx = band_index(R.cls);
+    const bool banded = bidx >= 0;
     if (banded ? wave != 0 : (R.w <= 0 || R.wave != wave)) return;
     const sa_job J = jobs[job];
     const JobState st = state[job];
@@ -443,9 +452,8 @@ __global__ void k_traceback(const sa_job* __restrict__ jobs, uint32_t job_begin,
     // banded jobs walk in window coordinates (start at the best cell, border at
     // column 0); rectangle jobs in rectangle coordinates (border at column 0 of
     // the rectangle, window column i_lo - 1)
-    const int bw = R.cls == kClsBand16 ? 16 : 32;
-    const int bc = R.cls == kClsBand16 ? 0 : 1;
-    const uint64_t bbase = banded ? band.base[bc] + (uint64_t)(R.lpos >> 5) * band.warp_stride[bc] + (R.lpos & 31u) : 0;
+    const int bw = banded ? band_width_of(bidx) : 0;
+    const uint64_t bbase = banded ? band.base[bidx] + (uint64_t)(R.lpos >> 5) * band.warp_stride[bidx] + (R.lpos & 31u) : 0;
     if (banded) {
         si = st.i_star;
         sj = st.j_star;

@@ -208,3 +208,14 @@ def test_full_size_mate_rescue_sampled(sa):
     assert not bad, "\n".join(bad)
     # the CIGAR buffer is compact and in job order
     assert (np.diff(res["cigar_off"].astype(np.int64)) == res["cigar_len"][:-1]).all()
+
+
+def test_every_direction_pass_class_is_exercised(sa):
+    """The low-similarity sweep puts traced jobs in the band-16, wider band and
+    whole-rectangle direction passes; all three must match the oracle."""
+    wl = workloads.lowsim(seed=2, n_jobs=1_200)
+    with sa.Reference(wl.ref) as ref:
+        assert_parity(sa, ref, wl)
+        st = ref.stats()
+        assert st["band16_jobs"] > 0 and st["band_wide_jobs"] > 0 and st["rect_jobs"] > 0, st
+        assert_parity(sa, ref, wl, mode=1)
