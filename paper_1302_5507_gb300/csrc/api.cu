@@ -91,20 +91,21 @@ struct PlanBlock {
     uint32_t _pad;
     uint64_t totals[4];
     uint32_t cls_count[5];         // direction-pass classes (none, band 16, band 32, rectangle, band 64)
+    uint32_t ovf_count[kNumCfg];   // jobs the 16-bit pass sent to the 32-bit rerun, per bucket
 };
 
 // Device buffers of one computation at a time (grown on demand, reused).
 struct Workspace {
     DevBuf jobs, reads, out, cigar;          // inputs/outputs of the host-buffer entry points
     DevBuf key, order, rpack, state, rect, tb, count, coff, sizes, offs, bsum;
-    DevBuf colbest, tmp_ops, arena, plan, counters, list16, list32, list64, band;
+    DevBuf colbest, tmp_ops, arena, plan, counters, list16, list32, list64, band, ovf;
     PlanBlock* h_plan = nullptr;             // pinned mirror of the plan block
     cudaEvent_t ev[16] = {};
     bool ev_ok = false;
     void release() {
         DevBuf* all[] = {&jobs, &reads, &out, &cigar, &key, &order, &rpack, &state, &rect, &tb,
                          &count, &coff, &sizes, &offs, &bsum, &colbest, &tmp_ops, &arena,
-                         &plan, &counters, &list16, &list32, &list64, &band};
+                         &plan, &counters, &list16, &list32, &list64, &band, &ovf};
         for (DevBuf* b : all) b->release();
         if (h_plan) cudaFreeHost(h_plan);
         h_plan = nullptr;
@@ -160,6 +161,17 @@ int check_params(const sa_params* p, Score* sc) {
     sc->dx = sc->b - sc->GO;
     sc->mode = p->mode;
     return SA_OK;
+}
+
+// The 16-bit packed score pass is exact for LOCAL alignment when every value the
+// recurrence forms stays inside the biased 16-bit range (see fill16.cuh): match
+// <= 8191 (a positive overflow threshold), mismatch and gap open + 2 x extend
+// <= 16383.  Larger values are handled by overflow detection and the 32-bit
+// rerun only on the upper side, so they need the 32-bit path from the start.
+bool use16(const sa_params* P) {
+    if (P->mode != SA_LOCAL || P->width == 32 || P->form == SA_FORM_PLAIN) return false;
+    const sa_scoring& s = P->sc;
+    return s.match <= 8191 && s.mismatch <= 16383 && (int64_t)s.gap_open + 2 * (int64_t)s.gap_extend <= 16383;
 }
 
 int ensure_events(Workspace& ws) {
@@ -299,12 +311,15 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
         if (bps < 1) bps = 1;
         return X.num_sms * bps;
     };
+    const bool w16 = use16(P);
     int max_groups = 1;
     for (int c = 0; c < kNumCfg; c++) {
         if (plain ? c != plain_cfg : !cfg_count[c]) continue;
-        const int kind = plain ? (int)kFillPlain : (int)kFillScore;
-        const int groups = grid_for(c, kind) * (kBlock / 32) * (32 / cfg_L(c));
-        max_groups = std::max(max_groups, groups);
+        const int kinds[2] = {plain ? (int)kFillPlain : (int)kFillScore, w16 ? (int)kFillScore16 : (int)kFillScore};
+        for (int kind : kinds) {
+            const int groups = grid_for(c, kind) * (kBlock / 32) * (32 / cfg_L(c));
+            max_groups = std::max(max_groups, groups);
+        }
     }
     TRY(ws.colbest.ensure((size_t)max_groups * max_m * 4, "column maxima"));
 
@@ -340,9 +355,11 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
     uint32_t* counters = ws.counters.as<uint32_t>();
     auto next_counter = [&]() { return counters + (counter_next++ % 256); };
 
-    int tfill1 = -1, trect1 = -1, ttb1 = -1;
+    int tfill1 = -1, tfill16 = -1, trect1 = -1, ttb1 = -1;
     if (!plain) {
-        // --- score pass: one persistent launch per non-empty length bucket
+        // --- score pass: one persistent launch per non-empty length bucket; in
+        // 16-bit pairs when exact (LOCAL, scores in range), then a 32-bit rerun of
+        // the jobs whose maximum reached the 16-bit overflow threshold
         for (int c = 0; c < kNumCfg; c++) {
             if (!cfg_count[c]) continue;
             FillLaunch fl{};
@@ -350,11 +367,11 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             fl.args.pos_begin = cfg_begin[c];
             fl.args.pos_count = cfg_count[c];
             fl.args.item_counter = next_counter();
-            fl.kind = kFillScore;
+            fl.kind = w16 ? kFillScore16 : kFillScore;
             fl.block = kBlock;
-            const uint32_t G = 32 / cfg_L(c);
-            const uint64_t warps_needed = (cfg_count[c] + G - 1) / G;
-            fl.grid = (int)std::min<uint64_t>(grid_for(c, kFillScore), (warps_needed + 3) / 4);
+            const uint32_t per_warp = (32 / cfg_L(c)) * (w16 ? 2 : 1);
+            const uint64_t warps_needed = (cfg_count[c] + per_warp - 1) / per_warp;
+            fl.grid = (int)std::min<uint64_t>(grid_for(c, fl.kind), (warps_needed + 3) / 4);
             fl.stream = st;
             launch_fill_cfg(c, fl);
             stats.fill_launches++;
@@ -362,6 +379,33 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             if (trace.on) { char b[64]; snprintf(b, sizeof b, "score pass cfg %d (%u jobs)", c, cfg_count[c]); trace(b); }
         }
         CU(cudaGetLastError());
+        if (w16) {
+            tfill16 = tm.mark();
+            TRY(ws.ovf.ensure((size_t)n_jobs * 4, "overflow list"));
+            launch_collect_overflow(ws.order.as<uint32_t>(), n_jobs, ws.state.as<JobState>(), dp->cfg_begin,
+                                    ws.ovf.as<uint32_t>(), dp->ovf_count, st);
+            launches++;
+            for (int c = 0; c < kNumCfg; c++) {
+                if (!cfg_count[c]) continue;
+                FillLaunch fl{};
+                fl.args = base;
+                fl.args.order = ws.ovf.as<uint32_t>();
+                fl.args.pos_begin = cfg_begin[c];
+                fl.args.pos_count = 0;
+                fl.args.count_ptr = &dp->ovf_count[c];
+                fl.args.item_counter = next_counter();
+                fl.kind = kFillScore;
+                fl.block = kBlock;
+                const uint32_t G = 32 / cfg_L(c);
+                const uint64_t warps_needed = (cfg_count[c] + G - 1) / G;
+                fl.grid = (int)std::min<uint64_t>(grid_for(c, kFillScore), (warps_needed + 3) / 4);
+                fl.stream = st;
+                launch_fill_cfg(c, fl);
+                launches++;
+            }
+            CU(cudaGetLastError());
+            trace("overflow rerun");
+        }
         tfill1 = tm.mark();
 
         if (want_cigar) {
@@ -382,6 +426,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             trace("rect plan + scan");
             CU(cudaMemcpyAsync(&hp->totals[0], &dp->totals[0], 8, cudaMemcpyDeviceToHost, st));
             CU(cudaMemcpyAsync(hp->cls_count, dp->cls_count, sizeof(hp->cls_count), cudaMemcpyDeviceToHost, st));
+            CU(cudaMemcpyAsync(hp->ovf_count, dp->ovf_count, sizeof(hp->ovf_count), cudaMemcpyDeviceToHost, st));
             TRY(check_bad_read(dp, hp, st));
             const uint64_t total_words = hp->totals[0];
             uint32_t nb[kNumBand];
@@ -389,6 +434,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             stats.band16_jobs = nb[0];
             stats.band_wide_jobs = nb[1] + nb[2];
             stats.rect_jobs = hp->cls_count[kClsRect];
+            for (int c = 0; c < kNumCfg; c++) stats.overflow_reruns += w16 ? hp->ovf_count[c] : 0u;
             // band regions: 32 jobs of a class share a region of max_n rows x B/8 words x 32 lanes
             BandLayout bl{};
             uint64_t band_words = 0;
@@ -470,7 +516,9 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             }
             ttb1 = tm.mark();
         } else {
+            CU(cudaMemcpyAsync(hp->ovf_count, dp->ovf_count, sizeof(hp->ovf_count), cudaMemcpyDeviceToHost, st));
             TRY(check_bad_read(dp, hp, st));
+            for (int c = 0; c < kNumCfg; c++) stats.overflow_reruns += w16 ? hp->ovf_count[c] : 0u;
         }
     } else {
         // --- plain form: fixed-size batches in job order, one configuration for the
@@ -551,7 +599,8 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
     stats.kernel_launches = launches;
     if (P->profile) {
         stats.ms_stage = tm.ms(t0, t1);
-        stats.ms_fill = tm.ms(t1, tfill1);
+        stats.ms_fill = tm.ms(t1, tfill16 >= 0 ? tfill16 : tfill1);
+        stats.ms_rerun = tfill16 >= 0 ? tm.ms(tfill16, tfill1) : 0.f;
         stats.ms_rect = tm.ms(tfill1, trect1);   // rectangle planning + direction pass
         stats.ms_traceback = tm.ms(trect1, ttb1);
         stats.ms_finalize = tm.ms(tfin0, tfin1);

@@ -114,18 +114,27 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
         // match masks: bit r of mX is set when the lane's row r holds base X
         uint32_t mA = 0, mC = 0, mG = 0, mT = 0;
         if (PROF) {
-            // profile: word ((t*K4 + r/4)*32 + lane)*4 + r%4 holds the diagonal term of
-            // row r against window base t (rows that are padding never match)
+            // profile: int4 ((t*K4 + r/4)*32 + lane) holds the diagonal terms of rows
+            // r..r+3 against window base t (rows that are padding never match);
+            // written and read as int4, so later reads cannot move above these stores
             const uint32_t* rp = A.rpack + (size_t)job * A.rw;
+            int4* prof4 = reinterpret_cast<int4*>(prof);
 #pragma unroll
-            for (int r = 0; r < 4 * K4; r++) {
-                const int j = g * K + r + 1 - pad;
-                int code = -1;
-                if (r < K && w > 0 && j >= 1 && j <= rows)
-                    code = (int)((__ldg(rp + ((j - 1) >> 4)) >> (2 * ((j - 1) & 15))) & 3u);
+            for (int q = 0; q < K4; q++) {
+                int code[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int r = 4 * q + u;
+                    const int j = g * K + r + 1 - pad;
+                    code[u] = -1;
+                    if (r < K && w > 0 && j >= 1 && j <= rows)
+                        code[u] = (int)((__ldg(rp + ((j - 1) >> 4)) >> (2 * ((j - 1) & 15))) & 3u);
+                }
 #pragma unroll
                 for (int t = 0; t < 4; t++)
-                    prof[((t * K4 + r / 4) * 32 + lane) * 4 + (r & 3)] = code == t ? S.dm : S.dx;
+                    prof4[(t * K4 + q) * 32 + lane] =
+                        make_int4(code[0] == t ? S.dm : S.dx, code[1] == t ? S.dm : S.dx,
+                                  code[2] == t ? S.dm : S.dx, code[3] == t ? S.dm : S.dx);
             }
         } else {
             const uint32_t* rp = A.rpack + (size_t)job * A.rw;

@@ -1,6 +1,6 @@
 // One configuration's wavefront kernels (compiled once per configuration with
 // -DSA_CFG=<index>, so the translation units build in parallel).
-#include "fill.cuh"
+#include "fill16.cuh"
 #include "kernels.h"
 
 #ifndef SA_CFG
@@ -33,6 +33,17 @@ void launch_one(const FillLaunch& fl) {
     k_fill32<kL, kK, MODE, DIR, BEST><<<fl.grid, fl.block, smem_bytes<DIR, BEST>(), fl.stream>>>(fl.args);
 }
 
+constexpr size_t smem16_bytes() { return 4 * prof16_words_per_warp<kK>() * sizeof(int32_t); }
+
+void prepare16() {
+    static bool done = false;
+    if (!done) {
+        cudaFuncSetAttribute(k_fill16<kL, kK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem16_bytes());
+        done = true;
+    }
+}
+
 template <int MODE, bool DIR, bool BEST>
 int blocks_per_sm() {
     prepare<MODE, DIR, BEST>();
@@ -56,6 +67,10 @@ void launch_fill<SA_CFG>(const FillLaunch& fl) {
     case kFillPlain:
         local ? launch_one<SA_LOCAL, true, true>(fl) : launch_one<SA_GLOCAL, true, true>(fl);
         break;
+    case kFillScore16:
+        prepare16();
+        k_fill16<kL, kK><<<fl.grid, fl.block, smem16_bytes(), fl.stream>>>(fl.args);
+        break;
     default:
         break;
     }
@@ -71,6 +86,12 @@ int fill_blocks_per_sm<SA_CFG>(int kind, int mode) {
         return local ? blocks_per_sm<SA_LOCAL, true, false>() : blocks_per_sm<SA_GLOCAL, true, false>();
     case kFillPlain:
         return local ? blocks_per_sm<SA_LOCAL, true, true>() : blocks_per_sm<SA_GLOCAL, true, true>();
+    case kFillScore16: {
+        prepare16();
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fill16<kL, kK>, 128, smem16_bytes());
+        return nb;
+    }
     }
     return 0;
 }

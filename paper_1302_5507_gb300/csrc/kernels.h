@@ -47,6 +47,9 @@ void launch_plan(const sa_job* jobs, uint32_t n_jobs, uint64_t reads_len, int64_
                  uint16_t* key, uint32_t* hist, PlanStats* stats, cudaStream_t st);
 void launch_plan_order(const uint16_t* key, uint32_t n_jobs, const uint32_t* hist,
                        uint32_t* key_off, uint32_t* cursor, uint32_t* order, cudaStream_t st);
+void launch_collect_overflow(const uint32_t* order, uint32_t n_pos, const JobState* state,
+                             const uint32_t* cfg_begin, uint32_t* list, uint32_t* cnt,
+                             cudaStream_t st);
 void launch_pack_reads(const sa_job* jobs, uint32_t n_jobs, const uint8_t* reads, uint32_t* rpack,
                        uint32_t rw, unsigned* bad_job, cudaStream_t st);
 void launch_rect_plan(const sa_job* jobs, const uint32_t* order, uint32_t n_pos,

@@ -136,6 +136,30 @@ void launch_plan_order(const uint16_t* key, uint32_t n_jobs, const uint32_t* his
 }
 
 // ---------------------------------------------------------------------------
+// jobs the 16-bit pass flagged: per length bucket, compacted into that bucket's
+// range of `list` (list[cfg_begin[c] + k]), counts in cnt[c]
+
+__global__ void k_collect_overflow(const uint32_t* __restrict__ order, uint32_t n_pos,
+                                   const JobState* __restrict__ state,
+                                   const uint32_t* __restrict__ cfg_begin, uint32_t* __restrict__ list,
+                                   uint32_t* __restrict__ cnt) {
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_pos) return;
+    const uint32_t job = order[p];
+    if (!(state[job].flags & kStOverflow)) return;
+    int c = 0;
+    while (c + 1 < kNumCfg && cfg_begin[c + 1] <= p) c++;
+    list[cfg_begin[c] + atomicAdd(&cnt[c], 1u)] = job;
+}
+
+void launch_collect_overflow(const uint32_t* order, uint32_t n_pos, const JobState* state,
+                             const uint32_t* cfg_begin, uint32_t* list, uint32_t* cnt,
+                             cudaStream_t st) {
+    if (!n_pos) return;
+    k_collect_overflow<<<(n_pos + 255) / 256, 256, 0, st>>>(order, n_pos, state, cfg_begin, list, cnt);
+}
+
+// ---------------------------------------------------------------------------
 // read packing: one warp per job, one lane per output word
 
 __global__ void k_pack_reads(const sa_job* __restrict__ jobs, uint32_t n_jobs,

@@ -219,3 +219,44 @@ def test_every_direction_pass_class_is_exercised(sa):
         st = ref.stats()
         assert st["band16_jobs"] > 0 and st["band_wide_jobs"] > 0 and st["rect_jobs"] > 0, st
         assert_parity(sa, ref, wl, mode=1)
+
+
+@pytest.mark.parametrize("width", [16, 32])
+def test_width_16_and_32_agree_with_oracle(sa, width):
+    """The 16-bit packed score pass (two jobs per lane group) and the 32-bit one."""
+    wl = workloads.uneven(seed=3, n_jobs=6_000)
+    with sa.Reference(wl.ref) as ref:
+        assert_parity(sa, ref, wl, width=width)
+        assert_parity(sa, ref, wl, width=width, want_cigar=False)
+        assert ref.stats()["overflow_reruns"] == 0
+
+
+def test_overflow_rerun_is_exact(sa):
+    """A large-score scheme pushes long reads past the 16-bit range: those jobs are
+    flagged and recomputed in 32-bit; every result still equals the oracle."""
+    scoring = (200, 150, 300, 40)
+    wl = workloads.uneven(seed=5, n_jobs=3_000)
+    with sa.Reference(wl.ref) as ref:
+        res, ores = assert_parity(sa, ref, wl, scoring=scoring, width=16)
+        st = ref.stats()
+        assert st["overflow_reruns"] > 0
+        # every job whose true best could not be held below the threshold was rerun
+        assert st["overflow_reruns"] >= int((ores["score"] >= 16383 - 200).sum())
+        assert_parity(sa, ref, wl, scoring=scoring, width=16, want_cigar=False)
+
+
+def test_results_do_not_depend_on_pairing_or_run(sa):
+    """The 16-bit pass pairs jobs in an order that varies between runs; every
+    run must give the same (oracle-exact) results."""
+    wl = workloads.small(106, 1500, n_range=(1, 70), m_range=(1, 160), alphabet=4)
+    jobs = sa.jobs_array(wl.read_off, wl.read_len, wl.flags, wl.ref_pos, wl.win_len)
+    ores, oops = oracle.align(wl)
+    with sa.Reference(wl.ref) as ref:
+        first = None
+        for _ in range(4):
+            res, cig = ref.align(jobs, wl.reads, sa.make_params(width=16))
+            bad = compare(res, cig, ores, oops)
+            assert not bad, "\n".join(bad)
+            if first is None:
+                first = (res.copy(), cig.copy())
+            assert (res == first[0]).all() and np.array_equal(cig, first[1])
