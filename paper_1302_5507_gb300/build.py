@@ -20,6 +20,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "libsa.so")
+PROBE = os.path.join(HERE, "libsa_probe.so")   # instruction-throughput probe used by bench.py
 BUILD = os.path.join(HERE, "_build")
 NUM_CFG = 14
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -79,6 +80,10 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
     tmp = OUT + ".tmp"
     subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], check=True, capture_output=True)
     os.replace(tmp, OUT)
+    ptmp = PROBE + ".tmp"
+    subprocess.run([nvcc, *ARCH, *FLAGS, "-shared", "-o", ptmp, os.path.join(CSRC, "dpx_probe.cu")],
+                   check=True, capture_output=True)
+    os.replace(ptmp, PROBE)
     with open(stamp, "w") as f:
         f.write(machine)
     return OUT

@@ -1,0 +1,98 @@
+// Throughput probe of the integer operations the DP cell update uses.
+//
+// Each thread runs kChains independent dependency chains of one operation, so
+// the measurement is bound by the issue rate of that operation's pipe, not by
+// its latency.  The host entry times `iters` rounds with CUDA events and
+// returns lane-operations per SM per clock (ops / (time x SMs x clock)), the
+// number the ALU roofline of the score pass is built from.  Used by bench.py;
+// not part of the alignment interface.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace {
+
+constexpr int kChains = 8;
+
+enum Op {
+    kViaddmaxS32 = 0, kVimax3S32 = 1, kVimax3ReluS32 = 2, kIaddS32 = 3, kImaxS32 = 4, kImadS32 = 5,
+    kViaddmaxS16x2 = 6, kVimax3S16x2 = 7, kPrmt = 8, kNumOps = 9
+};
+
+template <int OP>
+__global__ void __launch_bounds__(256) k_probe(int iters, uint32_t seed, uint32_t* sink) {
+    uint32_t x[kChains], y = seed ^ threadIdx.x, z = seed * 3u + 7u;
+    const uint32_t one = blockDim.x >> 8;          // 1 at run time
+#pragma unroll
+    for (int c = 0; c < kChains; c++) x[c] = seed + c * 977u + threadIdx.x;
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int rep = 0; rep < 16; rep++) {
+#pragma unroll
+            for (int c = 0; c < kChains; c++) {
+                if (OP == kViaddmaxS32) x[c] = (uint32_t)__viaddmax_s32((int)x[c], (int)y, (int)z);
+                if (OP == kVimax3S32) x[c] = (uint32_t)__vimax3_s32((int)x[c], (int)y, (int)(z + c));
+                if (OP == kVimax3ReluS32) x[c] = (uint32_t)__vimax3_s32_relu((int)x[c], (int)y, (int)(z + c));
+                if (OP == kIaddS32) x[c] = x[c] + y;
+                if (OP == kImaxS32) x[c] = (uint32_t)max((int)x[c], (int)(y + c));
+                if (OP == kImadS32) x[c] = x[c] * one + y;
+                if (OP == kViaddmaxS16x2) x[c] = __viaddmax_s16x2(x[c], y, z);
+                if (OP == kVimax3S16x2) x[c] = __vimax3_s16x2(x[c], y, z + c);
+                if (OP == kPrmt) x[c] = __byte_perm(x[c], y, 0x5410 + c);
+            }
+            y += 1;
+        }
+    }
+    uint32_t acc = 0;
+#pragma unroll
+    for (int c = 0; c < kChains; c++) acc ^= x[c];
+    if (acc == 0x9E3779B9u) sink[threadIdx.x] = acc;     // keeps the chains alive
+}
+
+template <int OP>
+float run(int blocks, int iters, uint32_t* sink) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    k_probe<OP><<<blocks, 256>>>(2, 1u, sink);           // warm-up
+    cudaEventRecord(a);
+    k_probe<OP><<<blocks, 256>>>(iters, 1u, sink);
+    cudaEventRecord(b);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return ms;
+}
+
+}  // namespace
+
+// Lane-operations per SM per clock of operation `op` (see Op), measured at the
+// given SM clock (MHz, as sampled by the caller); -1 on error.
+extern "C" double sa_probe_ops_per_sm_clk(int op, double sm_mhz) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1.0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    uint32_t* sink = nullptr;
+    if (cudaMalloc(&sink, 256 * sizeof(uint32_t)) != cudaSuccess) return -1.0;
+    const int blocks = sms * 8, iters = 2048;
+    float ms = -1.f;
+    switch (op) {
+    case kViaddmaxS32: ms = run<kViaddmaxS32>(blocks, iters, sink); break;
+    case kVimax3S32: ms = run<kVimax3S32>(blocks, iters, sink); break;
+    case kVimax3ReluS32: ms = run<kVimax3ReluS32>(blocks, iters, sink); break;
+    case kIaddS32: ms = run<kIaddS32>(blocks, iters, sink); break;
+    case kImaxS32: ms = run<kImaxS32>(blocks, iters, sink); break;
+    case kImadS32: ms = run<kImadS32>(blocks, iters, sink); break;
+    case kViaddmaxS16x2: ms = run<kViaddmaxS16x2>(blocks, iters, sink); break;
+    case kVimax3S16x2: ms = run<kVimax3S16x2>(blocks, iters, sink); break;
+    case kPrmt: ms = run<kPrmt>(blocks, iters, sink); break;
+    default: break;
+    }
+    cudaFree(sink);
+    if (ms <= 0.f || cudaGetLastError() != cudaSuccess) return -1.0;
+    const double ops = (double)blocks * 256 * iters * 16 * kChains;
+    return ops / ((double)ms * 1e-3) / sms / (sm_mhz * 1e6);
+}
+
+extern "C" int sa_probe_num_ops(void) { return kNumOps; }

@@ -169,8 +169,10 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
         int32_t h_up_prev = hup0;
         int32_t hg_bot = HG[K - 1], e_bot = kNeg32, cm_bot = 0;
 
-        // best tracking (LOCAL) and the row of H(., n) (GLOCAL)
+        // best tracking (LOCAL) and the row of H(., n) (GLOCAL); the score pass keeps
+        // the best as a key (H*32 + 31 - row) and a threshold with the row bits set
         int32_t bv = 0, bi = 0, br = 0;
+        int32_t bkey = 0, bvx = 31;
         const int gn = LOCAL ? 0 : (rows - 1) / K;
         const int rn = LOCAL ? 0 : (rows - 1) % K;
 
@@ -200,18 +202,29 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
                 int4 dq = make_int4(0, 0, 0, 0);
                 int32_t e = e_up, hga = hg_up;
                 int32_t lm = 0, hpair = 0;
+                // score pass: the diagonal term of row r+1 is formed while row r still
+                // holds H(i-1, j) (no copy of the old value is kept)
+                int32_t gcur = 0;
+                if (PROF) {
+                    dq = pt[0];
+                    gcur = add_fma(dq.x, diag, one);
+                }
 #pragma unroll
                 for (int r = 0; r < K; r++) {
-                    int32_t d;
+                    int32_t gv;
                     if (PROF) {
-                        if ((r & 3) == 0) dq = pt[(r / 4) * 32];
-                        d = (r & 3) == 0 ? dq.x : (r & 3) == 1 ? dq.y : (r & 3) == 2 ? dq.z : dq.w;
+                        gv = gcur;
+                        if (r + 1 < K) {
+                            const int rn = r + 1;
+                            if ((rn & 3) == 0) dq = pt[(rn / 4) * 32];
+                            const int32_t dn = (rn & 3) == 0 ? dq.x : (rn & 3) == 1 ? dq.y : (rn & 3) == 2 ? dq.z : dq.w;
+                            gcur = add_fma(dn, HG[r], one);
+                        }
                     } else {
-                        d = ((mk >> r) & 1u) ? S.dm : S.dx;
+                        const int32_t d = ((mk >> r) & 1u) ? S.dm : S.dx;
+                        gv = diag + d;                    // H(i-1,j-1) + delta
+                        diag = HG[r];
                     }
-                    // H(i-1,j-1) + delta
-                    const int32_t gv = PROF ? add_fma(d, diag, one) : diag + d;
-                    diag = HG[r];
                     int32_t f, h;
                     if (!DIR) {
                         f = addmax(F[r], S.GE, HG[r]);    // max(F(i-1,j)+GE, H(i-1,j)+GO)
@@ -238,11 +251,13 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
                     HG[r] = PROF ? add_fma(h, S.GO, one) : h + S.GO;
                     hga = HG[r];
                     if (BEST && LOCAL) {
-                        // column maximum, two rows per 3-input max
                         if (PROF) {
-                            if ((r & 1) == 1) lm = __vimax3_s32(lm, hpair, h);
-                            else if (r == K - 1) lm = max(lm, h);
-                            else hpair = h;
+                            // column maximum of keys H*32 + (31 - r): the maximum key holds the
+                            // largest H and, among equal H, the first row (two rows per 3-input max)
+                            const int32_t key = add_fma(h, 31 - r, 32 * one);
+                            if ((r & 1) == 1) lm = __vimax3_s32(lm, hpair, key);
+                            else if (r == K - 1) lm = max(lm, key);
+                            else hpair = key;
                         } else {
                             lm = max(lm, h);
                         }
@@ -250,13 +265,24 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
                 }
                 hg_bot = HG[K - 1];
                 e_bot = e;
-                if (s < g) {                              // before this lane's first column
+                if (8 * b < L && s < g) {                 // before this lane's first column
                     reset_col0();
                     h_up_prev = hup0;
                 }
-                const bool active = (i >= 1) && (i <= w);
+                const bool active = (unsigned)(i - 1) < (unsigned)w;
                 if (BEST) {
-                    if (LOCAL) {
+                    if (LOCAL && PROF) {
+                        // keys: colbest slots hold keys; the lane best is the first column
+                        // whose maximum beats the best value (compare the H part only)
+                        const int32_t cm = max(cm_up, lm);
+                        cm_bot = cm;
+                        if (active && g == L - 1) cb[i - 1] = cm;
+                        if (active && lm > bvx) {
+                            bkey = lm;
+                            bvx = lm | 31;
+                            bi = i;
+                        }
+                    } else if (LOCAL) {
                         const int32_t cm = max(cm_up, lm);
                         cm_bot = cm;
                         if (active) {
@@ -295,6 +321,10 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
             int32_t best;
             int istar, jstar;
             bool empty = false;
+            if (LOCAL && PROF) {
+                bv = bkey >> 5;
+                br = 31 - (bkey & 31);
+            }
             if (LOCAL) {
                 int bj = g * K + br + 1 - pad;
 #pragma unroll
@@ -335,7 +365,7 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
             for (int ii = g + 1; ii <= wsec; ii += L) {
                 const int dd = ii > istar ? ii - istar : istar - ii;
                 if (dd < n) continue;
-                const int32_t x = cb[ii - 1];
+                const int32_t x = (LOCAL && PROF) ? (cb[ii - 1] >> 5) : cb[ii - 1];
                 if (si == 0 || x > sv) { sv = x; si = ii; }
             }
 #pragma unroll

@@ -161,16 +161,22 @@ __global__ void __launch_bounds__(128) k_fill16(FillArgs A) {
                 const uint32_t tA = (wb[0] >> (2 * u)) & 3u, tB = (wb[1] >> (2 * u)) & 3u;
                 const uint2* pa = prof2 + (tA * K4) * 32 + lane;
                 const uint2* pb = prof2 + ((4 + tB) * K4) * 32 + lane;
-                uint2 qa = make_uint2(0, 0), qb = make_uint2(0, 0);
+                uint2 qa = pa[0], qb = pb[0];
                 uint32_t e = e_up, hga = hg_up;
                 uint32_t lm = BIAS2, hpair = BIAS2;
+                // the diagonal term of row r+1 is formed while row r still holds
+                // H(i-1, j) (no copy of the old value is kept)
+                uint32_t gcur = __viaddmax_s16x2(diag, __byte_perm(qa.x, qb.x, 0x5410), BIAS2);
 #pragma unroll
                 for (int r = 0; r < K; r++) {
-                    if ((r & 3) == 0) { qa = pa[(r / 4) * 32]; qb = pb[(r / 4) * 32]; }
-                    const uint32_t xa = (r & 2) ? qa.y : qa.x, xb = (r & 2) ? qb.y : qb.x;
-                    const uint32_t d = __byte_perm(xa, xb, (r & 1) ? 0x7632 : 0x5410);
-                    const uint32_t gv = __viaddmax_s16x2(diag, d, BIAS2);     // max(G, 0) + bias
-                    diag = HG[r];
+                    const uint32_t gv = gcur;                                  // max(G, 0) + bias
+                    if (r + 1 < K) {
+                        const int rn = r + 1;
+                        if ((rn & 3) == 0) { qa = pa[(rn / 4) * 32]; qb = pb[(rn / 4) * 32]; }
+                        const uint32_t xa = (rn & 2) ? qa.y : qa.x, xb = (rn & 2) ? qb.y : qb.x;
+                        const uint32_t dn = __byte_perm(xa, xb, (rn & 1) ? 0x7632 : 0x5410);
+                        gcur = __viaddmax_s16x2(HG[r], dn, BIAS2);
+                    }
                     const uint32_t f = __viaddmax_s16x2(F[r], GE2, HG[r]);
                     e = __viaddmax_s16x2(e, GE2, hga);
                     const uint32_t hv = __vimax3_s16x2(gv, e, f);
@@ -183,7 +189,7 @@ __global__ void __launch_bounds__(128) k_fill16(FillArgs A) {
                 }
                 hg_bot = HG[K - 1];
                 e_bot = e;
-                if (s < g) {
+                if (8 * b < L && s < g) {
                     reset_col0();
                     h_up_prev = hg0;
                 }
