@@ -25,7 +25,8 @@
  *  - Scores are BWA magnitudes (the paper adopts BWA's scoring scheme): match
  *    a, mismatch b, gap open o, gap extend e, all >= 0; a gap of length L costs
  *    o + L*e.  In the paper's signed form S_MA = a, S_MI = -b, S_GO = -(o+e),
- *    S_GE = -e.  Limits: a, b, o + e <= 16383 and n * max(a, b, o + e) < 2^28.
+ *    S_GE = -e.  Limits: a <= 2047 (a LOCAL best score then fits 21 bits),
+ *    b, o + e <= 16383.
  *  - Best cell: the first maximum in window-major order (smallest reference
  *    end, then smallest read end).  LOCAL with no positive cell: no alignment
  *    (SA_RES_EMPTY, score 0, coordinates -1, second SA_NO_SCORE).

@@ -98,13 +98,13 @@ struct PlanBlock {
 struct Workspace {
     DevBuf jobs, reads, out, cigar;          // inputs/outputs of the host-buffer entry points
     DevBuf key, order, rpack, state, rect, tb, count, coff, sizes, offs, bsum;
-    DevBuf colbest, tmp_ops, arena, plan, counters, list16, list32, list64, band, ovf;
+    DevBuf colbest, tmp_ops, arena, plan, counters, list16, list32, list64, band, ovf, lkeys;
     PlanBlock* h_plan = nullptr;             // pinned mirror of the plan block
     cudaEvent_t ev[16] = {};
     bool ev_ok = false;
     void release() {
         DevBuf* all[] = {&jobs, &reads, &out, &cigar, &key, &order, &rpack, &state, &rect, &tb,
-                         &count, &coff, &sizes, &offs, &bsum, &colbest, &tmp_ops, &arena,
+                         &count, &coff, &sizes, &offs, &bsum, &colbest, &lkeys, &tmp_ops, &arena,
                          &plan, &counters, &list16, &list32, &list64, &band, &ovf};
         for (DevBuf* b : all) b->release();
         if (h_plan) cudaFreeHost(h_plan);
@@ -148,8 +148,8 @@ int check_params(const sa_params* p, Score* sc) {
     const sa_scoring& s = p->sc;
     if (s.match < 0 || s.mismatch < 0 || s.gap_open < 0 || s.gap_extend < 0)
         return fail(SA_EINVAL, "scores are magnitudes and must be >= 0");
-    if (s.match > 16383 || s.mismatch > 16383 || (int64_t)s.gap_open + s.gap_extend > 16383)
-        return fail(SA_EINVAL, "match, mismatch and gap_open + gap_extend must be <= 16383");
+    if (s.match > 2047 || s.mismatch > 16383 || (int64_t)s.gap_open + s.gap_extend > 16383)
+        return fail(SA_EINVAL, "match must be <= 2047, mismatch and gap_open + gap_extend <= 16383");
     if (p->mode != SA_LOCAL && p->mode != SA_GLOCAL) return fail(SA_EINVAL, "mode must be SA_LOCAL or SA_GLOCAL");
     if (p->width != 0 && p->width != 16 && p->width != 32) return fail(SA_EINVAL, "width must be 0, 16 or 32");
     if (p->form != SA_FORM_BATCHED && p->form != SA_FORM_PLAIN) return fail(SA_EINVAL, "unknown form");
@@ -163,15 +163,14 @@ int check_params(const sa_params* p, Score* sc) {
     return SA_OK;
 }
 
-// The 16-bit packed score pass is exact for LOCAL alignment when every value the
-// recurrence forms stays inside the biased 16-bit range (see fill16.cuh): match
-// <= 8191 (a positive overflow threshold), mismatch and gap open + 2 x extend
-// <= 16383.  Larger values are handled by overflow detection and the 32-bit
-// rerun only on the upper side, so they need the 32-bit path from the start.
+// The 16-bit packed score pass serves LOCAL alignment: with match <= 2047 and
+// mismatch, gap open + extend <= 16383 every value it forms below its overflow
+// threshold fits a signed 16-bit half (see fill16.cuh); jobs that reach the
+// threshold are flagged and recomputed by the 32-bit pass.
 bool use16(const sa_params* P) {
     if (P->mode != SA_LOCAL || P->width == 32 || P->form == SA_FORM_PLAIN) return false;
     const sa_scoring& s = P->sc;
-    return s.match <= 8191 && s.mismatch <= 16383 && (int64_t)s.gap_open + 2 * (int64_t)s.gap_extend <= 16383;
+    return s.match <= 2047 && s.mismatch <= 16383 && (int64_t)s.gap_open + s.gap_extend <= 16383;
 }
 
 int ensure_events(Workspace& ws) {
@@ -311,17 +310,28 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
         if (bps < 1) bps = 1;
         return X.num_sms * bps;
     };
-    const bool w16 = use16(P);
-    int max_groups = 1;
+    // 16-bit pairs per length bucket: when asked for (width 16), or by default when
+    // no job of the bucket can reach the 16-bit threshold (a * rows + beta < 1024 - a)
+    bool w16[kNumCfg] = {};
+    bool any16 = false;
+    for (int c = 0; c < kNumCfg; c++) {
+        const int64_t rows = (int64_t)cfg_L(c) * cfg_K(c);
+        const bool safe = (int64_t)P->sc.match * (rows + 1) + P->sc.gap_open + P->sc.gap_extend < 1024;
+        w16[c] = !plain && cfg_count[c] && use16(P) && (P->width == 16 || safe);
+        any16 = any16 || w16[c];
+    }
+    int max_groups = 1, max_warps16 = 1;
     for (int c = 0; c < kNumCfg; c++) {
         if (plain ? c != plain_cfg : !cfg_count[c]) continue;
-        const int kinds[2] = {plain ? (int)kFillPlain : (int)kFillScore, w16 ? (int)kFillScore16 : (int)kFillScore};
+        const int kinds[2] = {plain ? (int)kFillPlain : (int)kFillScore, w16[c] ? (int)kFillScore16 : (int)kFillScore};
         for (int kind : kinds) {
             const int groups = grid_for(c, kind) * (kBlock / 32) * (32 / cfg_L(c));
             max_groups = std::max(max_groups, groups);
         }
+        if (w16[c]) max_warps16 = std::max(max_warps16, grid_for(c, kFillScore16) * (kBlock / 32));
     }
-    TRY(ws.colbest.ensure((size_t)max_groups * max_m * 4, "column maxima"));
+    TRY(ws.colbest.ensure((size_t)max_groups * cb_words(max_m) * 4, "column maxima"));
+    if (any16) TRY(ws.lkeys.ensure((size_t)max_warps16 * lane_key_words(max_m) * 4, "lane keys"));
 
     // --- stage: order, packed reads
     if (!plain) {
@@ -349,7 +359,9 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
     base.sc = sc;
     base.state = ws.state.as<JobState>();
     base.colbest = ws.colbest.as<int32_t>();
-    base.cb_stride = max_m;
+    base.cb_stride = cb_words(max_m);
+    base.lane_keys = any16 ? ws.lkeys.as<uint32_t>() : nullptr;
+    base.lk_stride = lane_key_words(max_m);
     base.rect = ws.rect.as<Rect>();
     base.wave = 0;
     uint32_t* counters = ws.counters.as<uint32_t>();
@@ -367,9 +379,9 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             fl.args.pos_begin = cfg_begin[c];
             fl.args.pos_count = cfg_count[c];
             fl.args.item_counter = next_counter();
-            fl.kind = w16 ? kFillScore16 : kFillScore;
+            fl.kind = w16[c] ? kFillScore16 : kFillScore;
             fl.block = kBlock;
-            const uint32_t per_warp = (32 / cfg_L(c)) * (w16 ? 2 : 1);
+            const uint32_t per_warp = (32 / cfg_L(c)) * (w16[c] ? 2 : 1);
             const uint64_t warps_needed = (cfg_count[c] + per_warp - 1) / per_warp;
             fl.grid = (int)std::min<uint64_t>(grid_for(c, fl.kind), (warps_needed + 3) / 4);
             fl.stream = st;
@@ -379,14 +391,14 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             if (trace.on) { char b[64]; snprintf(b, sizeof b, "score pass cfg %d (%u jobs)", c, cfg_count[c]); trace(b); }
         }
         CU(cudaGetLastError());
-        if (w16) {
+        if (any16) {
             tfill16 = tm.mark();
             TRY(ws.ovf.ensure((size_t)n_jobs * 4, "overflow list"));
             launch_collect_overflow(ws.order.as<uint32_t>(), n_jobs, ws.state.as<JobState>(), dp->cfg_begin,
                                     ws.ovf.as<uint32_t>(), dp->ovf_count, st);
             launches++;
             for (int c = 0; c < kNumCfg; c++) {
-                if (!cfg_count[c]) continue;
+                if (!w16[c]) continue;
                 FillLaunch fl{};
                 fl.args = base;
                 fl.args.order = ws.ovf.as<uint32_t>();
@@ -434,7 +446,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             stats.band16_jobs = nb[0];
             stats.band_wide_jobs = nb[1] + nb[2];
             stats.rect_jobs = hp->cls_count[kClsRect];
-            for (int c = 0; c < kNumCfg; c++) stats.overflow_reruns += w16 ? hp->ovf_count[c] : 0u;
+            for (int c = 0; c < kNumCfg; c++) stats.overflow_reruns += w16[c] ? hp->ovf_count[c] : 0u;
             // band regions: 32 jobs of a class share a region of max_n rows x B/8 words x 32 lanes
             BandLayout bl{};
             uint64_t band_words = 0;
@@ -518,7 +530,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
         } else {
             CU(cudaMemcpyAsync(hp->ovf_count, dp->ovf_count, sizeof(hp->ovf_count), cudaMemcpyDeviceToHost, st));
             TRY(check_bad_read(dp, hp, st));
-            for (int c = 0; c < kNumCfg; c++) stats.overflow_reruns += w16 ? hp->ovf_count[c] : 0u;
+            for (int c = 0; c < kNumCfg; c++) stats.overflow_reruns += w16[c] ? hp->ovf_count[c] : 0u;
         }
     } else {
         // --- plain form: fixed-size batches in job order, one configuration for the

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
     const int g = lane % L;
     const int grp = lane / L;
     const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    int32_t* cb = BEST ? A.colbest + (size_t)(gwarp * G + grp) * A.cb_stride : nullptr;
+    int32_t* cb = BEST ? A.colbest + (size_t)(gwarp * G + grp) * A.cb_stride + kCbFront : nullptr;
     const Score S = A.sc;
     const uint32_t count = A.count_ptr ? *A.count_ptr : A.pos_count;
     // the score pass takes the match/mismatch term from a shared-memory profile
@@ -73,6 +73,14 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
     int32_t* prof = s_prof + (threadIdx.x >> 5) * prof_words_per_warp<K>();
     // 1 at run time (every launch uses 128-thread blocks), unknown to the compiler
     const int32_t one = (int32_t)(blockDim.x >> 7);
+    // lane 0 of a group takes the top border instead of a neighbour's values:
+    // x * nf + c with (nf, c) = (1, 0) on other lanes, (0, border) on lane 0
+    const int32_t nf = g != 0 ? one : 0;
+    const int32_t hg_c = g != 0 ? 0 : S.GO, e_c = g != 0 ? 0 : kNeg32;
+    // score pass, LOCAL: column-maximum keys H * 1024 + (1023 - row index in the
+    // group); the lane's own keys use its row r and are shifted by -g*K in the
+    // max that passes them down the group
+    const int32_t key_shift = -g * K;
 
     for (;;) {
         uint32_t item = 0;
@@ -110,31 +118,37 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
         for (int o = 16; o >= 1; o >>= 1) nblk_warp = max(nblk_warp, __shfl_xor_sync(FULL, nblk_warp, o));
         if (nblk_warp == 0) continue;
 
-        const int pad = LOCAL ? (L * K - rows) : 0;
+        // LOCAL and the score pass pad the group's rows at the top (GLOCAL padding
+        // rows score 0 against every base and stay at H = 0); the GLOCAL direction
+        // passes pad at the bottom
+        const int pad = (LOCAL || PROF) ? (L * K - rows) : 0;
         // match masks: bit r of mX is set when the lane's row r holds base X
         uint32_t mA = 0, mC = 0, mG = 0, mT = 0;
         if (PROF) {
             // profile: int4 ((t*K4 + r/4)*32 + lane) holds the diagonal terms of rows
-            // r..r+3 against window base t (rows that are padding never match);
-            // written and read as int4, so later reads cannot move above these stores
+            // r..r+3 against window base t (LOCAL padding rows never match, GLOCAL
+            // padding rows score 0); written and read as int4, so later reads cannot
+            // move above these stores
             const uint32_t* rp = A.rpack + (size_t)job * A.rw;
             int4* prof4 = reinterpret_cast<int4*>(prof);
 #pragma unroll
             for (int q = 0; q < K4; q++) {
                 int code[4];
+                int32_t miss[4];
 #pragma unroll
                 for (int u = 0; u < 4; u++) {
                     const int r = 4 * q + u;
                     const int j = g * K + r + 1 - pad;
                     code[u] = -1;
+                    miss[u] = (!LOCAL && j < 1) ? -S.GO : S.dx;
                     if (r < K && w > 0 && j >= 1 && j <= rows)
                         code[u] = (int)((__ldg(rp + ((j - 1) >> 4)) >> (2 * ((j - 1) & 15))) & 3u);
                 }
 #pragma unroll
                 for (int t = 0; t < 4; t++)
                     prof4[(t * K4 + q) * 32 + lane] =
-                        make_int4(code[0] == t ? S.dm : S.dx, code[1] == t ? S.dm : S.dx,
-                                  code[2] == t ? S.dm : S.dx, code[3] == t ? S.dm : S.dx);
+                        make_int4(code[0] == t ? S.dm : miss[0], code[1] == t ? S.dm : miss[1],
+                                  code[2] == t ? S.dm : miss[2], code[3] == t ? S.dm : miss[3]);
             }
         } else {
             const uint32_t* rp = A.rpack + (size_t)job * A.rw;
@@ -169,10 +183,8 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
         int32_t h_up_prev = hup0;
         int32_t hg_bot = HG[K - 1], e_bot = kNeg32, cm_bot = 0;
 
-        // best tracking (LOCAL) and the row of H(., n) (GLOCAL); the score pass keeps
-        // the best as a key (H*32 + 31 - row) and a threshold with the row bits set
+        // best tracking of the plain form (LOCAL) and its row of H(., n) (GLOCAL)
         int32_t bv = 0, bi = 0, br = 0;
-        int32_t bkey = 0, bvx = 31;
         const int gn = LOCAL ? 0 : (rows - 1) / K;
         const int rn = LOCAL ? 0 : (rows - 1) % K;
 
@@ -193,7 +205,13 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
                 int32_t e_up = __shfl_up_sync(FULL, e_bot, 1, L);
                 int32_t cm_up = 0;
                 if (BEST && LOCAL) cm_up = __shfl_up_sync(FULL, cm_bot, 1, L);
-                if (g == 0) { hg_up = S.GO; e_up = kNeg32; cm_up = 0; }
+                if (PROF) {
+                    hg_up = hg_up * nf + hg_c;
+                    e_up = e_up * nf + e_c;
+                    cm_up = cm_up * nf;
+                } else if (g == 0) {
+                    hg_up = S.GO; e_up = kNeg32; cm_up = 0;
+                }
                 int32_t diag = h_up_prev;
                 h_up_prev = hg_up;
                 const uint32_t t = (wb >> (2 * u)) & 3u;
@@ -252,9 +270,9 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
                     hga = HG[r];
                     if (BEST && LOCAL) {
                         if (PROF) {
-                            // column maximum of keys H*32 + (31 - r): the maximum key holds the
+                            // column maximum of keys H*1024 + (1023 - r): the maximum key holds the
                             // largest H and, among equal H, the first row (two rows per 3-input max)
-                            const int32_t key = add_fma(h, 31 - r, 32 * one);
+                            const int32_t key = add_fma(h, 1023 - r, 1024 * one);
                             if ((r & 1) == 1) lm = __vimax3_s32(lm, hpair, key);
                             else if (r == K - 1) lm = max(lm, key);
                             else hpair = key;
@@ -271,16 +289,16 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
                 }
                 const bool active = (unsigned)(i - 1) < (unsigned)w;
                 if (BEST) {
-                    if (LOCAL && PROF) {
-                        // keys: colbest slots hold keys; the lane best is the first column
-                        // whose maximum beats the best value (compare the H part only)
-                        const int32_t cm = max(cm_up, lm);
-                        cm_bot = cm;
-                        if (active && g == L - 1) cb[i - 1] = cm;
-                        if (active && lm > bvx) {
-                            bkey = lm;
-                            bvx = lm | 31;
-                            bi = i;
+                    if (PROF) {
+                        // the group's column maximum (LOCAL: key; GLOCAL: H(n, i) + S_GO)
+                        // goes to the column's slot from the last lane, for every step
+                        // (steps outside the window land in the slack slots)
+                        if (LOCAL) {
+                            const int32_t cm = __viaddmax_s32(lm, key_shift, cm_up);
+                            cm_bot = cm;
+                            if (g == L - 1) cb[i - 1] = cm;
+                        } else {
+                            if (g == L - 1) cb[i - 1] = HG[K - 1];
                         }
                     } else if (LOCAL) {
                         const int32_t cm = max(cm_up, lm);
@@ -321,11 +339,31 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
             int32_t best;
             int istar, jstar;
             bool empty = false;
-            if (LOCAL && PROF) {
-                bv = bkey >> 5;
-                br = 31 - (bkey & 31);
-            }
-            if (LOCAL) {
+            // column value of a slot: colbest(i) of the recurrence
+            auto colval = [&](int32_t raw) -> int32_t {
+                return PROF ? (LOCAL ? (raw >> 10) : raw - S.GO) : raw;
+            };
+            if (PROF && LOCAL) {
+                // best: the first column holding the largest H; the key of that column
+                // holds the first row with it (row index in the group = 1023 - tag)
+                int32_t v = -1, key = 0;
+                int vi = 0;
+                for (int ii = g + 1; ii <= w; ii += L) {
+                    const int32_t x = cb[ii - 1];
+                    if ((x >> 10) > v) { v = x >> 10; key = x; vi = ii; }
+                }
+#pragma unroll
+                for (int o = 1; o < L; o <<= 1) {
+                    const int32_t ov = __shfl_xor_sync(FULL, v, o, L);
+                    const int32_t ok = __shfl_xor_sync(FULL, key, o, L);
+                    const int oi = __shfl_xor_sync(FULL, vi, o, L);
+                    if (ov > v || (ov == v && oi < vi)) { v = ov; key = ok; vi = oi; }
+                }
+                best = v;
+                istar = vi;
+                jstar = 1024 - (key & 1023) - pad;
+                empty = v <= 0;
+            } else if (LOCAL) {
                 int bj = g * K + br + 1 - pad;
 #pragma unroll
                 for (int o = 1; o < L; o <<= 1) {
@@ -344,7 +382,7 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
                 int32_t v = kNeg32;
                 int vi = 0;
                 for (int ii = g + 1; ii <= w; ii += L) {
-                    const int32_t x = cb[ii - 1];
+                    const int32_t x = colval(cb[ii - 1]);
                     if (vi == 0 || x > v) { v = x; vi = ii; }
                 }
 #pragma unroll
@@ -365,7 +403,7 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
             for (int ii = g + 1; ii <= wsec; ii += L) {
                 const int dd = ii > istar ? ii - istar : istar - ii;
                 if (dd < n) continue;
-                const int32_t x = (LOCAL && PROF) ? (cb[ii - 1] >> 5) : cb[ii - 1];
+                const int32_t x = colval(cb[ii - 1]);
                 if (si == 0 || x > sv) { sv = x; si = ii; }
             }
 #pragma unroll

@@ -164,7 +164,7 @@ int run(sa_reference* R, const sa_params* P, const sa_job* d_jobs, uint32_t n_jo
     const int c = sa::cfg_for_rows((int)hs.max_n);
     const int L = sa::cfg_L(c);
     const int G = 32 / L;
-    const size_t slot = (size_t)hs.max_m * 4;
+    const size_t slot = (size_t)sa::cb_words(hs.max_m) * 4;
     const size_t block_slots = 4 * (size_t)G;        // 128-thread blocks: 4 warps x G groups
     if (off_cb > kScratchBytes || (kScratchBytes - off_cb) / slot < block_slots)
         return err(SA_EINVAL, "this batch needs about %zu bytes of scratch, more than the %zu-byte "
@@ -196,7 +196,7 @@ int run(sa_reference* R, const sa_params* P, const sa_job* d_jobs, uint32_t n_jo
     A.sc.mode = P->mode;
     A.state = reinterpret_cast<sa::JobState*>(base + off_state);
     A.colbest = reinterpret_cast<int32_t*>(base + off_cb);
-    A.cb_stride = hs.max_m;
+    A.cb_stride = sa::cb_words(hs.max_m);
     fl.kind = sa::kFillScore;
     fl.block = 128;
     int bps = sa::fill_max_blocks_per_sm(c, sa::kFillScore, P->mode);

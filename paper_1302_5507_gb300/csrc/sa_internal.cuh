@@ -105,6 +105,17 @@ __host__ __device__ inline int band_cls(int b) { return b == 0 ? kClsBand16 : (b
 __host__ __device__ inline int band_index(int cls) { return cls == kClsBand16 ? 0 : (cls == kClsBand32 ? 1 : (cls == kClsBand64 ? 2 : -1)); }
 __host__ __device__ inline int band_width_of(int b) { return 16 << b; }
 
+// Column-maximum slots of a lane group: window column i (1-based) at slot
+// kCbFront + i - 1.  The slack on both sides takes the stores of the skewed
+// wavefront's steps before column 1 and past the window end, which are then
+// written without a bounds test.
+constexpr int kCbFront = 32;
+constexpr int kCbTail = 40;
+__host__ __device__ inline uint32_t cb_words(uint32_t max_m) { return max_m + kCbFront + kCbTail; }
+// per-warp words of the 16-bit score pass's stored lane keys (one word per
+// wavefront step and lane; a job pair takes at most max_m + 38 steps)
+__host__ __device__ inline uint32_t lane_key_words(uint32_t max_m) { return (max_m + 48) * 32; }
+
 // Arguments of the wavefront kernels.
 struct FillArgs {
     const uint32_t* ref;          // padded packed reference (base 0 at ref + kRefFrontPad words)
@@ -120,7 +131,9 @@ struct FillArgs {
     Score sc;
     JobState* state;              // per job id
     int32_t* colbest;             // per group scratch, cb_stride words each
-    uint32_t cb_stride;
+    uint32_t cb_stride;           // cb_words(longest window)
+    uint32_t* lane_keys;          // 16-bit score pass: per warp scratch, lk_stride words each
+    uint32_t lk_stride;
     const Rect* rect;             // direction pass: per job id
     uint32_t* arena;              // direction bits
     int32_t wave;                 // direction pass: only jobs of this wave

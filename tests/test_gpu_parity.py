@@ -149,6 +149,10 @@ def test_invalid_inputs(sa):
         long_["read_len"][0] = sa.SA_MAX_READ + 1
         with pytest.raises(sa.SAError):
             ref.align(long_, wl.reads)
+        # a match score above 2047 (a LOCAL best past 21 bits) is refused
+        with pytest.raises(sa.SAError) as e:
+            ref.align(jobs, wl.reads, sa.make_params(scoring=(2048, 1, 1, 1)))
+        assert e.value.code == sa.SA_EINVAL
         # an empty batch is fine
         out, cig = ref.align(jobs[:0], wl.reads)
         assert len(out) == 0 and len(cig) == 0
@@ -240,8 +244,8 @@ def test_overflow_rerun_is_exact(sa):
         res, ores = assert_parity(sa, ref, wl, scoring=scoring, width=16)
         st = ref.stats()
         assert st["overflow_reruns"] > 0
-        # every job whose true best could not be held below the threshold was rerun
-        assert st["overflow_reruns"] >= int((ores["score"] >= 16383 - 200).sum())
+        # every job whose best reached the threshold (H + o + e >= 1024 - a) was rerun
+        assert st["overflow_reruns"] >= int((ores["score"] >= 1024 - 200 - (300 + 40)).sum())
         assert_parity(sa, ref, wl, scoring=scoring, width=16, want_cigar=False)
 
 
