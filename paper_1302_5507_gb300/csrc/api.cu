@@ -100,6 +100,12 @@ struct Workspace {
     DevBuf key, order, rpack, state, rect, tb, count, coff, sizes, offs, bsum;
     DevBuf colbest, tmp_ops, arena, plan, counters, list16, list32, list64, band, ovf, lkeys;
     PlanBlock* h_plan = nullptr;             // pinned mirror of the plan block
+    // lane-key scratch of the 16-bit score pass: entries carry the id of the item
+    // that wrote them; ids run on across launches until the 32-bit space is about
+    // to wrap, when (as after an allocation) the scratch is reset to id 0xFFFFFFFF
+    const void* lk_seen = nullptr;
+    size_t lk_seen_cap = 0;
+    uint64_t lk_next_id = 0;
     cudaEvent_t ev[16] = {};
     bool ev_ok = false;
     void release() {
@@ -331,7 +337,19 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
         if (w16[c]) max_warps16 = std::max(max_warps16, grid_for(c, kFillScore16) * (kBlock / 32));
     }
     TRY(ws.colbest.ensure((size_t)max_groups * cb_words(max_m) * 4, "column maxima"));
-    if (any16) TRY(ws.lkeys.ensure((size_t)max_warps16 * lane_key_words(max_m) * 4, "lane keys"));
+    if (any16) {
+        TRY(ws.lkeys.ensure((size_t)max_warps16 * lane_key_entries(max_m) * 8, "lane keys"));
+        uint64_t items = 0;
+        for (int c = 0; c < kNumCfg; c++)
+            if (w16[c]) items += (cfg_count[c] + 2 * (32 / cfg_L(c)) - 1) / (2 * (32 / cfg_L(c)));
+        if (ws.lkeys.p != ws.lk_seen || ws.lkeys.cap != ws.lk_seen_cap ||
+            ws.lk_next_id + items >= 0xFFFFFFFFull) {
+            CU(cudaMemsetAsync(ws.lkeys.p, 0xFF, ws.lkeys.cap, st));
+            ws.lk_seen = ws.lkeys.p;
+            ws.lk_seen_cap = ws.lkeys.cap;
+            ws.lk_next_id = 0;
+        }
+    }
 
     // --- stage: order, packed reads
     if (!plain) {
@@ -360,8 +378,8 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
     base.state = ws.state.as<JobState>();
     base.colbest = ws.colbest.as<int32_t>();
     base.cb_stride = cb_words(max_m);
-    base.lane_keys = any16 ? ws.lkeys.as<uint32_t>() : nullptr;
-    base.lk_stride = lane_key_words(max_m);
+    base.lane_keys = any16 ? ws.lkeys.as<uint2>() : nullptr;
+    base.lk_stride = lane_key_entries(max_m);
     base.rect = ws.rect.as<Rect>();
     base.wave = 0;
     uint32_t* counters = ws.counters.as<uint32_t>();
@@ -382,6 +400,10 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             fl.kind = w16[c] ? kFillScore16 : kFillScore;
             fl.block = kBlock;
             const uint32_t per_warp = (32 / cfg_L(c)) * (w16[c] ? 2 : 1);
+            if (w16[c]) {
+                fl.args.item_base = (uint32_t)ws.lk_next_id;
+                ws.lk_next_id += (cfg_count[c] + per_warp - 1) / per_warp;
+            }
             const uint64_t warps_needed = (cfg_count[c] + per_warp - 1) / per_warp;
             fl.grid = (int)std::min<uint64_t>(grid_for(c, fl.kind), (warps_needed + 3) / 4);
             fl.stream = st;
