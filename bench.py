@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 METRIC = "GCUPS (affine DP incl. traceback) at 1 GB300 vs plain form; p50/p99 request latency"
 WORKLOAD = "mate_rescue: 1M jobs, 150 bp mate (reverse-complemented) vs 800 bp window, 100 Mbp GC41 genome + 5% repeats"
 OPS_PER_CELL = 6          # minimal lane-ops per cell update (roofline)
-LANES_PER_SM = 128        # 32-bit integer lanes per SM per clock
+PROBE_S16X2, PROBE_S32 = 6, 0   # operation codes of the DPX throughput probe (viaddmax)
 
 
 def parse():
@@ -108,19 +108,48 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------------
 
+def kernel_source_sha():
+    """sha1 (12 hex digits) of the score-pass kernel sources (fill.cuh + fill16.cuh)."""
+    h = hashlib.sha1()
+    for f in ("fill.cuh", "fill16.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1302_5507_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
 def traffic_from_profiles():
     """DRAM bytes per launch of the score-pass kernel from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "fill_score_mate_rescue.md")
-    src = os.path.join(ROOT, "paper_1302_5507_gb300", "csrc", "fill.cuh")
+    summary, if it was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "fill16_score_mate_rescue.md")
     if not os.path.exists(path):
         return None
-    text = open(path).read()
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s*\(fill\.cuh sha1 ([0-9a-f]+)\)", text)
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s*\(kernel sources sha1 ([0-9a-f]+)\)",
+                  open(path).read())
     if not m:
         return None
-    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
-    return float(m.group(1)) if m.group(2) == sha else None
+    return float(m.group(1)) if m.group(2) == kernel_source_sha() else None
+
+
+def dpx_lane_ops_per_sm_clk(local_rank: int):
+    """Measured issue rate of the packed 16-bit and the 32-bit add-max (DPX)
+    instructions, lane-operations per SM per clock, from the probe library; the
+    clock is the median SM clock sampled while the probe runs."""
+    import ctypes
+    from paper_1302_5507_gb300 import build as sa_build
+    lib = ctypes.CDLL(sa_build.PROBE)
+    lib.sa_probe_ops_per_sm_clk.restype = ctypes.c_double
+    lib.sa_probe_ops_per_sm_clk.argtypes = [ctypes.c_int, ctypes.c_double]
+    rates = {PROBE_S16X2: [], PROBE_S32: []}
+    with ClockSampler(local_rank) as clk:
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 1.5:
+            for op in rates:
+                rates[op].append(lib.sa_probe_ops_per_sm_clk(op, 1e-6))   # ops per second per SM
+    mhz = clk.summary()["sm_mhz"] or 2070.0
+    out = {"sm_mhz": mhz}
+    for op, key in ((PROBE_S16X2, "viaddmax_s16x2"), (PROBE_S32, "viaddmax_s32")):
+        good = [r for r in rates[op] if r > 0]
+        out[key] = statistics.median(good) / (mhz * 1e6) if good else None
+    return out
 
 
 def cpu_baseline(wl, target_s: float = 8.0):
@@ -284,19 +313,29 @@ def run_ours(args, rank, world, dist):
     sm_mhz = clocks["sm_mhz"] or 2070.0
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
-    peak = n_sm * LANES_PER_SM * sm_mhz * 1e6 / OPS_PER_CELL / 1e9
+    # roofline of the score pass: the packed 16-bit kernel when every job ran in it
+    packed = int(stats["jobs16"]) == wl.n_jobs
+    dpx = dpx_lane_ops_per_sm_clk(local_rank)
+    lanes = dpx["viaddmax_s16x2" if packed else "viaddmax_s32"] or 64.0
+    cells_per_op = 2 if packed else 1
+    peak = n_sm * lanes * sm_mhz * 1e6 * cells_per_op / OPS_PER_CELL / 1e9
     fill_avg = float(np.mean(fill_ms)) if fill_ms else 0.0
     achieved = cells_rank / (fill_avg / 1e3) / 1e9 if fill_avg > 0 else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GCUPS",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic_from_profiles(),
-                "kernel": "k_fill32 score pass (score, ends, colbest, second best)",
-                "peak_basis": f"{n_sm} SMs x {LANES_PER_SM} int lanes/clk x {sm_mhz:.0f} MHz (median under load) / {OPS_PER_CELL} ops per cell, int32"}
+                "kernel": ("k_fill16 packed 16-bit score pass" if packed else "k_fill32 score pass")
+                          + " (score, ends, colbest, second best); CUDA events around the score-pass phase",
+                "peak_basis": f"{n_sm} SMs x {lanes:.1f} DPX lane-ops/SM/clk (measured, probe) x "
+                              f"{sm_mhz:.0f} MHz (median under load) x {cells_per_op} cells per lane-op "
+                              f"/ {OPS_PER_CELL} lane-ops per cell",
+                "dpx_probe": dpx, "kernel_sources_sha1": kernel_source_sha()}
 
     line = None
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": "s16x2" if packed else "int32",
+                "data": "synthetic",
                 "config": {"workload": WORKLOAD, "jobs_per_gpu": wl.n_jobs, "cells_per_gpu": cells_rank,
                            "mode": "LOCAL", "scoring": "match 1, mismatch 2, gap open 2, gap extend 1",
                            "form": "batched", "cache": "inputs + direction arena larger than L2 (no flush)",

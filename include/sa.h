@@ -134,10 +134,10 @@ typedef struct {           /* statistics of the last call on a reference or serv
     uint32_t kernel_launches;      /* all kernels launched by the call */
     float ms_stage, ms_fill, ms_rerun, ms_rect, ms_traceback, ms_finalize;  /* with profile != 0 */
     float ms_total;                /* device time of the whole call (profile != 0) */
-    uint32_t band16_jobs;          /* traced jobs whose optimal paths fit a band of 16 diagonals */
-    uint32_t band_wide_jobs;       /* ... a band of 32 or 64 diagonals */
+    uint32_t diag_jobs;            /* traced jobs whose optimal path is all matches (no direction pass) */
+    uint32_t band_jobs;            /* ... whose optimal paths fit a band of 8, 16, 32 or 64 diagonals */
     uint32_t rect_jobs;            /* ... neither: whole-rectangle direction pass */
-    uint32_t _pad;
+    uint32_t jobs16;               /* jobs whose score pass ran in 16-bit packed pairs */
 } sa_stats;
 
 typedef struct sa_reference sa_reference;

@@ -90,7 +90,7 @@ struct PlanBlock {
     uint32_t cfg_begin[kNumCfg + 1];
     uint32_t _pad;
     uint64_t totals[4];
-    uint32_t cls_count[5];         // direction-pass classes (none, band 16, band 32, rectangle, band 64)
+    uint32_t cls_count[kNumCls];   // jobs per direction-pass class (kCls*)
     uint32_t ovf_count[kNumCfg];   // jobs the 16-bit pass sent to the 32-bit rerun, per bucket
 };
 
@@ -98,7 +98,7 @@ struct PlanBlock {
 struct Workspace {
     DevBuf jobs, reads, out, cigar;          // inputs/outputs of the host-buffer entry points
     DevBuf key, order, rpack, state, rect, tb, count, coff, sizes, offs, bsum;
-    DevBuf colbest, tmp_ops, arena, plan, counters, list16, list32, list64, band, ovf, lkeys;
+    DevBuf colbest, tmp_ops, arena, plan, counters, blists, band, ovf, lkeys;
     PlanBlock* h_plan = nullptr;             // pinned mirror of the plan block
     // lane-key scratch of the 16-bit score pass: entries carry the id of the item
     // that wrote them; ids run on across launches until the 32-bit space is about
@@ -111,7 +111,7 @@ struct Workspace {
     void release() {
         DevBuf* all[] = {&jobs, &reads, &out, &cigar, &key, &order, &rpack, &state, &rect, &tb,
                          &count, &coff, &sizes, &offs, &bsum, &colbest, &lkeys, &tmp_ops, &arena,
-                         &plan, &counters, &list16, &list32, &list64, &band, &ovf};
+                         &plan, &counters, &blists, &band, &ovf};
         for (DevBuf* b : all) b->release();
         if (h_plan) cudaFreeHost(h_plan);
         h_plan = nullptr;
@@ -401,6 +401,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             fl.block = kBlock;
             const uint32_t per_warp = (32 / cfg_L(c)) * (w16[c] ? 2 : 1);
             if (w16[c]) {
+                stats.jobs16 += cfg_count[c];
                 fl.args.item_base = (uint32_t)ws.lk_next_id;
                 ws.lk_next_id += (cfg_count[c] + per_warp - 1) / per_warp;
             }
@@ -445,11 +446,9 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
         if (want_cigar) {
             // --- reduced traceback: banded direction pass for most jobs, the
             // wavefront rectangle pass (in arena waves) for wide bands, then the walk
-            TRY(ws.list16.ensure((size_t)n_jobs * 4, "band lists"));
-            TRY(ws.list32.ensure((size_t)n_jobs * 4, "band lists"));
-            TRY(ws.list64.ensure((size_t)n_jobs * 4, "band lists"));
-            uint32_t* lists[kNumBand] = {ws.list16.as<uint32_t>(), ws.list32.as<uint32_t>(),
-                                         ws.list64.as<uint32_t>()};
+            TRY(ws.blists.ensure((size_t)n_jobs * kNumBand * 4, "band lists"));
+            uint32_t* lists[kNumBand];
+            for (int k = 0; k < kNumBand; k++) lists[k] = ws.blists.as<uint32_t>() + (size_t)k * n_jobs;
             launch_rect_plan(d_jobs, ws.order.as<uint32_t>(), n_jobs, ws.state.as<JobState>(), sc,
                              min_score, 1, ws.rect.as<Rect>(), ws.sizes.as<uint64_t>(), lists,
                              dp->cls_count, st);
@@ -465,8 +464,8 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             const uint64_t total_words = hp->totals[0];
             uint32_t nb[kNumBand];
             for (int k = 0; k < kNumBand; k++) nb[k] = hp->cls_count[band_cls(k)];
-            stats.band16_jobs = nb[0];
-            stats.band_wide_jobs = nb[1] + nb[2];
+            stats.diag_jobs = hp->cls_count[kClsDiag];
+            stats.band_jobs = nb[0] + nb[1] + nb[2] + nb[3];
             stats.rect_jobs = hp->cls_count[kClsRect];
             for (int c = 0; c < kNumCfg; c++) stats.overflow_reruns += w16[c] ? hp->ovf_count[c] : 0u;
             // band regions: 32 jobs of a class share a region of max_n rows x B/8 words x 32 lanes

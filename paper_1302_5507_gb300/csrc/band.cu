@@ -15,20 +15,69 @@
 // Row j is computed left to right over the band slots k = i - j - d_lo; the
 // previous row stays in registers in place: slot k holds H(i-1, j-1) for the
 // diagonal move and slot k+1 holds H(i, j-1), E(i, j-1) for the vertical one.
-// Nibble words are stored interleaved by lane (word w of row j of the job in
-// lane t at ((j-1)*W + w)*32 + t of its warp's region), so the stores of a warp
-// are coalesced.
+// Rows whose band starts right of column 0 (all but the first few) take a copy
+// of the row loop without the border tests.  Nibble words are stored
+// interleaved by lane (word w of row j of the job in lane t at ((j-1)*W + w)*32
+// + t of its warp's region), so the stores of a warp are coalesced.
 #include "kernels.h"
 
 namespace sa {
 
 namespace {
 
+// a value the compiler must keep in a register (not re-read from the parameter
+// bank at every use)
+__device__ __forceinline__ int32_t in_reg(int32_t x) {
+    asm volatile("" : "+r"(x));
+    return x;
+}
+
+template <int B, bool LOCAL, bool EDGE>
+__device__ __forceinline__ void band_row(int32_t (&Hs)[B + 1], int32_t (&Es)[B + 1], uint32_t (&words)[(B + 7) / 8],
+                                         const uint64_t (&mmh)[B > 32 ? 2 : 1], int i0, int32_t border,
+                                         int32_t GO, int32_t GE, int32_t sa, int32_t sb) {
+    int32_t hleft = kNeg32, fleft = kNeg32;
+#pragma unroll
+    for (int k = 0; k < B; k++) {
+        int32_t hn, fn, en;
+        uint32_t nib = 0u;
+        if (EDGE && i0 + k <= 0) {
+            hn = (i0 + k == 0) ? border : kNeg32;   // column 0 (H(0, j)) or left of the window
+            en = kNeg32;
+            fn = kNeg32;
+        } else {
+            const int32_t diag = Hs[k], up = Hs[k + 1], eup = Es[k + 1];
+            const int32_t eo = up + GO, ee = eup + GE;
+            en = max(eo, ee);
+            const int32_t fo = hleft + GO, fe = fleft + GE;
+            fn = max(fo, fe);
+            const bool match = (mmh[k >> 5] >> (2 * (k & 31))) & 1ull;
+            const int32_t g = diag + (match ? sa : sb);
+            // source of H: diagonal > deletion (F) > insertion (E); LOCAL zero: stop.
+            // The source is decided by comparing the three candidates with each
+            // other, never by comparing a DPX maximum with one of its operands
+            // (on this toolchain such a comparison after __vimax3_s32_relu gave
+            // wrong predicates)
+            const int32_t ef = max(en, fn);
+            int32_t h = max(g, ef);
+            uint32_t src = g >= ef ? 1u : (fn >= en ? 2u : 3u);
+            if (LOCAL && h <= 0) { h = 0; src = 0u; }
+            nib = src | (eo >= ee ? 0u : 4u) | (fo >= fe ? 0u : 8u);
+            hn = h;
+        }
+        Hs[k] = hn;
+        Es[k] = en;
+        hleft = hn;
+        fleft = fn;
+        words[k >> 3] |= nib << (4 * (k & 7));
+    }
+}
+
 template <int B, int MODE>
 __global__ void __launch_bounds__(128) k_band(BandArgs A) {
     constexpr bool LOCAL = (MODE == SA_LOCAL);
-    constexpr int W = B / 8;
-    static_assert(B == 16 || B == 32 || B == 64, "band widths 16, 32 and 64");
+    constexpr int W = (B + 7) / 8;
+    static_assert(B == 8 || B == 16 || B == 32 || B == 64, "band widths 8, 16, 32 and 64");
     const uint32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
     if (pos >= A.count) return;
     const uint32_t job = A.list[pos];
@@ -36,7 +85,7 @@ __global__ void __launch_bounds__(128) k_band(BandArgs A) {
     const Rect R = A.rect[job];
     const int rows = R.rows;
     const int dlo = R.d_lo;
-    const Score S = A.sc;
+    const int32_t GO = in_reg(A.sc.GO), GE = in_reg(A.sc.GE), sa = in_reg(A.sc.a), sb = in_reg(A.sc.b);
     uint32_t* out = A.arena + (uint64_t)(pos >> 5) * A.warp_stride + (pos & 31);
     const uint32_t* rp = A.rpack + (size_t)job * A.rw;
     const uint32_t* refw = A.ref + kRefFrontPad;
@@ -70,44 +119,14 @@ __global__ void __launch_bounds__(128) k_band(BandArgs A) {
             const uint64_t x = wb ^ (rb * 0x5555555555555555ull);
             mmh[hh] = ~(x | (x >> 1)) & 0x5555555555555555ull;   // bit 2k: slot 32hh+k matches
         }
-        const int32_t border = (!LOCAL) ? S.GO + (j - 1) * S.GE : 0;  // H(0, j)
-        const bool edge = i0 < 1;
-        int32_t hleft = kNeg32, fleft = kNeg32;
         uint32_t words[W];
 #pragma unroll
         for (int w = 0; w < W; w++) words[w] = 0u;
-#pragma unroll
-        for (int k = 0; k < B; k++) {
-            int32_t hn, en, fn;
-            uint32_t nib = 0u;
-            const int i = i0 + k;
-            if (edge && i <= 0) {
-                hn = (i == 0) ? border : kNeg32;
-                en = kNeg32;
-                fn = kNeg32;
-            } else {
-                const int32_t diag = Hs[k], up = Hs[k + 1], eup = Es[k + 1];
-                const int32_t ee = eup + S.GE, eo = up + S.GO;
-                const bool eopen = eo >= ee;
-                en = eopen ? eo : ee;
-                const int32_t fe = fleft + S.GE, fo = hleft + S.GO;
-                const bool fopen = fo >= fe;
-                fn = fopen ? fo : fe;
-                const int32_t g = diag + (((mmh[k >> 5] >> (2 * (k & 31))) & 1ull) ? S.a : S.b);
-                const bool pF = fn >= en;
-                const int32_t ef = pF ? fn : en;
-                const bool pG = g >= ef;
-                int32_t h = pG ? g : ef;
-                uint32_t src = pG ? 1u : (pF ? 2u : 3u);
-                if (LOCAL && h <= 0) { h = 0; src = 0u; }
-                nib = src | (eopen ? 0u : 4u) | (fopen ? 0u : 8u);
-                hn = h;
-            }
-            Hs[k] = hn;
-            Es[k] = en;
-            hleft = hn;
-            fleft = fn;
-            words[k >> 3] |= nib << (4 * (k & 7));
+        if (i0 >= 1) {
+            band_row<B, LOCAL, false>(Hs, Es, words, mmh, i0, 0, GO, GE, sa, sb);
+        } else {
+            const int32_t border = (!LOCAL) ? GO + (j - 1) * GE : 0;  // H(0, j)
+            band_row<B, LOCAL, true>(Hs, Es, words, mmh, i0, border, GO, GE, sa, sb);
         }
 #pragma unroll
         for (int w = 0; w < W; w++) out[((uint64_t)(j - 1) * W + w) * 32] = words[w];
@@ -120,7 +139,9 @@ void launch_band(int cls, const BandArgs& a, cudaStream_t st) {
     if (!a.count) return;
     const unsigned grid = (a.count + 127) / 128;
     const bool local = a.sc.mode == SA_LOCAL;
-    if (cls == kClsBand16) {
+    if (cls == kClsBand8) {
+        local ? k_band<8, SA_LOCAL><<<grid, 128, 0, st>>>(a) : k_band<8, SA_GLOCAL><<<grid, 128, 0, st>>>(a);
+    } else if (cls == kClsBand16) {
         local ? k_band<16, SA_LOCAL><<<grid, 128, 0, st>>>(a) : k_band<16, SA_GLOCAL><<<grid, 128, 0, st>>>(a);
     } else if (cls == kClsBand32) {
         local ? k_band<32, SA_LOCAL><<<grid, 128, 0, st>>>(a) : k_band<32, SA_GLOCAL><<<grid, 128, 0, st>>>(a);

@@ -210,7 +210,12 @@ __global__ void __launch_bounds__(128) k_fill16(FillArgs A) {
                 // steps outside the windows land in slack slots / are never read
                 if (g == L - 1) cb[i - 1] = cm;
                 const uint32_t lb = __vimax3_s16x2(lane_best, lm, lm);
-                if (lb != lane_best) lk[(size_t)s * 32] = make_uint2(lm, item_id);
+                // the rise test goes through an opaque xor: a DPX maximum is never
+                // compared with one of its own operands (wrong predicates were
+                // seen for that pattern on this toolchain)
+                uint32_t rise = lb ^ lane_best;
+                asm volatile("" : "+r"(rise));
+                if (rise != 0u) lk[(size_t)s * 32] = make_uint2(lm, item_id);
                 lane_best = lb;
                 if (8 * b < L && s < g) {      // before this lane's first column
                     reset_col0();

@@ -93,17 +93,25 @@ struct Rect {
     int32_t start_i;    // traceback start cell in rect coordinates
     int32_t start_j;
     int32_t wave;
-    // banded form (cls 1, 2): diagonals d = i - j in [d_lo, d_lo + band width)
-    int32_t cls;        // 0 none, 1/2/4 band of 16/32/64, 3 wavefront rectangle
+    // banded classes: diagonals d = i - j in [d_lo, d_lo + band width)
+    int32_t cls;        // kCls*
     int32_t d_lo;
     uint32_t lpos;      // position in its class list
     int32_t _pad;
 };
-enum { kClsNone = 0, kClsBand16 = 1, kClsBand32 = 2, kClsRect = 3, kClsBand64 = 4 };
-constexpr int kNumBand = 3;                       // band classes 16, 32, 64
-__host__ __device__ inline int band_cls(int b) { return b == 0 ? kClsBand16 : (b == 1 ? kClsBand32 : kClsBand64); }
-__host__ __device__ inline int band_index(int cls) { return cls == kClsBand16 ? 0 : (cls == kClsBand32 ? 1 : (cls == kClsBand64 ? 2 : -1)); }
-__host__ __device__ inline int band_width_of(int b) { return 16 << b; }
+// direction-pass classes: none (no traceback), banded passes of 8/16/32/64
+// diagonals, the wavefront rectangle, and the pure diagonal (an optimal path
+// with S = a*j* - best = 0 is all matches: its CIGAR needs no direction bits)
+enum { kClsNone = 0, kClsBand16 = 1, kClsBand32 = 2, kClsRect = 3, kClsBand64 = 4, kClsDiag = 5,
+       kClsBand8 = 6, kNumCls = 7 };
+constexpr int kNumBand = 4;                       // band classes 8, 16, 32, 64
+__host__ __device__ inline int band_cls(int b) {
+    return b == 0 ? kClsBand8 : (b == 1 ? kClsBand16 : (b == 2 ? kClsBand32 : kClsBand64));
+}
+__host__ __device__ inline int band_index(int cls) {
+    return cls == kClsBand8 ? 0 : (cls == kClsBand16 ? 1 : (cls == kClsBand32 ? 2 : (cls == kClsBand64 ? 3 : -1)));
+}
+__host__ __device__ inline int band_width_of(int b) { return 8 << b; }
 
 // Column-maximum slots of a lane group: window column i (1-based) at slot
 // kCbFront + i - 1.  The slack on both sides takes the stores of the skewed

@@ -242,12 +242,17 @@ __global__ void k_rect_plan(const sa_job* __restrict__ jobs, const uint32_t* __r
             const int32_t e = -sc.GE;
             int64_t span = istar;
             R.cls = kClsRect;
-            if (e > 0) {
+            if (allow_band && slack == 0 && sc.a > 0) {
+                // every base of an optimal path is a match: the walk from (i*, j*)
+                // takes the diagonal (ties go to M first) down to row 0
+                R.cls = kClsDiag;
+                R.d_lo = istar - jstar;
+            } else if (e > 0) {
                 const int64_t dmax = slack / e, imax = slack / (sc.a + e);
                 const int64_t width = dmax + imax + 1;
                 R.d_lo = (int)((int64_t)(istar - jstar) - dmax);
                 if (allow_band)
-                    R.cls = width <= 16 ? kClsBand16
+                    R.cls = width <= 8 ? kClsBand8 : width <= 16 ? kClsBand16
                           : (width <= 32 ? kClsBand32 : (width <= 64 ? kClsBand64 : kClsRect));
                 span = (int64_t)jstar + dmax;
             }
@@ -278,9 +283,10 @@ __global__ void k_rect_plan(const sa_job* __restrict__ jobs, const uint32_t* __r
             }
         }
     }
-    {
-        const unsigned mask = __ballot_sync(0xffffffffu, valid && R.cls == kClsRect);
-        if (mask && (int)lane == __ffs(mask) - 1) atomicAdd(&cls_count[kClsRect], (uint32_t)__popc(mask));
+#pragma unroll
+    for (int cls : {(int)kClsRect, (int)kClsDiag}) {
+        const unsigned mask = __ballot_sync(0xffffffffu, valid && R.cls == cls);
+        if (mask && (int)lane == __ffs(mask) - 1) atomicAdd(&cls_count[cls], (uint32_t)__popc(mask));
     }
     if (valid) {
         rect[job] = R;
@@ -456,13 +462,23 @@ __global__ void k_traceback(const sa_job* __restrict__ jobs, uint32_t job_begin,
     const Rect R = rect[job];
     const int bidx = band_index(R.cls);
     const bool banded = bidx >= 0;
-    if (banded ? wave != 0 : (R.w <= 0 || R.wave != wave)) return;
-    const sa_job J = jobs[job];
-    const JobState st = state[job];
     TbOut out;
     out.n_rev = 0;
     out.read_begin = -1;
     out.ref_begin_rel = -1;
+    if (R.cls == kClsDiag && !plain) {
+        // all-match path: j* diagonal steps from (i*, j*) to (i* - j*, 0)
+        if (wave != 0) return;
+        tmp_ops[(uint64_t)job * tmp_stride] = ((uint32_t)R.rows << 4) | 0u;
+        out.n_rev = 1;
+        out.read_begin = 0;
+        out.ref_begin_rel = R.d_lo;
+        tb[job] = out;
+        return;
+    }
+    if (banded ? wave != 0 : (R.w <= 0 || R.wave != wave)) return;
+    const sa_job J = jobs[job];
+    const JobState st = state[job];
     int si = R.start_i, sj = R.start_j;
     if (plain) {
         // whole-window direction bits: start at the best cell found by the same fill

@@ -215,13 +215,14 @@ def test_full_size_mate_rescue_sampled(sa):
 
 
 def test_every_direction_pass_class_is_exercised(sa):
-    """The low-similarity sweep puts traced jobs in the band-16, wider band and
-    whole-rectangle direction passes; all three must match the oracle."""
+    """The low-similarity sweep puts traced jobs in every traceback class: the
+    all-match diagonal (no direction pass), the banded passes and the
+    whole-rectangle pass; all must match the oracle."""
     wl = workloads.lowsim(seed=2, n_jobs=1_200)
     with sa.Reference(wl.ref) as ref:
         assert_parity(sa, ref, wl)
         st = ref.stats()
-        assert st["band16_jobs"] > 0 and st["band_wide_jobs"] > 0 and st["rect_jobs"] > 0, st
+        assert st["diag_jobs"] > 0 and st["band_jobs"] > 0 and st["rect_jobs"] > 0, st
         assert_parity(sa, ref, wl, mode=1)
 
 
