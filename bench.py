@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving latency run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5"],
+                    help="c2 (default): the mate-rescue headline line; c3 uneven lengths, "
+                         "c4 low similarity, c5 serving sweep: one extra JSON line each (1 GPU)")
     return ap.parse_args()
 
 
@@ -349,9 +352,12 @@ def run_ours(args, rank, world, dist):
                 "phases_ms": phases,
                 "plain_form": plain}
 
-    # --- serving latency (continuous batching), rank 0 only
+    # --- serving latency (coalescing server), rank 0 only: a short run on this genome
     if rank == 0 and not args.no_serving:
-        line["serving"] = serving_run(sa, ref, wl)
+        import workloads
+        sizes, ppm = workloads.serving_arrivals(seed=3, n_requests=40)
+        reqs = [workloads.serving_request(wl.ref, 3, k, int(sizes[k])) for k in range(40)]
+        line["serving"] = serving_run(sa, ref, reqs, ppm, (0.8,), genome="the mate-rescue genome (100 Mbp)")
     ref.close()
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(wl)
@@ -359,51 +365,149 @@ def run_ours(args, rank, world, dist):
         print(json.dumps(line), flush=True)
 
 
-def serving_run(sa, ref, wl, n_requests: int = 40, load: float = 0.8):
-    """Poisson arrivals of requests of U[1, 50000] jobs (n U[50,250], m U[2n,6n] on the
-    same genome) at `load` x the offline batched throughput; p50/p99 submit->result."""
+def concat(reqs):
+    """One workload holding the jobs of `reqs` (read offsets rebased), same reference."""
     import workloads
-    sizes, ppm = workloads.serving_arrivals(seed=3, n_requests=n_requests)
-    reqs = [workloads.serving_request(wl.ref, 3, k, int(sizes[k])) for k in range(n_requests)]
-    # offline batched throughput on the same requests
+    off = np.cumsum([0] + [r.reads.size for r in reqs[:-1]]).astype(np.uint64)
+    return workloads.Workload(
+        "concat", reqs[0].ref, np.concatenate([r.reads for r in reqs]),
+        np.concatenate([r.read_off + o for r, o in zip(reqs, off)]),
+        np.concatenate([r.read_len for r in reqs]), np.concatenate([r.flags for r in reqs]),
+        np.concatenate([r.ref_pos for r in reqs]), np.concatenate([r.win_len for r in reqs]),
+        np.concatenate([r.truth for r in reqs]), dict(reqs[0].meta))
+
+
+def serving_run(sa, ref, reqs, ppm, loads, genome: str, plain: bool = False):
+    """Open-loop Poisson arrivals of `reqs` at each offered load (a fraction of the
+    offline batched throughput of the same jobs); p50/p99 submit -> result."""
+    allj = concat(reqs)
+    jobs_all = sa.jobs_array(allj.read_off, allj.read_len, allj.flags, allj.ref_pos, allj.win_len)
+    ref.align(jobs_all, allj.reads)                       # warm-up (workspace growth)
     t0 = time.perf_counter()
-    for r in reqs[:8]:
-        ref.align(sa.jobs_array(r.read_off, r.read_len, r.flags, r.ref_pos, r.win_len), r.reads)
-    offline = sum(r.cells for r in reqs[:8]) / (time.perf_counter() - t0)
-    mean_cells = float(np.mean([r.cells for r in reqs]))
-    rate = load * offline / mean_cells            # requests per second
-    gaps = -np.log(ppm.astype(np.float64) / 1e6) / rate
-    lat, done_cells = [], 0
+    ref.align(jobs_all, allj.reads)
+    offline = allj.cells / (time.perf_counter() - t0)
+    out = {"requests": len(reqs), "jobs": int(allj.n_jobs), "cells": int(allj.cells), "genome": genome,
+           "offline_batched_gcups": offline / 1e9,
+           "offline_form": "all jobs of the requests in one sa_align_batch call (host buffers)",
+           "server": "2 slots; queued requests coalesce into one device batch (<= 1M jobs)",
+           "poll": "one poller thread in submit order", "loads": []}
+    if plain:
+        pp = sa.make_params(form=sa.SA_FORM_PLAIN)
+        t0 = time.perf_counter()
+        ref.align(jobs_all, allj.reads, pp)
+        out["plain_gcups"] = allj.cells / (time.perf_counter() - t0) / 1e9
+    mean_cells = allj.cells / len(reqs)
+    arrays = [sa.jobs_array(r.read_off, r.read_len, r.flags, r.ref_pos, r.win_len) for r in reqs]
     import queue as _queue
-    pending = _queue.Queue()
-    with sa.Server(ref, sa.make_params(), max_inflight=4) as srv:
-        def poller():
-            while True:
-                item = pending.get()
-                if item is None:
-                    return
-                tk, ts, r = item
-                srv.poll(tk, r.n_jobs, sa.cigar_max_ops(r.read_len), timeout_ms=-1)
-                lat.append(time.perf_counter() - ts)
-        th = threading.Thread(target=poller)
-        th.start()
-        t_start = time.perf_counter()
-        t_next = t_start
-        for k, r in enumerate(reqs):
-            t_next += gaps[k]
-            while time.perf_counter() < t_next:
-                time.sleep(min(0.001, max(0.0, t_next - time.perf_counter())))
-            jobs = sa.jobs_array(r.read_off, r.read_len, r.flags, r.ref_pos, r.win_len)
-            pending.put((srv.submit(jobs, r.reads), time.perf_counter(), r))
-            done_cells += r.cells
-        pending.put(None)
-        th.join()
-        wall = time.perf_counter() - t_start
-    lat_ms = np.array(lat) * 1e3
-    return {"requests": n_requests, "offered_load": load, "offline_gcups": offline / 1e9,
-            "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
-            "gcups": done_cells / wall / 1e9, "genome": "the mate-rescue genome (100 Mbp)",
-            "poll": "one poller thread in submit order (FIFO admission)"}
+    for load in loads:
+        rate = load * offline / mean_cells            # requests per second
+        gaps = -np.log(np.maximum(ppm.astype(np.float64), 1.0) / 1e6) / rate
+        lat, done_cells = [], 0
+        pending = _queue.Queue()
+        with sa.Server(ref, sa.make_params(), max_inflight=2) as srv:
+            # warm-up: each slot runs one batch of every job once (device workspace and
+            # pinned staging grow to their largest size before the timed arrivals)
+            warm = [srv.submit(jobs_all, allj.reads) for _ in range(2)]
+            for tk in warm:
+                srv.poll(tk, allj.n_jobs, sa.cigar_max_ops(allj.read_len), timeout_ms=-1)
+
+            def poller():
+                while True:
+                    item = pending.get()
+                    if item is None:
+                        return
+                    tk, ts, r = item
+                    srv.poll(tk, r.n_jobs, sa.cigar_max_ops(r.read_len), timeout_ms=-1)
+                    lat.append(time.perf_counter() - ts)
+            th = threading.Thread(target=poller)
+            th.start()
+            t_start = time.perf_counter()
+            t_next = t_start
+            for k, r in enumerate(reqs):
+                t_next += gaps[k]
+                while time.perf_counter() < t_next:
+                    time.sleep(min(0.001, max(0.0, t_next - time.perf_counter())))
+                pending.put((srv.submit(arrays[k], r.reads), time.perf_counter(), r))
+                done_cells += r.cells
+            pending.put(None)
+            th.join()
+            wall = time.perf_counter() - t_start
+        lat_ms = np.array(lat) * 1e3
+        row = {"offered_load": load, "p50_ms": float(np.percentile(lat_ms, 50)),
+               "p99_ms": float(np.percentile(lat_ms, 99)), "gcups": done_cells / wall / 1e9}
+        row["vs_offline"] = row["gcups"] / out["offline_batched_gcups"]
+        if plain:
+            row["vs_plain"] = row["gcups"] / out["plain_gcups"]
+        out["loads"].append(row)
+    return out
+
+
+def device_line(sa, ref, wl, args, label, widths=(0,), cigar=(True, False)):
+    """GCUPS of one workload through sa_align_batch_dev (inputs resident), per
+    (width, CIGAR) setting, with the phase times of the library's CUDA events."""
+    import torch
+    dev = torch.device("cuda", 0)
+    jobs = sa.jobs_array(wl.read_off, wl.read_len, wl.flags, wl.ref_pos, wl.win_len)
+    d_jobs = torch.from_numpy(jobs.view(np.uint8)).to(dev)
+    d_reads = torch.from_numpy(wl.reads).to(dev)
+    d_out = torch.empty(len(jobs) * 56, dtype=torch.uint8, device=dev)
+    d_cig = torch.empty(sa.cigar_max_ops(wl.read_len), dtype=torch.int32, device=dev)
+    rows = []
+    for width in widths:
+        for cg in cigar:
+            p = sa.make_params(width=width, want_cigar=cg, profile=True)
+            for _ in range(max(3, args.warmup)):
+                ref.align_dev(d_jobs, d_reads, d_out, d_cig if cg else None, p)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            sts = []
+            e0.record()
+            for _ in range(args.steps):
+                ref.align_dev(d_jobs, d_reads, d_out, d_cig if cg else None, p)
+                sts.append(ref.stats())
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            ph = {k: float(np.mean([st[k] for st in sts])) for k in
+                  ("ms_stage", "ms_fill", "ms_rerun", "ms_rect", "ms_traceback", "ms_finalize")}
+            st = sts[-1]
+            rows.append({"width": width or "auto", "cigar": cg, "gcups": wl.cells / (ms / 1e3) / 1e9,
+                         "ms_per_step": ms, "score_pass_gcups": wl.cells / (ph["ms_fill"] / 1e3) / 1e9,
+                         "phases_ms": ph, "jobs16": int(st["jobs16"]), "overflow_reruns": int(st["overflow_reruns"]),
+                         "diag_jobs": int(st["diag_jobs"]), "band_jobs": int(st["band_jobs"]),
+                         "rect_jobs": int(st["rect_jobs"]), "kernel_launches": int(st["kernel_launches"])})
+    return {"config": label, "jobs": int(wl.n_jobs), "cells": int(wl.cells), "steps": args.steps, "rows": rows}
+
+
+def run_config(args):
+    """Extra measurement lines of the uneven, low-similarity and serving configurations."""
+    import torch
+    import paper_1302_5507_gb300 as sa
+    import __graft_entry__
+    import workloads
+    torch.cuda.set_device(0)
+    __graft_entry__.build()
+    if args.config == "c3":
+        wl = workloads.uneven(seed=1, n_jobs=4_000_000)
+        with sa.Reference(wl.ref) as ref:
+            line = device_line(sa, ref, wl, args, "c3 uneven: 4M jobs, n U[50,250], m U[1.5n,6n]",
+                               widths=(0, 32), cigar=(True,))
+    elif args.config == "c4":
+        wl = workloads.lowsim(seed=1, n_jobs=500_000)
+        with sa.Reference(wl.ref) as ref:
+            line = device_line(sa, ref, wl, args,
+                               "c4 low similarity: 500k jobs, n 250, m 1000, divergence 0-40%")
+    else:
+        ref_acgt = workloads.serving_reference(seed=1)
+        n_req = 200
+        sizes, ppm = workloads.serving_arrivals(seed=3, n_requests=n_req)
+        reqs = [workloads.serving_request(ref_acgt, 3, k, int(sizes[k])) for k in range(n_req)]
+        with sa.Reference(ref_acgt) as ref:
+            line = serving_run(sa, ref, reqs, ppm, (0.5, 0.8, 0.95),
+                               genome="3.1 Gbp i.i.d. reference (775 MB packed, device-resident)", plain=True)
+        line["config"] = "c5 serving: requests of U[1,50000] jobs, n U[50,250], m U[2n,6n]"
+    line["data"] = "synthetic"
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -413,6 +517,10 @@ def main():
     dist = None
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.config != "c2":
+        if rank == 0:
+            run_config(args)
         return
     if world > 1:
         import torch

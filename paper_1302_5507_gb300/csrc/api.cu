@@ -729,44 +729,132 @@ uint64_t estimate_bytes(const sa_job* jobs, uint32_t n, uint64_t reads_len) {
     return b;
 }
 
+// Pinned host staging buffer of a server slot (grown on demand).
+struct PinnedBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    bool ensure(size_t bytes) {
+        if (bytes <= cap && p) return true;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+        const size_t nb = std::max<size_t>(bytes + bytes / 2, 1 << 16);
+        if (cudaHostAlloc(&p, nb, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return false;
+        }
+        cap = nb;
+        return true;
+    }
+    ~PinnedBuf() {
+        if (p) cudaFreeHost(p);
+    }
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// Jobs of one coalesced device batch at most.
+constexpr uint64_t kCoalesceJobs = 1ull << 20;
+
+// Runs the requests of `batch` as one device batch: jobs concatenated (read
+// offsets rebased), results and CIGAR ops split back per request.
+int run_batch(sa_server* S, sa_server::Slot* slot, std::vector<std::shared_ptr<Request>>& batch,
+              PinnedBuf& hjobs, PinnedBuf& hreads, PinnedBuf& hout, PinnedBuf& hcig) {
+    uint64_t nj = 0, nr = 0, cap = 0;
+    for (auto& rq : batch) {
+        nj += rq->jobs.size();
+        nr += rq->reads.size();
+        for (const sa_job& j : rq->jobs) cap += 2ull * j.read_len + 3;   // 2n+3 ops bound every job
+    }
+    if (!hjobs.ensure(nj * sizeof(sa_job)) || !hreads.ensure(nr + 16) ||
+        !hout.ensure(nj * sizeof(sa_result)) || !hcig.ensure(std::max<uint64_t>(cap, 1) * 4))
+        return fail(SA_ENOMEM, "pinned staging allocation failed");
+    sa_job* J = hjobs.as<sa_job>();
+    char* Rd = hreads.as<char>();
+    uint64_t jo = 0, ro = 0;
+    for (auto& rq : batch) {
+        for (const sa_job& j : rq->jobs) {
+            J[jo] = j;
+            J[jo].read_off += ro;
+            jo++;
+        }
+        if (!rq->reads.empty()) std::memcpy(Rd + ro, rq->reads.data(), rq->reads.size());
+        ro += rq->reads.size();
+    }
+    Ctx X{S->ref->d_words, S->ref->len, S->ref->num_sms, &slot->ws, &slot->last};
+    uint64_t used = 0;
+    const int rc = run_host(X, &S->params, S->sc, J, (uint32_t)nj, Rd, nr, hout.as<sa_result>(),
+                            hcig.as<uint32_t>(), cap, &used, slot->stream);
+    if (rc != SA_OK) return rc;
+    const sa_result* O = hout.as<sa_result>();
+    const uint32_t* C = hcig.as<uint32_t>();
+    uint64_t b = 0;
+    for (auto& rq : batch) {
+        const uint64_t n = rq->jobs.size();
+        rq->out.assign(O + b, O + b + n);
+        uint64_t c0 = 0, c1 = 0;
+        if (n) {
+            c0 = O[b].cigar_off;
+            c1 = (uint64_t)O[b + n - 1].cigar_off + O[b + n - 1].cigar_len;
+        }
+        rq->cigar.assign(C + c0, C + c1);
+        for (sa_result& r : rq->out) r.cigar_off -= (uint32_t)c0;
+        b += n;
+    }
+    return SA_OK;
+}
+
 void slot_main(sa_server* S, sa_server::Slot* slot) {
     cudaSetDevice(S->ref->device);
+    PinnedBuf hjobs, hreads, hout, hcig;
     for (;;) {
-        std::shared_ptr<Request> rq;
+        std::vector<std::shared_ptr<Request>> batch;
+        uint64_t est = 0;
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            // FIFO admission: the head request starts when the memory budget allows
+            // FIFO admission: the head request starts when the memory budget allows;
+            // the requests queued behind it join its device batch while they fit
             S->cv_work.wait(lk, [&] {
                 return S->stop || (!S->queue.empty() &&
                                    S->in_use + S->queue.front()->est_bytes <= S->budget);
             });
             if (S->stop) return;
-            rq = S->queue.front();
-            S->queue.pop_front();
-            S->in_use += rq->est_bytes;
+            uint64_t nj = 0;
+            while (!S->queue.empty()) {
+                const auto& q = S->queue.front();
+                if (!batch.empty() && (nj + q->jobs.size() > kCoalesceJobs ||
+                                       S->in_use + est + q->est_bytes > S->budget))
+                    break;
+                nj += q->jobs.size();
+                est += q->est_bytes;
+                batch.push_back(q);
+                S->queue.pop_front();
+            }
+            S->in_use += est;
         }
-        Ctx X{S->ref->d_words, S->ref->len, S->ref->num_sms, &slot->ws, &slot->last};
-        const uint32_t n = (uint32_t)rq->jobs.size();
-        rq->out.resize(n);
-        uint64_t used = 0;
-        // CIGAR capacity: 2n+3 ops per job bounds every job
-        uint64_t cap = 0;
-        for (const sa_job& j : rq->jobs) cap += 2ull * j.read_len + 3;
-        rq->cigar.resize(cap);
-        const int rc = run_host(X, &S->params, S->sc, rq->jobs.data(), n, rq->reads.data(),
-                                rq->reads.size(), rq->out.data(), rq->cigar.data(), cap, &used,
-                                slot->stream);
-        std::string msg = rc == SA_OK ? std::string() : std::string(g_err);
-        rq->cigar.resize(used);
+        int rc = run_batch(S, slot, batch, hjobs, hreads, hout, hcig);
+        std::vector<int> rcs(batch.size(), rc);
+        std::vector<std::string> msgs(batch.size(), rc == SA_OK ? std::string() : std::string(g_err));
+        if (rc != SA_OK && batch.size() > 1) {
+            // one request's error (an invalid job) must not fail its batch mates
+            for (size_t k = 0; k < batch.size(); k++) {
+                std::vector<std::shared_ptr<Request>> one{batch[k]};
+                rcs[k] = run_batch(S, slot, one, hjobs, hreads, hout, hcig);
+                msgs[k] = rcs[k] == SA_OK ? std::string() : std::string(g_err);
+            }
+        }
         {
             std::lock_guard<std::mutex> lk(S->mu);
-            S->in_use -= rq->est_bytes;
-            rq->err = msg;
-            rq->rc = rc;
-            rq->jobs.clear();
-            rq->jobs.shrink_to_fit();
-            rq->reads.clear();
-            rq->reads.shrink_to_fit();
+            S->in_use -= est;
+            for (size_t k = 0; k < batch.size(); k++) {
+                Request& rq = *batch[k];
+                rq.err = msgs[k];
+                rq.rc = rcs[k];
+                rq.jobs.clear();
+                rq.jobs.shrink_to_fit();
+                rq.reads.clear();
+                rq.reads.shrink_to_fit();
+            }
         }
         S->cv_done.notify_all();
         S->cv_work.notify_all();

@@ -1,0 +1,89 @@
+"""Serving loop (sa_server_create / sa_submit / sa_poll) against the oracle.
+
+Requests queued behind a running one are coalesced into one device batch; the
+results must still come back per request, exactly as the oracle computes them,
+with each request's CIGAR ops and offsets of its own."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from oracle.compare import compare
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sa():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1302_5507_gb300 as sa
+    return sa
+
+
+def _requests(n_req=12, seed=41):
+    wl = workloads.small(seed, 3000, n_range=(1, 150), m_range=(1, 500), alphabet=4)
+    rng = np.random.default_rng(seed)
+    cuts = np.sort(rng.choice(np.arange(1, wl.n_jobs), n_req - 1, replace=False))
+    bounds = np.concatenate([[0], cuts, [wl.n_jobs]])
+    return wl, [wl.subset(np.arange(bounds[k], bounds[k + 1])) for k in range(n_req)]
+
+
+def test_coalesced_requests_match_the_oracle(sa):
+    wl, reqs = _requests()
+    with sa.Reference(wl.ref) as ref, sa.Server(ref, max_inflight=2) as srv:
+        # submit everything before polling so that queued requests share batches
+        tickets = [srv.submit(sa.jobs_array(r.read_off, r.read_len, r.flags, r.ref_pos, r.win_len), r.reads)
+                   for r in reqs]
+        for r, tk in zip(reqs, tickets):
+            rc, res, cig = srv.poll(tk, r.n_jobs, sa.cigar_max_ops(r.read_len))
+            assert rc == sa.SA_OK
+            ores, oops = oracle.align(r)
+            bad = compare(res, cig, ores, oops)
+            assert not bad, "\n".join(bad)
+            # each request's CIGAR buffer is its own, compact, in job order
+            assert res["cigar_off"][0] == 0
+            assert (np.diff(res["cigar_off"].astype(np.int64)) == res["cigar_len"][:-1]).all()
+
+
+def test_one_bad_request_does_not_fail_its_batch_mates(sa):
+    wl, reqs = _requests(n_req=5, seed=43)
+    with sa.Reference(wl.ref) as ref, sa.Server(ref, max_inflight=1) as srv:
+        arrays = [sa.jobs_array(r.read_off, r.read_len, r.flags, r.ref_pos, r.win_len) for r in reqs]
+        bad_reads = reqs[2].reads.copy()
+        bad_reads[0] = ord("N")
+        tickets = [srv.submit(a, bad_reads if k == 2 else r.reads)
+                   for k, (a, r) in enumerate(zip(arrays, reqs))]
+        for k, (r, tk) in enumerate(zip(reqs, tickets)):
+            if k == 2:
+                with pytest.raises(sa.SAError) as e:
+                    srv.poll(tk, r.n_jobs, sa.cigar_max_ops(r.read_len))
+                assert e.value.code == sa.SA_EINVAL
+                continue
+            rc, res, cig = srv.poll(tk, r.n_jobs, sa.cigar_max_ops(r.read_len))
+            assert rc == sa.SA_OK
+            ores, oops = oracle.align(r)
+            assert not compare(res, cig, ores, oops)
+
+
+def test_poll_states_and_budget(sa):
+    wl, reqs = _requests(n_req=2, seed=47)
+    r = reqs[0]
+    jobs = sa.jobs_array(r.read_off, r.read_len, r.flags, r.ref_pos, r.win_len)
+    with sa.Reference(wl.ref) as ref:
+        with sa.Server(ref) as srv:
+            tk = srv.submit(jobs, r.reads)
+            rc, _, _ = srv.poll(tk, r.n_jobs, sa.cigar_max_ops(r.read_len), timeout_ms=0)
+            assert rc in (sa.SA_OK, sa.SA_PENDING)
+            if rc == sa.SA_PENDING:
+                rc, res, cig = srv.poll(tk, r.n_jobs, sa.cigar_max_ops(r.read_len))
+                assert rc == sa.SA_OK
+            # a ticket is consumed by its successful poll
+            with pytest.raises(sa.SAError) as e:
+                srv.poll(tk, r.n_jobs, sa.cigar_max_ops(r.read_len))
+            assert e.value.code == sa.SA_ENOTFOUND
+        # a request larger than the whole device-memory budget is refused at submit
+        with sa.Server(ref, hbm_budget=1 << 10) as srv:
+            with pytest.raises(sa.SAError) as e:
+                srv.submit(jobs, r.reads)
+            assert e.value.code == sa.SA_EBUSY
