@@ -397,6 +397,8 @@ def serving_run(sa, ref, reqs, ppm, loads, genome: str, plain: bool = False):
         ref.align(jobs_all, allj.reads, pp)
         out["plain_gcups"] = allj.cells / (time.perf_counter() - t0) / 1e9
     mean_cells = allj.cells / len(reqs)
+    warm_wl = allj.subset(np.arange(min(allj.n_jobs, 1 << 20)))
+    warm_jobs = sa.jobs_array(warm_wl.read_off, warm_wl.read_len, warm_wl.flags, warm_wl.ref_pos, warm_wl.win_len)
     arrays = [sa.jobs_array(r.read_off, r.read_len, r.flags, r.ref_pos, r.win_len) for r in reqs]
     import queue as _queue
     for load in loads:
@@ -405,11 +407,12 @@ def serving_run(sa, ref, reqs, ppm, loads, genome: str, plain: bool = False):
         lat, done_cells = [], 0
         pending = _queue.Queue()
         with sa.Server(ref, sa.make_params(), max_inflight=2) as srv:
-            # warm-up: each slot runs one batch of every job once (device workspace and
-            # pinned staging grow to their largest size before the timed arrivals)
-            warm = [srv.submit(jobs_all, allj.reads) for _ in range(2)]
+            # warm-up: each slot runs one batch as large as a coalesced batch can get
+            # (device workspace and pinned staging reach their largest size before
+            # the timed arrivals)
+            warm = [srv.submit(warm_jobs, warm_wl.reads) for _ in range(2)]
             for tk in warm:
-                srv.poll(tk, allj.n_jobs, sa.cigar_max_ops(allj.read_len), timeout_ms=-1)
+                srv.poll(tk, warm_wl.n_jobs, sa.cigar_max_ops(warm_wl.read_len), timeout_ms=-1)
 
             def poller():
                 while True:

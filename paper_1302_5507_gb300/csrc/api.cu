@@ -714,19 +714,21 @@ struct sa_server {
 
 namespace {
 
-// Device memory one request needs while it runs (workspace buffers and the
-// direction arena, bounded by whole-window direction bits).
+// Device memory one request needs while it runs: per-job workspace (job, result,
+// state, rectangle, plan and scan entries, packed read, CIGAR scratch of 2n+3
+// ops), the band regions at their widest (64 diagonals: 8 words a row), and the
+// wavefront-rectangle arena, which runs in waves and is charged at most 4 GB.
 uint64_t estimate_bytes(const sa_job* jobs, uint32_t n, uint64_t reads_len) {
-    uint64_t b = reads_len + (uint64_t)n * (sizeof(sa_job) + sizeof(sa_result) + 64 + 8 * 7);
-    uint32_t max_n = 1;
+    uint64_t b = reads_len + (uint64_t)n * (sizeof(sa_job) + sizeof(sa_result) + 256);
+    uint64_t rect = 0;
     for (uint32_t k = 0; k < n; k++) {
-        const uint32_t rn = std::min(jobs[k].read_len, SA_MAX_READ), m = std::min(jobs[k].win_len, SA_MAX_WINDOW);
-        max_n = std::max(max_n, rn);
-        const int c = cfg_for_rows((int)std::max(rn, 1u));
-        b += 4 * dir_words(cfg_L(c), cfg_K(c), (int)m) + (uint64_t)4 * ((rn + 15) / 16);
+        const uint32_t rn = std::max(std::min(jobs[k].read_len, SA_MAX_READ), 1u);
+        const uint32_t m = std::min(jobs[k].win_len, SA_MAX_WINDOW);
+        const int c = cfg_for_rows((int)rn);
+        b += (uint64_t)4 * ((rn + 15) / 16) + (uint64_t)4 * (2 * rn + 3) + (uint64_t)32 * rn;
+        rect += 4 * dir_words(cfg_L(c), cfg_K(c), (int)m);
     }
-    b += (uint64_t)n * (2 * max_n + 3) * 4;
-    return b;
+    return b + std::min<uint64_t>(rect, 4ull << 30);
 }
 
 // Pinned host staging buffer of a server slot (grown on demand).
@@ -757,7 +759,8 @@ struct PinnedBuf {
 constexpr uint64_t kCoalesceJobs = 1ull << 20;
 
 // Runs the requests of `batch` as one device batch: jobs concatenated (read
-// offsets rebased), results and CIGAR ops split back per request.
+// offsets rebased) in pinned staging, results and CIGAR ops split back per
+// request.  The CIGAR staging is sized by the ops actually produced.
 int run_batch(sa_server* S, sa_server::Slot* slot, std::vector<std::shared_ptr<Request>>& batch,
               PinnedBuf& hjobs, PinnedBuf& hreads, PinnedBuf& hout, PinnedBuf& hcig) {
     uint64_t nj = 0, nr = 0, cap = 0;
@@ -766,8 +769,7 @@ int run_batch(sa_server* S, sa_server::Slot* slot, std::vector<std::shared_ptr<R
         nr += rq->reads.size();
         for (const sa_job& j : rq->jobs) cap += 2ull * j.read_len + 3;   // 2n+3 ops bound every job
     }
-    if (!hjobs.ensure(nj * sizeof(sa_job)) || !hreads.ensure(nr + 16) ||
-        !hout.ensure(nj * sizeof(sa_result)) || !hcig.ensure(std::max<uint64_t>(cap, 1) * 4))
+    if (!hjobs.ensure(nj * sizeof(sa_job)) || !hreads.ensure(nr + 16) || !hout.ensure(nj * sizeof(sa_result)))
         return fail(SA_ENOMEM, "pinned staging allocation failed");
     sa_job* J = hjobs.as<sa_job>();
     char* Rd = hreads.as<char>();
@@ -781,11 +783,23 @@ int run_batch(sa_server* S, sa_server::Slot* slot, std::vector<std::shared_ptr<R
         if (!rq->reads.empty()) std::memcpy(Rd + ro, rq->reads.data(), rq->reads.size());
         ro += rq->reads.size();
     }
-    Ctx X{S->ref->d_words, S->ref->len, S->ref->num_sms, &slot->ws, &slot->last};
+    Workspace& ws = slot->ws;
+    const cudaStream_t st = slot->stream;
+    Ctx X{S->ref->d_words, S->ref->len, S->ref->num_sms, &ws, &slot->last};
     uint64_t used = 0;
-    const int rc = run_host(X, &S->params, S->sc, J, (uint32_t)nj, Rd, nr, hout.as<sa_result>(),
-                            hcig.as<uint32_t>(), cap, &used, slot->stream);
-    if (rc != SA_OK) return rc;
+    if (nj) {
+        TRY(ws.jobs.ensure(nj * sizeof(sa_job), "jobs"));
+        TRY(ws.reads.ensure(nr + 16, "reads"));
+        TRY(ws.out.ensure(nj * sizeof(sa_result), "results"));
+        CU(cudaMemcpyAsync(ws.jobs.p, J, nj * sizeof(sa_job), cudaMemcpyHostToDevice, st));
+        if (nr) CU(cudaMemcpyAsync(ws.reads.p, Rd, nr, cudaMemcpyHostToDevice, st));
+        TRY(run_device(X, &S->params, S->sc, ws.jobs.as<sa_job>(), (uint32_t)nj, ws.reads.as<char>(), nr,
+                       ws.out.as<sa_result>(), nullptr, cap, &used, &ws.cigar, st));
+        if (!hcig.ensure(std::max<uint64_t>(used, 1) * 4)) return fail(SA_ENOMEM, "pinned staging allocation failed");
+        CU(cudaMemcpyAsync(hout.p, ws.out.p, nj * sizeof(sa_result), cudaMemcpyDeviceToHost, st));
+        if (used) CU(cudaMemcpyAsync(hcig.p, ws.cigar.p, used * 4, cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+    }
     const sa_result* O = hout.as<sa_result>();
     const uint32_t* C = hcig.as<uint32_t>();
     uint64_t b = 0;
