@@ -41,7 +41,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--jobs", type=int, default=1_000_000)
+    ap.add_argument("--jobs", type=int, default=None,
+                    help="jobs per GPU (default: the configuration's size, 1M for c2)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving latency run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
@@ -180,7 +181,7 @@ def run_reference(args, rank, world):
     import workloads  # noqa: F401
     if rank != 0:
         return
-    wl = make_workload(0, args.jobs)
+    wl = make_workload(0, args.jobs or 1_000_000)
     import oracle
     nthreads = oracle.threads()
     # each step: a bounded sample (about 2 s of oracle work), same workload and metric
@@ -219,7 +220,7 @@ def run_ours(args, rank, world, dist):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     __graft_entry__.build()
-    wl = make_workload(rank, args.jobs)
+    wl = make_workload(rank, args.jobs or 1_000_000)
     jobs = sa.jobs_array(wl.read_off, wl.read_len, wl.flags, wl.ref_pos, wl.win_len)
     ref = sa.Reference(wl.ref, device=local_rank)
     params = sa.make_params(profile=True)
@@ -491,12 +492,12 @@ def run_config(args):
     torch.cuda.set_device(0)
     __graft_entry__.build()
     if args.config == "c3":
-        wl = workloads.uneven(seed=1, n_jobs=4_000_000)
+        wl = workloads.uneven(seed=1, n_jobs=args.jobs or 4_000_000)
         with sa.Reference(wl.ref) as ref:
             line = device_line(sa, ref, wl, args, "c3 uneven: 4M jobs, n U[50,250], m U[1.5n,6n]",
                                widths=(0, 32), cigar=(True,))
     elif args.config == "c4":
-        wl = workloads.lowsim(seed=1, n_jobs=500_000)
+        wl = workloads.lowsim(seed=1, n_jobs=args.jobs or 500_000)
         with sa.Reference(wl.ref) as ref:
             line = device_line(sa, ref, wl, args,
                                "c4 low similarity: 500k jobs, n 250, m 1000, divergence 0-40%")

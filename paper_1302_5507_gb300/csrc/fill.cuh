@@ -192,15 +192,19 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
         for (int b = 0; b < nblk_warp; b++) {
             const uint32_t wb = wb_next;
             wb_next = load_window16<L, K>(A, wstart, b + 1, g);
-            uint32_t dw[K];
-            if (DIR) {
-#pragma unroll
-                for (int k = 0; k < K; k++) dw[k] = 0u;
-            }
-#pragma unroll
+            // the direction passes keep the step loop rolled: their step body (K rows
+            // of compare/select and nibble packing) is large, and eight copies of it
+            // overflow the instruction cache
+            constexpr int kUnrollSteps = DIR ? 1 : 8;
+#pragma unroll kUnrollSteps
             for (int u = 0; u < 8; u++) {
                 const int s = 8 * b + u;
                 const int i = s - g + 1;
+                uint32_t dw[(K + 7) / 8];
+                if (DIR) {
+#pragma unroll
+                    for (int k = 0; k < (K + 7) / 8; k++) dw[k] = 0u;
+                }
                 int32_t hg_up = __shfl_up_sync(FULL, hg_bot, 1, L);
                 int32_t e_up = __shfl_up_sync(FULL, e_bot, 1, L);
                 int32_t cm_up = 0;
@@ -262,8 +266,7 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
                         uint32_t src = pG ? 1u : (pF ? 2u : 3u);
                         if (LOCAL && h <= 0) { h = 0; src = 0u; }
                         const uint32_t nib = src | (eopen ? 0u : 4u) | (fopen ? 0u : 8u);
-                        const int q = u * K + r;          // compile-time after unrolling
-                        dw[q >> 3] |= nib << (4 * (q & 7));
+                        dw[r >> 3] |= nib << (4 * (r & 7));
                     }
                     F[r] = f;
                     HG[r] = PROF ? add_fma(h, S.GO, one) : h + S.GO;
@@ -324,12 +327,9 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
                     }
                 }
                 if (DIR && b < nblk) {
-                    // words whose last nibble was produced in this step are complete
 #pragma unroll
-                    for (int k = 0; k < K; k++) {
-                        if ((8 * k + 7) / K == u)
-                            A.arena[aoff + ((uint64_t)b * K + k) * L + g] = dw[k];
-                    }
+                    for (int k = 0; k < (K + 7) / 8; k++)
+                        A.arena[aoff + ((uint64_t)s * ((K + 7) / 8) + k) * L + g] = dw[k];
                 }
             }
         }

@@ -163,14 +163,14 @@ template <int C> void launch_fill(const FillLaunch& fl);
 template <int C> int fill_blocks_per_sm(int kind, int mode);   // resident 128-thread blocks per SM
 
 // direction-bit layout shared by the wavefront kernels and the traceback:
-// a job's bits are blocks of 8 wavefront steps; in a block, lane g of the
-// group stores K words, word w of lane g at ((block*K + w) * L + g); nibble q =
-// step_in_block*K + r of lane g lives in word q/8, bits 4*(q%8).
+// at wavefront step s lane g of the group stores KW = ceil(K/8) words, word w
+// at ((s*KW + w) * L + g); the nibble of its row r is in word r/8, bits
+// 4*(r%8).  Steps are counted in whole blocks of 8.
 // A nibble: bits 0-1 source of H (0 stop, 1 diagonal, 2 F/deletion,
 // 3 E/insertion), bit 2 E extends, bit 3 F extends.
 __host__ __device__ inline uint64_t dir_words(int L, int K, int w) {
     uint64_t blocks = (uint64_t)(w + L - 1 + 7) / 8;
-    return blocks * (uint64_t)K * (uint64_t)L;
+    return blocks * 8 * (uint64_t)((K + 7) / 8) * (uint64_t)L;
 }
 
 }  // namespace sa

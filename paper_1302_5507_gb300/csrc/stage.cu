@@ -437,11 +437,9 @@ __device__ __forceinline__ uint32_t nibble_at(const uint32_t* __restrict__ arena
                                               int L, int K, int pad, int i, int j) {
     const int idx = j - 1 + pad;
     const int g = idx / K, r = idx - g * K;
-    const int s = i - 1 + g;
-    const int b = s >> 3, u = s & 7;
-    const int q = u * K + r;
-    const uint32_t word = arena[off + ((uint64_t)b * K + (q >> 3)) * L + g];
-    return (word >> (4 * (q & 7))) & 15u;
+    const int s = i - 1 + g;                 // the step at which lane g computed column i
+    const uint32_t word = arena[off + ((uint64_t)s * ((K + 7) / 8) + (r >> 3)) * L + g];
+    return (word >> (4 * (r & 7))) & 15u;
 }
 
 __device__ __forceinline__ uint32_t band_nibble(const uint32_t* __restrict__ arena, uint64_t base,
