@@ -491,6 +491,11 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
                 ba.arena = ws.band.as<uint32_t>() + bl.base[k];
                 ba.warp_stride = bl.warp_stride[k];
                 ba.sc = sc;
+                ba.state = ws.state.as<JobState>();
+                ba.tmp_ops = ws.tmp_ops.as<uint32_t>();
+                ba.tmp_stride = tmp_stride;
+                ba.tb = ws.tb.as<TbOut>();
+                ba.err_job = &dp->st.bad_walk;
                 if (ba.count) {
                     launch_band(band_cls(k), ba, st);
                     launches++;

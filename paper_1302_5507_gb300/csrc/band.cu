@@ -18,8 +18,11 @@
 // Rows whose band starts right of column 0 (all but the first few) take a copy
 // of the row loop without the border tests.  Nibble words are stored
 // interleaved by lane (word w of row j of the job in lane t at ((j-1)*W + w)*32
-// + t of its warp's region), so the stores of a warp are coalesced.
+// + t of its warp's region), so the stores of a warp are coalesced.  The same
+// thread then walks its nibbles from (i*, j*): they were written moments before
+// and are read back from L2.
 #include "kernels.h"
+#include "walk.cuh"
 
 namespace sa {
 
@@ -131,6 +134,22 @@ __global__ void __launch_bounds__(128) k_band(BandArgs A) {
 #pragma unroll
         for (int w = 0; w < W; w++) out[((uint64_t)(j - 1) * W + w) * 32] = words[w];
     }
+
+    const JobState st = A.state[job];
+    auto nib = [&](int ii, int jj, bool* bad) -> uint32_t {
+        const int k = ii - jj - dlo;
+        if (k < 0 || k >= B) { *bad = true; return 0u; }
+        const uint32_t word = out[((uint64_t)(jj - 1) * W + (k >> 3)) * 32];
+        return (word >> (4 * (k & 7))) & 15u;
+    };
+    const WalkEnd e = walk_nibbles(st.i_star, st.j_star, st.i_star, rows, MODE, nib,
+                                   A.tmp_ops + (uint64_t)job * A.tmp_stride, A.tmp_stride);
+    TbOut t;
+    t.n_rev = e.n_rev;
+    t.read_begin = e.bad ? 0 : e.j;
+    t.ref_begin_rel = e.bad ? 0 : e.i;
+    A.tb[job] = t;
+    if (e.bad) atomicMin(A.err_job, job);
 }
 
 }  // namespace

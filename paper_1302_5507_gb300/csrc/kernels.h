@@ -15,6 +15,12 @@ struct PlanStats {                 // filled by the plan kernel (device)
     unsigned long long bad_ref_pos;
 };
 
+struct TbOut {                     // traceback result of one job
+    int32_t n_rev;                 // ops written (reverse order) to the temporary slot
+    int32_t read_begin;            // 0-based
+    int32_t ref_begin_rel;         // 0-based, relative to the job's window start
+};
+
 struct BandArgs {                  // banded direction pass of one class
     const uint32_t* ref;
     int64_t ref_len;
@@ -27,6 +33,12 @@ struct BandArgs {                  // banded direction pass of one class
     uint32_t* arena;               // this class's region
     uint64_t warp_stride;          // words per 32 list entries (max_n * B/8 * 32)
     Score sc;
+    // the walk from the best cell runs in the same thread right after the pass
+    const JobState* state;
+    uint32_t* tmp_ops;             // reversed ops, tmp_stride words per job
+    uint32_t tmp_stride;
+    TbOut* tb;
+    unsigned* err_job;             // smallest job whose walk failed (internal error)
 };
 
 struct BandLayout {                // where the traceback finds band nibbles
@@ -35,11 +47,7 @@ struct BandLayout {                // where the traceback finds band nibbles
     uint64_t warp_stride[kNumBand];
 };
 
-struct TbOut {                     // traceback result of one job
-    int32_t n_rev;                 // ops written (reverse order) to the temporary slot
-    int32_t read_begin;            // 0-based
-    int32_t ref_begin_rel;         // 0-based, relative to the job's window start
-};
+
 
 void launch_pack_ref(const uint8_t* ascii, uint64_t len, uint64_t base_off, uint32_t* words,
                      unsigned long long* bad_pos, cudaStream_t st);

@@ -12,6 +12,7 @@
 #include <cstdio>
 
 #include "kernels.h"
+#include "walk.cuh"
 
 namespace sa {
 
@@ -116,10 +117,16 @@ __global__ void k_plan_scan(const uint32_t* __restrict__ hist, uint32_t* __restr
 __global__ void k_plan_scatter(const uint16_t* __restrict__ key, uint32_t n_jobs,
                                const uint32_t* __restrict__ key_off, uint32_t* __restrict__ cursor,
                                uint32_t* __restrict__ order) {
+    // lanes with the same key take their slots with one atomic per key and warp
     const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n_jobs) return;
-    const int k = key[j];
-    order[key_off[k] + atomicAdd(&cursor[k], 1u)] = j;
+    const int lane = threadIdx.x & 31;
+    const int k = j < n_jobs ? (int)key[j] : -1;
+    const unsigned same = __match_any_sync(0xffffffffu, k);
+    const int leader = __ffs(same) - 1;
+    uint32_t base = 0;
+    if (lane == leader && k >= 0) base = atomicAdd(&cursor[k], (uint32_t)__popc(same));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (k >= 0) order[key_off[k] + base + (uint32_t)__popc(same & ((1u << lane) - 1u))] = j;
 }
 
 void launch_plan(const sa_job* jobs, uint32_t n_jobs, uint64_t reads_len, int64_t ref_len,
@@ -160,33 +167,37 @@ void launch_collect_overflow(const uint32_t* order, uint32_t n_pos, const JobSta
 }
 
 // ---------------------------------------------------------------------------
-// read packing: one warp per job, one lane per output word
+// read packing: one warp per job; the lanes read 32 consecutive bases at a time
+// (coalesced) and two OR-reductions over half-warps form two 16-base words
 
 __global__ void k_pack_reads(const sa_job* __restrict__ jobs, uint32_t n_jobs,
                              const uint8_t* __restrict__ reads, uint32_t* __restrict__ rpack,
                              uint32_t rw, unsigned* bad_job) {
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (warp >= n_jobs) return;
+    if (warp >= n_jobs) return;              // whole warps
     const sa_job J = jobs[warp];
     const uint32_t n = J.read_len;
     const bool rc = (J.flags & SA_RC) != 0u;
     const uint8_t* r = reads + J.read_off;
     uint32_t* out = rpack + (size_t)warp * rw;
     bool bad = false;
-    for (uint32_t wi = lane; wi * 16 < n; wi += 32) {
-        uint32_t v = 0;
-        for (int k = 0; k < 16; k++) {
-            const uint32_t p = wi * 16 + k;
-            if (p >= n) break;
-            int c = base_code(rc ? r[n - 1 - p] : r[p]);
-            if (c < 0) { bad = true; c = 0; }
-            if (rc) c = 3 - c;   // complement: A<->T, C<->G
-            v |= (uint32_t)c << (2 * k);
+    for (uint32_t b = 0; b < n; b += 32) {
+        const uint32_t p = b + (uint32_t)lane;
+        uint32_t c = 0;
+        if (p < n) {
+            int cc = base_code(rc ? r[n - 1 - p] : r[p]);
+            if (cc < 0) { bad = true; cc = 0; }
+            if (rc) cc = 3 - cc;             // complement: A<->T, C<->G
+            c = (uint32_t)cc;
         }
-        out[wi] = v;
+        const uint32_t v = c << (2 * (lane & 15));
+        const uint32_t lo = __reduce_or_sync(0xffffffffu, lane < 16 ? v : 0u);
+        const uint32_t hi = __reduce_or_sync(0xffffffffu, lane < 16 ? 0u : v);
+        if (lane == 0) out[b / 16] = lo;
+        if (lane == 1 && b + 16 < n) out[b / 16 + 1] = hi;
     }
-    if (bad) atomicMin(bad_job, warp);
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicMin(bad_job, warp);
 }
 
 void launch_pack_reads(const sa_job* jobs, uint32_t n_jobs, const uint8_t* reads, uint32_t* rpack,
@@ -474,7 +485,8 @@ __global__ void k_traceback(const sa_job* __restrict__ jobs, uint32_t job_begin,
         tb[job] = out;
         return;
     }
-    if (banded ? wave != 0 : (R.w <= 0 || R.wave != wave)) return;
+    // banded jobs were walked by their band pass
+    if (banded || R.w <= 0 || R.wave != wave) return;
     const sa_job J = jobs[job];
     const JobState st = state[job];
     int si = R.start_i, sj = R.start_j;
@@ -497,22 +509,7 @@ __global__ void k_traceback(const sa_job* __restrict__ jobs, uint32_t job_begin,
         sj = st.j_star;
     }
     const int imax_walk = banded ? st.i_star : R.w;
-    uint32_t* ops = tmp_ops + (uint64_t)job * tmp_stride;
-    int nrev = 0;
-    uint32_t cur_op = 15u, cur_len = 0;
-    auto emit = [&](uint32_t op, uint32_t len) {
-        if (op == cur_op) { cur_len += len; return; }
-        if (cur_len) ops[nrev++] = (cur_len << 4) | cur_op;
-        cur_op = op;
-        cur_len = len;
-    };
-    int i = si, j = sj;
-    int state_ = 0;   // 0 H, 1 E (insertion), 2 F (deletion)
     const uint64_t off = R.off;
-    // a valid walk emits at most w + rows ops and enters at most as many gap
-    // runs (one extra iteration each); anything longer is an internal error
-    int budget = 2 * (imax_walk + R.rows) + 4;
-    bool bad = (i < 0 || j < 0 || i > imax_walk || j > R.rows);
     auto nib_at = [&](int ii, int jj, bool* out_bad) -> uint32_t {
         if (banded) {
             const int k = ii - jj - R.d_lo;
@@ -521,35 +518,9 @@ __global__ void k_traceback(const sa_job* __restrict__ jobs, uint32_t job_begin,
         }
         return nibble_at(arena, off, L, K, pad, ii, jj);
     };
-    while (!bad) {
-        if (--budget < 0) { bad = true; break; }
-        if (state_ == 0) {
-            if (i == 0 || j == 0) break;
-            const uint32_t nib = nib_at(i, j, &bad);
-            if (bad) break;
-            const uint32_t src = nib & 3u;
-            if (src == 0u) break;
-            if (src == 1u) { emit(0u, 1u); i--; j--; }
-            else if (src == 2u) state_ = 2;
-            else state_ = 1;
-        } else if (state_ == 2) {
-            if (i < 1 || j < 1) { bad = true; break; }
-            const uint32_t nib = nib_at(i, j, &bad);
-            if (bad) break;
-            emit(2u, 1u);
-            i--;
-            state_ = (nib & 8u) ? 2 : 0;
-        } else {
-            if (i < 1 || j < 1) { bad = true; break; }
-            const uint32_t nib = nib_at(i, j, &bad);
-            if (bad) break;
-            emit(1u, 1u);
-            j--;
-            state_ = (nib & 4u) ? 1 : 0;
-        }
-        if (nrev >= (int)tmp_stride - 1) { bad = true; break; }
-    }
-    if (bad) {
+    const WalkEnd e = walk_nibbles(si, sj, imax_walk, R.rows, mode, nib_at,
+                                   tmp_ops + (uint64_t)job * tmp_stride, tmp_stride);
+    if (e.bad) {
         atomicMin(err_job, job);
         out.n_rev = 0;
         out.read_begin = 0;
@@ -557,11 +528,9 @@ __global__ void k_traceback(const sa_job* __restrict__ jobs, uint32_t job_begin,
         tb[job] = out;
         return;
     }
-    if (mode == SA_GLOCAL && j > 0) { emit(1u, (uint32_t)j); j = 0; }
-    if (cur_len) ops[nrev++] = (cur_len << 4) | cur_op;
-    out.n_rev = nrev;
-    out.read_begin = j;
-    out.ref_begin_rel = banded ? i : (R.i_lo - 1) + i;
+    out.n_rev = e.n_rev;
+    out.read_begin = e.j;
+    out.ref_begin_rel = banded ? e.i : (R.i_lo - 1) + e.i;
     tb[job] = out;
 }
 
