@@ -204,6 +204,33 @@ int sa_align_batch_noalloc(sa_reference* ref, const sa_params* params, const sa_
 /* Statistics of the last sa_align_batch / sa_align_batch_dev call on ref. */
 int sa_last_stats(const sa_reference* ref, sa_stats* out);
 
+/* Tuned plan (SOAP3-dp classifies candidates by complexity before the DP,
+ * Methods section 3; here the bucketing and lane-group choice are tuned on the
+ * device).  Every reference holds a plan: the lane-group configuration serving
+ * each read length and the width of each configuration's score pass.  The
+ * default maps n to the smallest configuration with L*K >= n and picks 16-bit
+ * where no job of a bucket can overflow.
+ *
+ * sa_tune times the score pass (CUDA events, second of two runs, CIGAR off) of
+ * the sample `jobs` (host buffers, same layout as sa_align_batch; up to 65,536
+ * jobs per length class, classes with fewer than 256 jobs are skipped) under
+ * each candidate -- the default configuration, the next larger K with the same
+ * lane count, the first 32-lane configuration that covers the class; 16- and
+ * 32-bit where LOCAL 16-bit applies -- and keeps the fastest in the plan.
+ * *classes_tuned (nullable) receives the number of length classes tuned.
+ * Results never depend on the plan.  It must not run concurrently with other
+ * calls on the same reference or with a server on it.
+ *
+ * sa_plan_get copies the plan (a fixed-size byte string, *needed bytes) to
+ * out[size] (SA_EOVERFLOW if size is too small); sa_plan_set installs one
+ * (SA_EINVAL if it is malformed or maps a read length to a configuration with
+ * fewer rows); plan == NULL restores the default.  A saved plan is the plan
+ * cache between runs on the same GPU type. */
+int sa_tune(sa_reference* ref, const sa_params* params, const sa_job* jobs, uint32_t n_jobs,
+            const char* reads, uint64_t reads_len, uint32_t* classes_tuned);
+int sa_plan_get(const sa_reference* ref, void* out, uint64_t size, uint64_t* needed);
+int sa_plan_set(sa_reference* ref, const void* plan, uint64_t size);
+
 /* Serving: a background thread admits submitted requests while device memory
  * (hbm_budget bytes, 0 = 80% of free memory) and in-flight slots allow, and runs
  * them on a pool of streams, so requests overlap on the device.  The reference

@@ -92,11 +92,14 @@ def lib():
         L.sa_submit.argtypes = [_VP, _VP, _U32, _VP, _U64, ctypes.POINTER(_U64)]
         L.sa_poll.argtypes = [_VP, _U64, ctypes.c_int, _VP, _VP, _U64, ctypes.POINTER(_U64)]
         L.sa_server_destroy.argtypes = [_VP]
+        L.sa_tune.argtypes = [_VP, ctypes.POINTER(sa_params), _VP, _U32, _VP, _U64, ctypes.POINTER(_U32)]
+        L.sa_plan_get.argtypes = [_VP, _VP, _U64, ctypes.POINTER(_U64)]
+        L.sa_plan_set.argtypes = [_VP, _VP, _U64]
         L.sa_last_error.restype = ctypes.c_char_p
         for name in ("sa_create_reference", "sa_destroy_reference", "sa_align_batch",
                      "sa_align_batch_dev", "sa_align_batch_noalloc", "sa_last_stats",
                      "sa_server_create", "sa_submit",
-                     "sa_poll", "sa_server_destroy"):
+                     "sa_poll", "sa_server_destroy", "sa_tune", "sa_plan_get", "sa_plan_set"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -248,6 +251,32 @@ class Reference:
 
     def stats(self) -> dict:
         return sa_last_stats(self.h).as_dict()
+
+    def tune(self, jobs: np.ndarray, reads: np.ndarray, params: sa_params | None = None) -> int:
+        """sa_tune on a sample of jobs; returns the number of length classes tuned."""
+        params = params or make_params()
+        jobs = np.ascontiguousarray(jobs, JOB_DTYPE)
+        reads = np.ascontiguousarray(reads, np.uint8)
+        k = _U32()
+        _check(lib().sa_tune(self.h, ctypes.byref(params), _ptr(jobs), len(jobs), _ptr(reads), reads.size,
+                             ctypes.byref(k)))
+        return int(k.value)
+
+    def plan(self) -> bytes:
+        """The reference's plan as bytes (sa_plan_get)."""
+        need = _U64()
+        lib().sa_plan_get(self.h, None, 0, ctypes.byref(need))
+        buf = (ctypes.c_uint8 * need.value)()
+        _check(lib().sa_plan_get(self.h, buf, need.value, ctypes.byref(need)))
+        return bytes(buf)
+
+    def set_plan(self, plan: bytes | None) -> None:
+        """Install a plan (sa_plan_set); None restores the default."""
+        if plan is None:
+            _check(lib().sa_plan_set(self.h, None, 0))
+            return
+        buf = (ctypes.c_uint8 * len(plan)).from_buffer_copy(plan)
+        _check(lib().sa_plan_set(self.h, buf, len(plan)))
 
     def align(self, jobs: np.ndarray, reads: np.ndarray, params: sa_params | None = None,
               out: np.ndarray | None = None, cigar: np.ndarray | None = None, stream=None):

@@ -121,13 +121,15 @@ struct Workspace {
     }
 };
 
-// What a computation needs: the reference and a workspace of its own.
+// What a computation needs: the reference, its plan and a workspace of its own.
 struct Ctx {
     const uint32_t* d_words;
     uint64_t len;
     int num_sms;
     Workspace* ws;
     sa_stats* last;
+    const Plan* plan;
+    const uint8_t* d_plan_cfg;    // device copy of plan->cfg
 };
 
 }  // namespace
@@ -141,7 +143,9 @@ struct sa_reference {
     std::mutex mu;
     Workspace ws;
     sa_stats last{};
-    Ctx ctx() { return Ctx{d_words, len, num_sms, &ws, &last}; }
+    Plan plan;
+    uint8_t* d_plan_cfg = nullptr;
+    Ctx ctx() { return Ctx{d_words, len, num_sms, &ws, &last, &plan, d_plan_cfg}; }
 };
 
 // ---------------------------------------------------------------------------
@@ -269,7 +273,8 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
     TRY(ws.counters.ensure(256 * sizeof(uint32_t), "counters"));
     CU(cudaMemsetAsync(ws.counters.p, 0, 256 * sizeof(uint32_t), st));
     int counter_next = 0;
-    launch_plan(d_jobs, n_jobs, reads_len, (int64_t)X.len, ws.key.as<uint16_t>(), dp->hist, &dp->st, st);
+    launch_plan(d_jobs, n_jobs, reads_len, (int64_t)X.len, X.d_plan_cfg, ws.key.as<uint16_t>(), dp->hist,
+                &dp->st, st);
     launches++;
     CU(cudaGetLastError());
     trace("plan");
@@ -316,14 +321,17 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
         if (bps < 1) bps = 1;
         return X.num_sms * bps;
     };
-    // 16-bit pairs per length bucket: when asked for (width 16), or by default when
-    // no job of the bucket can reach the 16-bit threshold (a * rows + beta < 1024 - a)
+    // 16-bit pairs per length bucket: when asked for (width 16 in the parameters or
+    // the plan), or by default when no job of the bucket can reach the 16-bit
+    // threshold (a * rows + beta < 1024 - a)
     bool w16[kNumCfg] = {};
     bool any16 = false;
     for (int c = 0; c < kNumCfg; c++) {
         const int64_t rows = (int64_t)cfg_L(c) * cfg_K(c);
         const bool safe = (int64_t)P->sc.match * (rows + 1) + P->sc.gap_open + P->sc.gap_extend < 1024;
-        w16[c] = !plain && cfg_count[c] && use16(P) && (P->width == 16 || safe);
+        const int pw = X.plan ? X.plan->width[c] : 0;
+        const bool want16 = P->width == 16 || (P->width == 0 && (pw == 16 || (pw == 0 && safe)));
+        w16[c] = !plain && cfg_count[c] && use16(P) && want16;
         any16 = any16 || w16[c];
     }
     int max_groups = 1, max_warps16 = 1;
@@ -449,7 +457,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             TRY(ws.blists.ensure((size_t)n_jobs * kNumBand * 4, "band lists"));
             uint32_t* lists[kNumBand];
             for (int k = 0; k < kNumBand; k++) lists[k] = ws.blists.as<uint32_t>() + (size_t)k * n_jobs;
-            launch_rect_plan(d_jobs, ws.order.as<uint32_t>(), n_jobs, ws.state.as<JobState>(), sc,
+            launch_rect_plan(d_jobs, ws.order.as<uint32_t>(), n_jobs, dp->cfg_begin, ws.state.as<JobState>(), sc,
                              min_score, 1, ws.rect.as<Rect>(), ws.sizes.as<uint64_t>(), lists,
                              dp->cls_count, st);
             launch_scan_u64(ws.sizes.as<uint64_t>(), n_jobs, ws.offs.as<uint64_t>(),
@@ -790,7 +798,8 @@ int run_batch(sa_server* S, sa_server::Slot* slot, std::vector<std::shared_ptr<R
     }
     Workspace& ws = slot->ws;
     const cudaStream_t st = slot->stream;
-    Ctx X{S->ref->d_words, S->ref->len, S->ref->num_sms, &ws, &slot->last};
+    Ctx X{S->ref->d_words, S->ref->len, S->ref->num_sms, &ws, &slot->last, &S->ref->plan,
+          S->ref->d_plan_cfg};
     uint64_t used = 0;
     if (nj) {
         TRY(ws.jobs.ensure(nj * sizeof(sa_job), "jobs"));
@@ -923,6 +932,9 @@ int sa_create_reference(const char* acgt, uint64_t len, int device, sa_reference
         CU(cudaStreamCreateWithFlags(&R->own, cudaStreamNonBlocking));
         const uint64_t words = (len + 15) / 16 + kRefFrontPad + kRefTailPad;
         CU(cudaMalloc(&R->d_words, words * 4));
+        default_plan(&R->plan);
+        CU(cudaMalloc(&R->d_plan_cfg, sizeof(R->plan.cfg)));
+        CU(cudaMemcpy(R->d_plan_cfg, R->plan.cfg, sizeof(R->plan.cfg), cudaMemcpyHostToDevice));
         CU(cudaMemsetAsync(R->d_words, 0, words * 4, R->own));
         const uint64_t chunk = 256ull << 20;  // multiple of 16
         uint8_t* stage = nullptr;
@@ -970,6 +982,7 @@ int sa_destroy_reference(sa_reference* R) {
             cudaStreamSynchronize(R->own);
             R->ws.release();
             cudaFree(R->d_words);
+            cudaFree(R->d_plan_cfg);
             cudaStreamDestroy(R->own);
         }
         delete R;
@@ -1022,6 +1035,150 @@ int sa_align_batch(sa_reference* R, const sa_params* P, const sa_job* jobs, uint
         Ctx X = R->ctx();
         return run_host(X, P, sc, jobs, n_jobs, reads, reads_len, out, cigar, cigar_cap, cigar_used,
                         pick_stream(R, stream));
+    } catch (...) {
+        return fail(SA_ENOMEM, "unexpected host exception");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// tuned plan
+
+namespace {
+
+constexpr uint32_t kPlanMagic = 0x4C504153u;   // "SAPL"
+constexpr uint32_t kPlanVersion = 1u;
+constexpr uint64_t kPlanBytes = 8 + sizeof(Plan::cfg) + sizeof(Plan::width);
+
+int upload_plan(sa_reference* R) {
+    CU(cudaMemcpy(R->d_plan_cfg, R->plan.cfg, sizeof(R->plan.cfg), cudaMemcpyHostToDevice));
+    return SA_OK;
+}
+
+// Score-pass time (ms) of `jobs` under `trial`, second of two runs.
+int time_trial(sa_reference* R, const sa_params* P, const Score& sc, const Plan& trial, uint8_t* d_cfg,
+               const sa_job* jobs, uint32_t n, const char* reads, uint64_t reads_len, float* ms) {
+    CU(cudaMemcpy(d_cfg, trial.cfg, sizeof(trial.cfg), cudaMemcpyHostToDevice));
+    sa_params q = *P;
+    q.want_cigar = 0;
+    q.profile = 1;
+    q.width = 0;
+    Ctx X{R->d_words, R->len, R->num_sms, &R->ws, &R->last, &trial, d_cfg};
+    std::vector<sa_result> out(n);
+    for (int rep = 0; rep < 2; rep++)
+        TRY(run_host(X, &q, sc, jobs, n, reads, reads_len, out.data(), nullptr, 0, nullptr, R->own));
+    *ms = R->last.ms_fill + R->last.ms_rerun;
+    return SA_OK;
+}
+
+}  // namespace
+
+int sa_tune(sa_reference* R, const sa_params* P, const sa_job* jobs, uint32_t n_jobs, const char* reads,
+            uint64_t reads_len, uint32_t* classes_tuned) {
+    try {
+        g_err[0] = 0;
+        if (!R) return fail(SA_EINVAL, "reference is NULL");
+        Score sc;
+        TRY(check_params(P, &sc));
+        if (n_jobs && (!jobs || !reads)) return fail(SA_EINVAL, "NULL jobs or reads");
+        if (classes_tuned) *classes_tuned = 0;
+        std::lock_guard<std::mutex> lk(R->mu);
+        CU(cudaSetDevice(R->device));
+        uint8_t* d_cfg = nullptr;
+        CU(cudaMalloc(&d_cfg, sizeof(Plan::cfg)));
+        struct Free { uint8_t* p; ~Free() { cudaFree(p); } } guard{d_cfg};
+        const bool local16 = P->mode == SA_LOCAL && use16(P);
+        uint32_t tuned = 0;
+        for (int c0 = 0; c0 < kNumCfg; c0++) {
+            // the length class that the default plan gives to configuration c0
+            std::vector<uint32_t> idx;
+            for (uint32_t k = 0; k < n_jobs && idx.size() < 65536; k++) {
+                const uint32_t n = jobs[k].read_len;
+                if (n >= 1 && n <= SA_MAX_READ && cfg_for_rows((int)n) == c0) idx.push_back(k);
+            }
+            if (idx.size() < 256) continue;
+            std::vector<sa_job> sj(idx.size());
+            std::vector<char> sr;
+            for (size_t t = 0; t < idx.size(); t++) {
+                sj[t] = jobs[idx[t]];
+                if (sj[t].read_off + sj[t].read_len > reads_len)
+                    return fail(SA_EINVAL, "job %u: read outside the reads buffer", idx[t]);
+                sj[t].read_off = sr.size();
+                sr.insert(sr.end(), reads + jobs[idx[t]].read_off, reads + jobs[idx[t]].read_off + sj[t].read_len);
+            }
+            // candidates: c0, the next K with the same lane count, the first 32-lane
+            // configuration that covers the class; 16- and 32-bit where 16-bit applies
+            std::vector<int> cands{c0};
+            if (c0 + 1 < kNumCfg && cfg_L(c0 + 1) == cfg_L(c0)) cands.push_back(c0 + 1);
+            if (cfg_L(c0) == 8)
+                for (int c = 0; c < kNumCfg; c++)
+                    if (cfg_L(c) == 32 && cfg_L(c) * cfg_K(c) >= cfg_L(c0) * cfg_K(c0)) { cands.push_back(c); break; }
+            std::vector<int> widths = local16 ? std::vector<int>{16, 32} : std::vector<int>{32};
+            float best_ms = 0.f;
+            int best_c = c0, best_w = 0;
+            bool first = true;
+            for (int c : cands) {
+                for (int w : widths) {
+                    Plan trial = R->plan;
+                    for (int n = 1; n <= SA_MAX_READ; n++)
+                        if (cfg_for_rows(n) == c0) trial.cfg[n] = (uint8_t)c;
+                    trial.width[c] = (int8_t)w;
+                    float ms = 0.f;
+                    TRY(time_trial(R, P, sc, trial, d_cfg, sj.data(), (uint32_t)sj.size(), sr.data(), sr.size(), &ms));
+                    if (first || ms < best_ms) { best_ms = ms; best_c = c; best_w = w; first = false; }
+                }
+            }
+            for (int n = 1; n <= SA_MAX_READ; n++)
+                if (cfg_for_rows(n) == c0) R->plan.cfg[n] = (uint8_t)best_c;
+            R->plan.width[best_c] = (int8_t)(local16 ? best_w : 0);
+            tuned++;
+        }
+        TRY(upload_plan(R));
+        if (classes_tuned) *classes_tuned = tuned;
+        return SA_OK;
+    } catch (...) {
+        return fail(SA_ENOMEM, "unexpected host exception");
+    }
+}
+
+int sa_plan_get(const sa_reference* R, void* out, uint64_t size, uint64_t* needed) {
+    if (!R) return fail(SA_EINVAL, "reference is NULL");
+    if (needed) *needed = kPlanBytes;
+    if (!out || size < kPlanBytes) return fail(SA_EOVERFLOW, "the plan needs %llu bytes", (unsigned long long)kPlanBytes);
+    uint8_t* o = static_cast<uint8_t*>(out);
+    std::memcpy(o, &kPlanMagic, 4);
+    std::memcpy(o + 4, &kPlanVersion, 4);
+    std::memcpy(o + 8, R->plan.cfg, sizeof(Plan::cfg));
+    std::memcpy(o + 8 + sizeof(Plan::cfg), R->plan.width, sizeof(Plan::width));
+    return SA_OK;
+}
+
+int sa_plan_set(sa_reference* R, const void* plan, uint64_t size) {
+    try {
+        g_err[0] = 0;
+        if (!R) return fail(SA_EINVAL, "reference is NULL");
+        if (!plan) {
+            std::lock_guard<std::mutex> lk(R->mu);
+            CU(cudaSetDevice(R->device));
+            default_plan(&R->plan);
+            return upload_plan(R);
+        }
+        if (size != kPlanBytes) return fail(SA_EINVAL, "a plan has %llu bytes, got %llu",
+                                            (unsigned long long)kPlanBytes, (unsigned long long)size);
+        const uint8_t* b = static_cast<const uint8_t*>(plan);
+        uint32_t magic = 0, version = 0;
+        std::memcpy(&magic, b, 4);
+        std::memcpy(&version, b + 4, 4);
+        if (magic != kPlanMagic || version != kPlanVersion) return fail(SA_EINVAL, "not a plan of this version");
+        Plan p;
+        std::memcpy(p.cfg, b + 8, sizeof(Plan::cfg));
+        std::memcpy(p.width, b + 8 + sizeof(Plan::cfg), sizeof(Plan::width));
+        p.cfg[0] = (uint8_t)cfg_for_rows(1);
+        if (!plan_valid(p)) return fail(SA_EINVAL, "invalid plan: a read length mapped to a configuration "
+                                        "with fewer rows, or a width other than 0, 16, 32");
+        std::lock_guard<std::mutex> lk(R->mu);
+        CU(cudaSetDevice(R->device));
+        R->plan = p;
+        return upload_plan(R);
     } catch (...) {
         return fail(SA_ENOMEM, "unexpected host exception");
     }

@@ -52,7 +52,7 @@ struct BandLayout {                // where the traceback finds band nibbles
 void launch_pack_ref(const uint8_t* ascii, uint64_t len, uint64_t base_off, uint32_t* words,
                      unsigned long long* bad_pos, cudaStream_t st);
 void launch_plan(const sa_job* jobs, uint32_t n_jobs, uint64_t reads_len, int64_t ref_len,
-                 uint16_t* key, uint32_t* hist, PlanStats* stats, cudaStream_t st);
+                 const uint8_t* plan_cfg, uint16_t* key, uint32_t* hist, PlanStats* stats, cudaStream_t st);
 void launch_plan_order(const uint16_t* key, uint32_t n_jobs, const uint32_t* hist,
                        uint32_t* key_off, uint32_t* cursor, uint32_t* order, cudaStream_t st);
 void launch_collect_overflow(const uint32_t* order, uint32_t n_pos, const JobState* state,
@@ -60,7 +60,7 @@ void launch_collect_overflow(const uint32_t* order, uint32_t n_pos, const JobSta
                              cudaStream_t st);
 void launch_pack_reads(const sa_job* jobs, uint32_t n_jobs, const uint8_t* reads, uint32_t* rpack,
                        uint32_t rw, unsigned* bad_job, cudaStream_t st);
-void launch_rect_plan(const sa_job* jobs, const uint32_t* order, uint32_t n_pos,
+void launch_rect_plan(const sa_job* jobs, const uint32_t* order, uint32_t n_pos, const uint32_t* cfg_begin,
                       const JobState* state, const Score& sc, int32_t min_score, int allow_band,
                       Rect* rect, uint64_t* sizes, uint32_t* const* lists, uint32_t* cls_count,
                       cudaStream_t st);

@@ -148,7 +148,7 @@ int run(sa_reference* R, const sa_params* P, const sa_job* d_jobs, uint32_t n_jo
     Ctl* ctl = reinterpret_cast<Ctl*>(base);
     CK(cudaMemsetAsync(ctl, 0, sizeof(Ctl), st));
     CK(cudaMemsetAsync(&ctl->st.bad_job, 0xff, 2 * sizeof(uint32_t), st));
-    sa::launch_plan(d_jobs, n_jobs, reads_len, (int64_t)V.len,
+    sa::launch_plan(d_jobs, n_jobs, reads_len, (int64_t)V.len, nullptr,
                     reinterpret_cast<uint16_t*>(base + off_key), ctl->hist, &ctl->st, st);
     CK(cudaGetLastError());
     sa::PlanStats hs;

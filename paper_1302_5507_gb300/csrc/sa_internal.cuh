@@ -53,6 +53,27 @@ __host__ __device__ inline int cfg_for_rows(int n) {
     return -1;
 }
 
+// The plan: the configuration serving each read length and the width of each
+// configuration's score pass (0: 16-bit where no job of the bucket can reach the
+// overflow threshold, else 32-bit; 16 or 32: that width).  The default maps n
+// to the first configuration with L*K >= n; a tuning run may pick another one
+// (any configuration with L*K >= n is valid for n).
+struct Plan {
+    uint8_t cfg[SA_MAX_READ + 1];      // cfg[0] unused
+    int8_t width[kNumCfg];
+};
+inline void default_plan(Plan* p) {
+    for (int n = 0; n <= SA_MAX_READ; n++) p->cfg[n] = (uint8_t)cfg_for_rows(n < 1 ? 1 : n);
+    for (int c = 0; c < kNumCfg; c++) p->width[c] = 0;
+}
+inline bool plan_valid(const Plan& p) {
+    for (int n = 1; n <= SA_MAX_READ; n++)
+        if (p.cfg[n] >= kNumCfg || cfg_L(p.cfg[n]) * cfg_K(p.cfg[n]) < n) return false;
+    for (int c = 0; c < kNumCfg; c++)
+        if (p.width[c] != 0 && p.width[c] != 16 && p.width[c] != 32) return false;
+    return true;
+}
+
 // Size classes order jobs inside one configuration (largest windows first).
 constexpr int kNumSizeCls = 40;
 __host__ __device__ inline int size_class(uint32_t m) {
@@ -97,7 +118,7 @@ struct Rect {
     int32_t cls;        // kCls*
     int32_t d_lo;
     uint32_t lpos;      // position in its class list
-    int32_t _pad;
+    int32_t cfg;        // lane-group configuration of the job's score pass (its bucket)
 };
 // direction-pass classes: none (no traceback), banded passes of 8/16/32/64
 // diagonals, the wavefront rectangle, and the pure diagonal (an optimal path

@@ -56,8 +56,8 @@ void launch_pack_ref(const uint8_t* ascii, uint64_t len, uint64_t base_off, uint
 // planning
 
 __global__ void k_plan(const sa_job* __restrict__ jobs, uint32_t n_jobs, uint64_t reads_len,
-                       int64_t ref_len, uint16_t* __restrict__ key, uint32_t* __restrict__ hist,
-                       PlanStats* stats) {
+                       int64_t ref_len, const uint8_t* __restrict__ plan_cfg, uint16_t* __restrict__ key,
+                       uint32_t* __restrict__ hist, PlanStats* stats) {
     __shared__ uint32_t sh[kNumKeys];
     for (int k = threadIdx.x; k < kNumKeys; k += blockDim.x) sh[k] = 0;
     __syncthreads();
@@ -75,7 +75,7 @@ __global__ void k_plan(const sa_job* __restrict__ jobs, uint32_t n_jobs, uint64_
             atomicMin(&stats->bad_job, j);
             key[j] = 0;
         } else {
-            const int c = cfg_for_rows((int)n);
+            const int c = plan_cfg ? (int)plan_cfg[n] : cfg_for_rows((int)n);
             const int k = c * kNumSizeCls + (kNumSizeCls - 1 - size_class(m));
             key[j] = (uint16_t)k;
             atomicAdd(&sh[k], 1u);
@@ -130,9 +130,9 @@ __global__ void k_plan_scatter(const uint16_t* __restrict__ key, uint32_t n_jobs
 }
 
 void launch_plan(const sa_job* jobs, uint32_t n_jobs, uint64_t reads_len, int64_t ref_len,
-                 uint16_t* key, uint32_t* hist, PlanStats* stats, cudaStream_t st) {
+                 const uint8_t* plan_cfg, uint16_t* key, uint32_t* hist, PlanStats* stats, cudaStream_t st) {
     if (!n_jobs) return;
-    k_plan<<<(n_jobs + 255) / 256, 256, 0, st>>>(jobs, n_jobs, reads_len, ref_len, key, hist, stats);
+    k_plan<<<(n_jobs + 255) / 256, 256, 0, st>>>(jobs, n_jobs, reads_len, ref_len, plan_cfg, key, hist, stats);
 }
 
 void launch_plan_order(const uint16_t* key, uint32_t n_jobs, const uint32_t* hist,
@@ -223,7 +223,8 @@ struct BandLists { uint32_t* p[kNumBand]; };
 // With e = 0 the bound does not exist and the whole window is used.
 
 __global__ void k_rect_plan(const sa_job* __restrict__ jobs, const uint32_t* __restrict__ order,
-                            uint32_t n_pos, const JobState* __restrict__ state, Score sc,
+                            uint32_t n_pos, const uint32_t* __restrict__ cfg_begin,
+                            const JobState* __restrict__ state, Score sc,
                             int32_t min_score, int allow_band, Rect* __restrict__ rect,
                             uint64_t* __restrict__ sizes, BandLists lists, uint32_t* cls_count) {
     // no early return: the class lists are appended with warp-wide ballots
@@ -241,12 +242,12 @@ __global__ void k_rect_plan(const sa_job* __restrict__ jobs, const uint32_t* __r
     R.cls = kClsNone;
     R.d_lo = 0;
     R.lpos = 0;
-    R._pad = 0;
     int c = 0;
+    while (valid && c + 1 < kNumCfg && cfg_begin[c + 1] <= p) c++;   // the position's bucket
+    R.cfg = c;
     if (valid) {
         const sa_job J = jobs[job];
         const JobState st = state[job];
-        c = cfg_for_rows((int)J.read_len);
         if (!(st.flags & kStEmpty) && st.best >= min_score) {
             const int istar = st.i_star, jstar = st.j_star;
             const int64_t slack = (int64_t)sc.a * jstar - st.best;     // S = a*j* - best >= 0
@@ -305,14 +306,14 @@ __global__ void k_rect_plan(const sa_job* __restrict__ jobs, const uint32_t* __r
     }
 }
 
-void launch_rect_plan(const sa_job* jobs, const uint32_t* order, uint32_t n_pos,
+void launch_rect_plan(const sa_job* jobs, const uint32_t* order, uint32_t n_pos, const uint32_t* cfg_begin,
                       const JobState* state, const Score& sc, int32_t min_score, int allow_band,
                       Rect* rect, uint64_t* sizes, uint32_t* const* lists, uint32_t* cls_count,
                       cudaStream_t st) {
     if (!n_pos) return;
     BandLists bl;
     for (int k = 0; k < kNumBand; k++) bl.p[k] = lists[k];
-    k_rect_plan<<<(n_pos + 255) / 256, 256, 0, st>>>(jobs, order, n_pos, state, sc, min_score,
+    k_rect_plan<<<(n_pos + 255) / 256, 256, 0, st>>>(jobs, order, n_pos, cfg_begin, state, sc, min_score,
                                                       allow_band, rect, sizes, bl, cls_count);
 }
 
@@ -496,7 +497,7 @@ __global__ void k_traceback(const sa_job* __restrict__ jobs, uint32_t job_begin,
         si = st.i_star;
         sj = st.j_star;
     }
-    const int c = cfg_force >= 0 ? cfg_force : cfg_for_rows((int)J.read_len);
+    const int c = cfg_force >= 0 ? cfg_force : R.cfg;
     const int L = cfg_L(c), K = cfg_K(c);
     const int pad = (mode == SA_LOCAL) ? L * K - R.rows : 0;
     // banded jobs walk in window coordinates (start at the best cell, border at
@@ -571,7 +572,7 @@ __global__ void k_plain_rect(const sa_job* __restrict__ jobs, uint32_t j0, uint3
     R.cls = kClsRect;
     R.d_lo = 0;
     R.lpos = 0;
-    R._pad = 0;
+    R.cfg = -1;
     rect[j0 + k] = R;
 }
 

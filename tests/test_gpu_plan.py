@@ -1,0 +1,86 @@
+"""Tuned plan (sa_tune, sa_plan_get/set): results never depend on the plan, a
+plan round-trips through its bytes, and malformed plans are refused."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from oracle.compare import compare
+
+pytestmark = pytest.mark.gpu
+
+N_CFG = 14
+MAX_READ = 1024
+CFG_ROWS = [8 * k for k in (4, 7, 10, 13, 16, 19, 22, 25, 28, 32)] + [32 * k for k in (10, 16, 24, 32)]
+
+
+@pytest.fixture(scope="module")
+def sa():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1302_5507_gb300 as sa
+    return sa
+
+
+def _parity(sa, ref, wl, **kw):
+    jobs = sa.jobs_array(wl.read_off, wl.read_len, wl.flags, wl.ref_pos, wl.win_len)
+    res, cig = ref.align(jobs, wl.reads, sa.make_params(**kw))
+    ores, oops = oracle.align(wl, mode=kw.get("mode", 0))
+    bad = compare(res, cig, ores, oops)
+    assert not bad, "\n".join(bad[:10])
+    return ref.stats()
+
+
+def _plan_bytes(cfg, width):
+    head = np.array([0x4C504153, 1], np.uint32).tobytes()
+    return head + np.asarray(cfg, np.uint8).tobytes() + np.asarray(width, np.int8).tobytes()
+
+
+def test_tune_then_align_matches_the_oracle(sa):
+    sample = workloads.uneven(seed=7, n_jobs=20_000)
+    wl = workloads.uneven(seed=7, n_jobs=2_000, first_item=20_000)    # same genome, other jobs
+    with sa.Reference(sample.ref) as ref:
+        jobs = sa.jobs_array(sample.read_off, sample.read_len, sample.flags, sample.ref_pos, sample.win_len)
+        assert ref.tune(jobs, sample.reads) >= 1
+        plan = ref.plan()
+        cfg = np.frombuffer(plan[8:8 + MAX_READ + 1], np.uint8)
+        assert all(CFG_ROWS[cfg[n]] >= n for n in range(1, MAX_READ + 1))
+        for mode in (0, 1):
+            _parity(sa, ref, wl, mode=mode)
+
+
+def test_plan_round_trip_and_explicit_plans(sa):
+    wl = workloads.small(61, 1500, n_range=(1, 300), m_range=(1, 400), alphabet=4)
+    with sa.Reference(wl.ref) as ref:
+        default = ref.plan()
+        assert len(default) == 8 + MAX_READ + 1 + N_CFG
+        ref.set_plan(default)
+        assert ref.plan() == default
+        # every length on the 32-lane configurations, 32-bit everywhere
+        cfg = [10] + [next(c for c in range(10, N_CFG) if CFG_ROWS[c] >= n) for n in range(1, MAX_READ + 1)]
+        ref.set_plan(_plan_bytes(cfg, [32] * N_CFG))
+        st = _parity(sa, ref, wl)
+        assert st["jobs16"] == 0
+        # 16-bit forced on every configuration
+        ref.set_plan(_plan_bytes(cfg, [16] * N_CFG))
+        st = _parity(sa, ref, wl)
+        assert st["jobs16"] == wl.n_jobs
+        ref.set_plan(None)
+        assert ref.plan() == default
+
+
+def test_malformed_plans_are_refused(sa):
+    wl = workloads.small(62, 10)
+    with sa.Reference(wl.ref) as ref:
+        default = bytearray(ref.plan())
+        too_small = bytearray(default)
+        too_small[8 + 200] = 0                  # 200 bases on 8 x 4 = 32 rows
+        for bad in (bytes(too_small), bytes(default[:-1]), b"XXXX" + bytes(default[4:])):
+            with pytest.raises(sa.SAError) as e:
+                ref.set_plan(bad)
+            assert e.value.code == sa.SA_EINVAL
+        bad_width = bytearray(default)
+        bad_width[-1] = 8
+        with pytest.raises(sa.SAError):
+            ref.set_plan(bytes(bad_width))
+        assert ref.plan() == bytes(default)
