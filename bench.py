@@ -496,6 +496,17 @@ def run_config(args):
         with sa.Reference(wl.ref) as ref:
             line = device_line(sa, ref, wl, args, "c3 uneven: 4M jobs, n U[50,250], m U[1.5n,6n]",
                                widths=(0, 32), cigar=(True,))
+            # the tuned plan: sa_tune on a 200k-job sample of the same distribution
+            sample = workloads.uneven(seed=1, n_jobs=200_000, first_item=1 << 28)
+            t0 = time.perf_counter()
+            classes = ref.tune(sa.jobs_array(sample.read_off, sample.read_len, sample.flags,
+                                             sample.ref_pos, sample.win_len), sample.reads)
+            tune_s = time.perf_counter() - t0
+            tuned = device_line(sa, ref, wl, args, "tuned", widths=(0,), cigar=(True, False))
+            plan = np.frombuffer(ref.plan()[8:], np.uint8)
+            line["tuned_plan"] = {"classes_tuned": classes, "tune_seconds": tune_s,
+                                  "cfg_of_length": {str(n): int(plan[n]) for n in (50, 100, 150, 200, 250)},
+                                  "rows": tuned["rows"]}
     elif args.config == "c4":
         wl = workloads.lowsim(seed=1, n_jobs=args.jobs or 500_000)
         with sa.Reference(wl.ref) as ref:

@@ -100,12 +100,6 @@ struct Workspace {
     DevBuf key, order, rpack, state, rect, tb, count, coff, sizes, offs, bsum;
     DevBuf colbest, tmp_ops, arena, plan, counters, blists, band, ovf, lkeys;
     PlanBlock* h_plan = nullptr;             // pinned mirror of the plan block
-    // lane-key scratch of the 16-bit score pass: entries carry the id of the item
-    // that wrote them; ids run on across launches until the 32-bit space is about
-    // to wrap, when (as after an allocation) the scratch is reset to id 0xFFFFFFFF
-    const void* lk_seen = nullptr;
-    size_t lk_seen_cap = 0;
-    uint64_t lk_next_id = 0;
     cudaEvent_t ev[16] = {};
     bool ev_ok = false;
     void release() {
@@ -345,19 +339,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
         if (w16[c]) max_warps16 = std::max(max_warps16, grid_for(c, kFillScore16) * (kBlock / 32));
     }
     TRY(ws.colbest.ensure((size_t)max_groups * cb_words(max_m) * 4, "column maxima"));
-    if (any16) {
-        TRY(ws.lkeys.ensure((size_t)max_warps16 * lane_key_entries(max_m) * 8, "lane keys"));
-        uint64_t items = 0;
-        for (int c = 0; c < kNumCfg; c++)
-            if (w16[c]) items += (cfg_count[c] + 2 * (32 / cfg_L(c)) - 1) / (2 * (32 / cfg_L(c)));
-        if (ws.lkeys.p != ws.lk_seen || ws.lkeys.cap != ws.lk_seen_cap ||
-            ws.lk_next_id + items >= 0xFFFFFFFFull) {
-            CU(cudaMemsetAsync(ws.lkeys.p, 0xFF, ws.lkeys.cap, st));
-            ws.lk_seen = ws.lkeys.p;
-            ws.lk_seen_cap = ws.lkeys.cap;
-            ws.lk_next_id = 0;
-        }
-    }
+    if (any16) TRY(ws.lkeys.ensure((size_t)max_warps16 * lane_key_words(max_m) * 4, "lane keys"));
 
     // --- stage: order, packed reads
     if (!plain) {
@@ -386,8 +368,8 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
     base.state = ws.state.as<JobState>();
     base.colbest = ws.colbest.as<int32_t>();
     base.cb_stride = cb_words(max_m);
-    base.lane_keys = any16 ? ws.lkeys.as<uint2>() : nullptr;
-    base.lk_stride = lane_key_entries(max_m);
+    base.lane_keys = any16 ? ws.lkeys.as<uint32_t>() : nullptr;
+    base.lk_stride = lane_key_words(max_m);
     base.rect = ws.rect.as<Rect>();
     base.wave = 0;
     uint32_t* counters = ws.counters.as<uint32_t>();
@@ -408,11 +390,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             fl.kind = w16[c] ? kFillScore16 : kFillScore;
             fl.block = kBlock;
             const uint32_t per_warp = (32 / cfg_L(c)) * (w16[c] ? 2 : 1);
-            if (w16[c]) {
-                stats.jobs16 += cfg_count[c];
-                fl.args.item_base = (uint32_t)ws.lk_next_id;
-                ws.lk_next_id += (cfg_count[c] + per_warp - 1) / per_warp;
-            }
+            if (w16[c]) stats.jobs16 += cfg_count[c];
             const uint64_t warps_needed = (cfg_count[c] + per_warp - 1) / per_warp;
             fl.grid = (int)std::min<uint64_t>(grid_for(c, fl.kind), (warps_needed + 3) / 4);
             fl.stream = st;
@@ -1096,6 +1074,11 @@ int sa_tune(sa_reference* R, const sa_params* P, const sa_job* jobs, uint32_t n_
                 if (n >= 1 && n <= SA_MAX_READ && cfg_for_rows((int)n) == c0) idx.push_back(k);
             }
             if (idx.size() < 256) continue;
+            // the timed batch repeats the class's jobs up to 2^18, so that every
+            // candidate's persistent grid runs many items per lane group (a batch
+            // of one item per group would time the tail, not the kernel)
+            const size_t distinct = idx.size();
+            while (idx.size() < (1u << 18)) idx.push_back(idx[idx.size() % distinct]);
             std::vector<sa_job> sj(idx.size());
             std::vector<char> sr;
             for (size_t t = 0; t < idx.size(); t++) {
@@ -1113,9 +1096,19 @@ int sa_tune(sa_reference* R, const sa_params* P, const sa_job* jobs, uint32_t n_
                 for (int c = 0; c < kNumCfg; c++)
                     if (cfg_L(c) == 32 && cfg_L(c) * cfg_K(c) >= cfg_L(c0) * cfg_K(c0)) { cands.push_back(c); break; }
             std::vector<int> widths = local16 ? std::vector<int>{16, 32} : std::vector<int>{32};
+            // the default (c0, automatic width) is timed first and kept unless a
+            // candidate is more than 2 % faster
             float best_ms = 0.f;
             int best_c = c0, best_w = 0;
-            bool first = true;
+            {
+                Plan trial = R->plan;
+                for (int n = 1; n <= SA_MAX_READ; n++)
+                    if (cfg_for_rows(n) == c0) trial.cfg[n] = (uint8_t)c0;
+                trial.width[c0] = 0;
+                TRY(time_trial(R, P, sc, trial, d_cfg, sj.data(), (uint32_t)sj.size(), sr.data(), sr.size(), &best_ms));
+            }
+            const float bar = 0.98f * best_ms;
+            float cand_ms = bar;
             for (int c : cands) {
                 for (int w : widths) {
                     Plan trial = R->plan;
@@ -1124,7 +1117,7 @@ int sa_tune(sa_reference* R, const sa_params* P, const sa_job* jobs, uint32_t n_
                     trial.width[c] = (int8_t)w;
                     float ms = 0.f;
                     TRY(time_trial(R, P, sc, trial, d_cfg, sj.data(), (uint32_t)sj.size(), sr.data(), sr.size(), &ms));
-                    if (first || ms < best_ms) { best_ms = ms; best_c = c; best_w = w; first = false; }
+                    if (ms < cand_ms) { cand_ms = ms; best_c = c; best_w = w; }
                 }
             }
             for (int n = 1; n <= SA_MAX_READ; n++)

@@ -16,14 +16,13 @@
 //
 // Best cell: each cell's key (H + beta) * 32 + (31 - r) (r the row in the lane)
 // is formed with one multiply-add on both halves; a lane keeps the maximum key of
-// its rows per column (the largest H and, among equal H, the first row) and
-// passes it down the group, whose last lane stores the group's column maximum.
-// A lane also stores its column key pair, tagged with the item id, at every step
-// where the key of either half beats the lane's running maximum key (from its
-// first column on).  The epilogue finds the first column i* holding the largest
-// H from the group's column maxima; a lane whose H at i* equals it had not
-// reached that H in an earlier column, so its key rose there and was stored,
-// which gives the first row.
+// its rows per column (the largest H and, among equal H, the first row), stores
+// it at every step (one 128-byte line per warp and step) and passes it down the
+// group, whose last lane stores the group's column maximum.  The epilogue finds
+// the first column i* holding the largest H from the group's column maxima and
+// the first row from the lanes' stored keys of column i*.  (Storing only where a
+// lane's key rises leaves partial sectors that cost the same DRAM traffic as
+// whole lines, plus the rise test on the ALU pipe.)
 //
 // Exact overflow detection: keys are exact while H + beta <= 1023.  A cell's H
 // is at most its diagonal predecessor + a, so while every H + beta so far is
@@ -61,7 +60,7 @@ __global__ void __launch_bounds__(128) k_fill16(FillArgs A) {
     const int grp = lane / L;
     const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     uint32_t* cb = reinterpret_cast<uint32_t*>(A.colbest) + (size_t)(gwarp * G + grp) * A.cb_stride + kCbFront;
-    uint2* lk = A.lane_keys + (size_t)gwarp * A.lk_stride + lane;
+    uint32_t* lk = A.lane_keys + (size_t)gwarp * A.lk_stride + lane;
     const Score S = A.sc;
     const uint32_t count = A.count_ptr ? *A.count_ptr : A.pos_count;
     extern __shared__ __align__(16) int32_t s_prof[];
@@ -82,7 +81,6 @@ __global__ void __launch_bounds__(128) k_fill16(FillArgs A) {
         if (lane == 0) item = atomicAdd(A.item_counter, 1u);
         item = __shfl_sync(FULL, item, 0);
         if (item * (uint32_t)(2 * G) >= count) break;
-        const uint32_t item_id = A.item_base + item;
         uint32_t jobv[2];
         int n[2] = {0, 0}, w[2] = {0, 0};
         int64_t wstart[2] = {0, 0};
@@ -150,7 +148,6 @@ __global__ void __launch_bounds__(128) k_fill16(FillArgs A) {
         reset_col0();
         uint32_t h_up_prev = 0u;
         uint32_t hg_bot = 0u, e_bot = 0u, cm_bot = 0u;
-        uint32_t lane_best = 0u;       // per half: running maximum key
 
         uint32_t wbn[2];
 #pragma unroll
@@ -209,18 +206,10 @@ __global__ void __launch_bounds__(128) k_fill16(FillArgs A) {
                 cm_bot = cm;
                 // steps outside the windows land in slack slots / are never read
                 if (g == L - 1) cb[i - 1] = cm;
-                const uint32_t lb = __vimax3_s16x2(lane_best, lm, lm);
-                // the rise test goes through an opaque xor: a DPX maximum is never
-                // compared with one of its own operands (wrong predicates were
-                // seen for that pattern on this toolchain)
-                uint32_t rise = lb ^ lane_best;
-                asm volatile("" : "+r"(rise));
-                if (rise != 0u) lk[(size_t)s * 32] = make_uint2(lm, item_id);
-                lane_best = lb;
+                lk[(size_t)s * 32] = lm;
                 if (8 * b < L && s < g) {      // before this lane's first column
                     reset_col0();
                     h_up_prev = 0u;
-                    lane_best = 0u;
                 }
             }
         }
@@ -254,9 +243,8 @@ __global__ void __launch_bounds__(128) k_fill16(FillArgs A) {
             // first row of that column: the lanes' stored keys of column vi
             int vj = 1 << 20;
             if (vi > 0) {
-                const uint2 e = lk[(size_t)(vi + g - 1) * 32];
-                const int32_t k = half16(e.x, h);
-                if (e.y == item_id && (k >> 5) == v) vj = g * K + (31 - (k & 31)) + 1 - pad[h];
+                const int32_t k = half16(lk[(size_t)(vi + g - 1) * 32], h);
+                if ((k >> 5) == v) vj = g * K + (31 - (k & 31)) + 1 - pad[h];
             }
 #pragma unroll
             for (int o = 1; o < L; o <<= 1) vj = min(vj, __shfl_xor_sync(FULL, vj, o, L));

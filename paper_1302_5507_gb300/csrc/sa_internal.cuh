@@ -141,10 +141,9 @@ __host__ __device__ inline int band_width_of(int b) { return 8 << b; }
 constexpr int kCbFront = 32;
 constexpr int kCbTail = 40;
 __host__ __device__ inline uint32_t cb_words(uint32_t max_m) { return max_m + kCbFront + kCbTail; }
-// per-warp entries of the 16-bit score pass's stored lane keys (one (key pair,
-// item id) entry per wavefront step and lane; a job pair takes at most
-// max_m + 38 steps)
-__host__ __device__ inline uint32_t lane_key_entries(uint32_t max_m) { return (max_m + 48) * 32; }
+// per-warp words of the 16-bit score pass's stored lane keys (one key pair per
+// wavefront step and lane; a job pair takes at most max_m + 38 steps)
+__host__ __device__ inline uint32_t lane_key_words(uint32_t max_m) { return (max_m + 48) * 32; }
 
 // Arguments of the wavefront kernels.
 struct FillArgs {
@@ -162,9 +161,8 @@ struct FillArgs {
     JobState* state;              // per job id
     int32_t* colbest;             // per group scratch, cb_stride words each
     uint32_t cb_stride;           // cb_words(longest window)
-    uint2* lane_keys;             // 16-bit score pass: per warp scratch, lk_stride entries each
+    uint32_t* lane_keys;          // 16-bit score pass: per warp scratch, lk_stride words each
     uint32_t lk_stride;
-    uint32_t item_base;           // 16-bit score pass: id of this launch's item 0 in lane_keys
     const Rect* rect;             // direction pass: per job id
     uint32_t* arena;              // direction bits
     int32_t wave;                 // direction pass: only jobs of this wave
