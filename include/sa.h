@@ -138,6 +138,9 @@ typedef struct {           /* statistics of the last call on a reference or serv
     uint32_t band_jobs;            /* ... whose optimal paths fit a band of 8, 16, 32 or 64 diagonals */
     uint32_t rect_jobs;            /* ... neither: whole-rectangle direction pass */
     uint32_t jobs16;               /* jobs whose score pass ran in 16-bit packed pairs */
+    uint32_t graph_replays;        /* 1 if the score segment ran as a replayed CUDA graph
+                                      (graphs are used when profile == 0) */
+    uint32_t _pad;
 } sa_stats;
 
 typedef struct sa_reference sa_reference;

@@ -100,6 +100,10 @@ struct Workspace {
     DevBuf key, order, rpack, state, rect, tb, count, coff, sizes, offs, bsum;
     DevBuf colbest, tmp_ops, arena, plan, counters, blists, band, ovf, lkeys;
     PlanBlock* h_plan = nullptr;             // pinned mirror of the plan block
+    // the score segment (order, packing, score passes, overflow rerun) as a CUDA
+    // graph, replayed while a call's launches would be identical (same key)
+    cudaGraphExec_t seg_exec = nullptr;
+    uint64_t seg_key = 0;
     cudaEvent_t ev[16] = {};
     bool ev_ok = false;
     void release() {
@@ -109,6 +113,9 @@ struct Workspace {
         for (DevBuf* b : all) b->release();
         if (h_plan) cudaFreeHost(h_plan);
         h_plan = nullptr;
+        if (seg_exec) cudaGraphExecDestroy(seg_exec);
+        seg_exec = nullptr;
+        seg_key = 0;
         if (ev_ok)
             for (auto& e : ev) cudaEventDestroy(e);
         ev_ok = false;
@@ -194,6 +201,14 @@ struct Timer {
         if (!on || next >= 16) return -1;
         cudaEventRecord(ws.ev[next], st);
         return next++;
+    }
+    // the index a mark recorded inside a replayed graph takes (nothing recorded here)
+    int reserve() {
+        if (!on || next >= 16) return -1;
+        return next++;
+    }
+    void mark_at(int k) {
+        if (k >= 0) cudaEventRecord(ws.ev[k], st);
     }
     float ms(int a, int b) {
         if (!on || a < 0 || b < 0) return 0.f;
@@ -341,22 +356,6 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
     TRY(ws.colbest.ensure((size_t)max_groups * cb_words(max_m) * 4, "column maxima"));
     if (any16) TRY(ws.lkeys.ensure((size_t)max_warps16 * lane_key_words(max_m) * 4, "lane keys"));
 
-    // --- stage: order, packed reads
-    if (!plain) {
-        launch_plan_order(ws.key.as<uint16_t>(), n_jobs, dp->hist, dp->key_off, dp->cursor,
-                          ws.order.as<uint32_t>(), st);
-        launches += 2;
-    } else {
-        launch_iota(ws.order.as<uint32_t>(), n_jobs, st);
-        launches++;
-    }
-    launch_pack_reads(d_jobs, n_jobs, reinterpret_cast<const uint8_t*>(d_reads),
-                      ws.rpack.as<uint32_t>(), rw, &dp->st.bad_read, st);
-    launches++;
-    CU(cudaGetLastError());
-    trace("order + pack reads");
-    const int t1 = tm.mark();
-
     FillArgs base{};
     base.ref = X.d_words;
     base.ref_len = (int64_t)X.len;
@@ -375,11 +374,44 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
     uint32_t* counters = ws.counters.as<uint32_t>();
     auto next_counter = [&]() { return counters + (counter_next++ % 256); };
 
-    int tfill1 = -1, tfill16 = -1, trect1 = -1, ttb1 = -1;
+    int t1 = -1, tfill1 = -1, tfill16 = -1, trect1 = -1, ttb1 = -1;
+    if (plain) {
+        launch_iota(ws.order.as<uint32_t>(), n_jobs, st);
+        launch_pack_reads(d_jobs, n_jobs, reinterpret_cast<const uint8_t*>(d_reads),
+                          ws.rpack.as<uint32_t>(), rw, &dp->st.bad_read, st);
+        launches += 2;
+        CU(cudaGetLastError());
+        trace("order + pack reads");
+        t1 = tm.mark();
+    }
     if (!plain) {
-        // --- score pass: one persistent launch per non-empty length bucket; in
-        // 16-bit pairs when exact (LOCAL, scores in range), then a 32-bit rerun of
-        // the jobs whose maximum reached the 16-bit overflow threshold
+        if (any16) TRY(ws.ovf.ensure((size_t)n_jobs * 4, "overflow list"));
+        // the score segment: stage (order, packed reads), one persistent score-pass
+        // launch per non-empty length bucket (16-bit pairs where chosen), then the
+        // 32-bit rerun of the jobs whose maximum reached the 16-bit threshold.  Its
+        // launches depend only on `key` below, so without phase timing it is
+        // captured once as a CUDA graph and replayed while the key stays the same.
+        const int counter_base = counter_next;
+        int seg_counters = 0;          // item counters the segment's launches take
+        for (int c = 0; c < kNumCfg; c++) {
+            if (!cfg_count[c]) continue;
+            stats.fill_launches++;
+            if (w16[c]) stats.jobs16 += cfg_count[c];
+            launches += 1 + (w16[c] ? 1 : 0);
+            seg_counters += 1 + (w16[c] ? 1 : 0);
+        }
+        launches += 3 + (any16 ? 1 : 0);
+        t1 = tm.reserve();
+        tfill16 = any16 ? tm.reserve() : -1;
+        tfill1 = tm.reserve();
+        auto issue_segment = [&]() -> int {
+        launch_plan_order(ws.key.as<uint16_t>(), n_jobs, dp->hist, dp->key_off, dp->cursor,
+                          ws.order.as<uint32_t>(), st);
+        launch_pack_reads(d_jobs, n_jobs, reinterpret_cast<const uint8_t*>(d_reads),
+                          ws.rpack.as<uint32_t>(), rw, &dp->st.bad_read, st);
+        CU(cudaGetLastError());
+        trace("order + pack reads");
+        tm.mark_at(t1);
         for (int c = 0; c < kNumCfg; c++) {
             if (!cfg_count[c]) continue;
             FillLaunch fl{};
@@ -390,22 +422,17 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             fl.kind = w16[c] ? kFillScore16 : kFillScore;
             fl.block = kBlock;
             const uint32_t per_warp = (32 / cfg_L(c)) * (w16[c] ? 2 : 1);
-            if (w16[c]) stats.jobs16 += cfg_count[c];
             const uint64_t warps_needed = (cfg_count[c] + per_warp - 1) / per_warp;
             fl.grid = (int)std::min<uint64_t>(grid_for(c, fl.kind), (warps_needed + 3) / 4);
             fl.stream = st;
             launch_fill_cfg(c, fl);
-            stats.fill_launches++;
-            launches++;
             if (trace.on) { char b[64]; snprintf(b, sizeof b, "score pass cfg %d (%u jobs)", c, cfg_count[c]); trace(b); }
         }
         CU(cudaGetLastError());
         if (any16) {
-            tfill16 = tm.mark();
-            TRY(ws.ovf.ensure((size_t)n_jobs * 4, "overflow list"));
+            tm.mark_at(tfill16);
             launch_collect_overflow(ws.order.as<uint32_t>(), n_jobs, ws.state.as<JobState>(), dp->cfg_begin,
                                     ws.ovf.as<uint32_t>(), dp->ovf_count, st);
-            launches++;
             for (int c = 0; c < kNumCfg; c++) {
                 if (!w16[c]) continue;
                 FillLaunch fl{};
@@ -422,12 +449,51 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
                 fl.grid = (int)std::min<uint64_t>(grid_for(c, kFillScore), (warps_needed + 3) / 4);
                 fl.stream = st;
                 launch_fill_cfg(c, fl);
-                launches++;
             }
             CU(cudaGetLastError());
             trace("overflow rerun");
         }
-        tfill1 = tm.mark();
+        tm.mark_at(tfill1);
+        return SA_OK;
+        };
+        // everything the segment's launches depend on
+        uint64_t key = 1469598103934665603ull;
+        auto mix = [&](uint64_t v) { key = (key ^ v) * 1099511628211ull; };
+        const void* ptrs[] = {d_jobs, d_reads, X.d_words, ws.key.p, ws.order.p, ws.rpack.p, ws.state.p,
+                              ws.colbest.p, ws.lkeys.p, ws.ovf.p, ws.counters.p, dp, (const void*)st};
+        for (const void* q : ptrs) mix((uint64_t)(uintptr_t)q);
+        mix(n_jobs); mix(reads_len); mix(X.len); mix(max_n); mix(max_m); mix((uint64_t)mode);
+        mix((uint64_t)(uint32_t)sc.a); mix((uint64_t)(uint32_t)sc.b); mix((uint64_t)(uint32_t)sc.GO);
+        mix((uint64_t)(uint32_t)sc.GE);
+        for (int c = 0; c < kNumCfg; c++) { mix(cfg_count[c]); mix(w16[c]); }
+        mix(tm.on ? 1 : 0);
+        if (trace.on || tm.on) {
+            // phase timing and tracing run the launches directly (their event
+            // records and synchronisations are not graph nodes)
+            TRY(issue_segment());
+        } else if (ws.seg_exec && ws.seg_key == key) {
+            CU(cudaGraphLaunch(ws.seg_exec, st));
+            stats.graph_replays++;
+        } else {
+            if (ws.seg_exec) cudaGraphExecDestroy(ws.seg_exec);
+            ws.seg_exec = nullptr;
+            ws.seg_key = 0;
+            CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            const int rc = issue_segment();
+            cudaGraph_t g = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(st, &g);
+            if (rc != SA_OK) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            CU(ce);
+            const cudaError_t ie = cudaGraphInstantiate(&ws.seg_exec, g, 0);
+            cudaGraphDestroy(g);
+            CU(ie);
+            ws.seg_key = key;
+            CU(cudaGraphLaunch(ws.seg_exec, st));
+        }
+        counter_next = counter_base + seg_counters;
 
         if (want_cigar) {
             // --- reduced traceback: banded direction pass for most jobs, the
