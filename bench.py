@@ -172,9 +172,21 @@ def cpu_baseline(wl, target_s: float = 8.0):
             "sample": f"first {n} of {wl.n_jobs} jobs ({sample.cells:.3g} cells, {dt:.1f} s, LOCAL + CIGAR)"}
 
 
-def make_workload(rank: int, n_jobs: int):
+def make_workload(rank: int, n_jobs: int, genome_len: int = 100_000_000):
+    """This rank's shard: jobs rank*n_jobs .. (rank+1)*n_jobs-1 of the mate-rescue
+    stream on the shared genome (independent jobs, no exchange between ranks)."""
     import workloads
-    return workloads.mate_rescue(seed=1, n_pairs=n_jobs, first_item=rank * n_jobs)
+    return workloads.mate_rescue(seed=1, n_pairs=n_jobs, genome_len=genome_len, first_item=rank * n_jobs)
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest value of `x` over all ranks (the timed region of the slowest rank)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def run_reference(args, rank, world):
@@ -262,11 +274,7 @@ def run_ours(args, rank, world, dist):
             step_stats.append(st_)
             fill_ms.append(st_["ms_fill"])
         barrier()
-    ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     ms_per_step = ms / args.steps
     cells_rank = wl.cells
     cells_all = cells_rank * world
@@ -292,11 +300,7 @@ def run_ours(args, rank, world, dist):
         _, c = ref.align(jobs_np, reads_np, e2e_params, out=out_np, cigar=cig_np, stream=None)
         used = len(c)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
     e2e_value = cells_all * args.steps / e2e_s / 1e9
 
     # --- plain form on the same workload (comparison form)
