@@ -13,7 +13,12 @@
 //
 // LOCAL pads the group's rows at the top (rows j <= 0 never match, so they
 // stay at H = 0 and feed row 1 exactly the border values H(i,0) = 0,
-// E(i,0) = -inf); GLOCAL pads at the bottom and reads row n by index.
+// E(i,0) = -inf); so does the GLOCAL score pass (its padding rows score 0
+// against every base and stay at H = 0), which puts row n on the last lane's
+// last row; the GLOCAL direction passes pad at the bottom.
+//
+// The score pass and the rectangle direction pass take the match term from a
+// per-lane shared-memory profile; the plain form uses per-lane match masks.
 //
 // Three variants (template flags):
 //   BEST && !DIR  score pass: best cell, colbest(i), second best
@@ -66,8 +71,10 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
     int32_t* cb = BEST ? A.colbest + (size_t)(gwarp * G + grp) * A.cb_stride + kCbFront : nullptr;
     const Score S = A.sc;
     const uint32_t count = A.count_ptr ? *A.count_ptr : A.pos_count;
-    // the score pass takes the match/mismatch term from a shared-memory profile
+    // the score pass and the rectangle direction pass take the match/mismatch term
+    // from a shared-memory profile (SPROF); PROF marks the score pass
     constexpr bool PROF = BEST && !DIR;
+    constexpr bool SPROF = PROF || (DIR && !BEST);
     constexpr int K4 = (K + 3) / 4;
     extern __shared__ __align__(16) int32_t s_prof[];
     int32_t* prof = s_prof + (threadIdx.x >> 5) * prof_words_per_warp<K>();
@@ -124,7 +131,7 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
         const int pad = (LOCAL || PROF) ? (L * K - rows) : 0;
         // match masks: bit r of mX is set when the lane's row r holds base X
         uint32_t mA = 0, mC = 0, mG = 0, mT = 0;
-        if (PROF) {
+        if (SPROF) {
             // profile: int4 ((t*K4 + r/4)*32 + lane) holds the diagonal terms of rows
             // r..r+3 against window base t (LOCAL padding rows never match, GLOCAL
             // padding rows score 0); written and read as int4, so later reads cannot
@@ -219,7 +226,7 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
                 int32_t diag = h_up_prev;
                 h_up_prev = hg_up;
                 const uint32_t t = (wb >> (2 * u)) & 3u;
-                const uint32_t mk = PROF ? 0u : (t == 0 ? mA : (t == 1 ? mC : (t == 2 ? mG : mT)));
+                const uint32_t mk = SPROF ? 0u : (t == 0 ? mA : (t == 1 ? mC : (t == 2 ? mG : mT)));
                 const int4* pt = reinterpret_cast<const int4*>(prof) + (t * K4) * 32 + lane;
                 int4 dq = make_int4(0, 0, 0, 0);
                 int32_t e = e_up, hga = hg_up;
@@ -227,14 +234,14 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
                 // score pass: the diagonal term of row r+1 is formed while row r still
                 // holds H(i-1, j) (no copy of the old value is kept)
                 int32_t gcur = 0;
-                if (PROF) {
+                if (SPROF) {
                     dq = pt[0];
                     gcur = add_fma(dq.x, diag, one);
                 }
 #pragma unroll
                 for (int r = 0; r < K; r++) {
                     int32_t gv;
-                    if (PROF) {
+                    if (SPROF) {
                         gv = gcur;
                         if (r + 1 < K) {
                             const int rn = r + 1;
@@ -269,7 +276,7 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
                         dw[r >> 3] |= nib << (4 * (r & 7));
                     }
                     F[r] = f;
-                    HG[r] = PROF ? add_fma(h, S.GO, one) : h + S.GO;
+                    HG[r] = SPROF ? add_fma(h, S.GO, one) : h + S.GO;
                     hga = HG[r];
                     if (BEST && LOCAL) {
                         if (PROF) {

@@ -15,7 +15,7 @@ constexpr int kK = kCfgs[SA_CFG].K;
 
 // dynamic shared memory of a 128-thread block: the score pass's profile
 template <bool DIR, bool BEST>
-constexpr size_t smem_bytes() { return (BEST && !DIR) ? 4 * prof_words_per_warp<kK>() * sizeof(int32_t) : 0; }
+constexpr size_t smem_bytes() { return (BEST != DIR) ? 4 * prof_words_per_warp<kK>() * sizeof(int32_t) : 0; }
 
 template <int MODE, bool DIR, bool BEST>
 void prepare() {
