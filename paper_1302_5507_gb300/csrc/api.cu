@@ -523,8 +523,10 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             // band regions: 32 jobs of a class share a region of max_n rows x B/8 words x 32 lanes
             BandLayout bl{};
             uint64_t band_words = 0;
+            // byte heights instead of nibbles when LOCAL scores stay below 255
+            const bool heights = mode == SA_LOCAL && (int64_t)sc.a * max_n <= 254;
             for (int k = 0; k < kNumBand; k++) {
-                bl.warp_stride[k] = (uint64_t)max_n * (band_width_of(k) / 8) * 32;
+                bl.warp_stride[k] = (uint64_t)max_n * (band_width_of(k) / (heights ? 4 : 8)) * 32;
                 bl.base[k] = band_words;
                 band_words += (uint64_t)((nb[k] + 31) / 32) * bl.warp_stride[k];
             }
@@ -549,7 +551,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
                 ba.tb = ws.tb.as<TbOut>();
                 ba.err_job = &dp->st.bad_walk;
                 if (ba.count) {
-                    launch_band(band_cls(k), ba, st);
+                    launch_band(band_cls(k), ba, heights, st);
                     launches++;
                 }
             }

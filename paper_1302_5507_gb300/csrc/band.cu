@@ -21,6 +21,15 @@
 // + t of its warp's region), so the stores of a warp are coalesced.  The same
 // thread then walks its nibbles from (i*, j*): they were written moments before
 // and are read back from L2.
+//
+// LOCAL jobs whose scores fit a byte (a * n <= 254) take a lighter form
+// (`k_band_h`): the pass stores each in-band H as a byte (255 = -inf) instead
+// of a direction nibble, and the walk re-derives every decision from those
+// heights: M when H = H(i-1,j-1) + delta; D when H equals F(i,j) = max over
+// k >= 1 of H(i-k,j) + S_GO + (k-1) S_GE (the recurrence's deletion value,
+// summed along the row); I otherwise; a gap run extends from (i,j) while its
+// value is strictly above H(neighbour) + S_GO.  These are the comparisons the
+// nibbles record, taken on the same band values, so the CIGAR is the same.
 #include "kernels.h"
 #include "walk.cuh"
 
@@ -152,12 +161,179 @@ __global__ void __launch_bounds__(128) k_band(BandArgs A) {
     if (e.bad) atomicMin(A.err_job, job);
 }
 
+template <int B, bool EDGE>
+__device__ __forceinline__ void band_row_h(int32_t (&Hs)[B + 1], int32_t (&Es)[B + 1], uint32_t (&words)[B / 4],
+                                           const uint64_t (&mmh)[B > 32 ? 2 : 1], int i0,
+                                           int32_t GO, int32_t GE, int32_t sa, int32_t sb) {
+    int32_t hleft = kNeg32, fleft = kNeg32;
+#pragma unroll
+    for (int k = 0; k < B; k++) {
+        int32_t hn, fn, en;
+        uint32_t byte;
+        if (EDGE && i0 + k <= 0) {
+            hn = (i0 + k == 0) ? 0 : kNeg32;        // column 0 (LOCAL: H(0,j) = 0) or left of it
+            en = kNeg32;
+            fn = kNeg32;
+            byte = (i0 + k == 0) ? 0u : 255u;
+        } else {
+            en = max(Hs[k + 1] + GO, Es[k + 1] + GE);
+            fn = max(hleft + GO, fleft + GE);
+            const bool match = (mmh[k >> 5] >> (2 * (k & 31))) & 1ull;
+            hn = __vimax3_s32_relu(Hs[k] + (match ? sa : sb), en, fn);
+            byte = (uint32_t)hn;
+        }
+        Hs[k] = hn;
+        Es[k] = en;
+        hleft = hn;
+        fleft = fn;
+        words[k >> 2] |= byte << (8 * (k & 3));
+    }
+}
+
+template <int B>
+__global__ void __launch_bounds__(128) k_band_h(BandArgs A) {
+    constexpr int W = B / 4;                   // words of heights a row
+    static_assert(B == 8 || B == 16 || B == 32 || B == 64, "band widths 8, 16, 32 and 64");
+    const uint32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= A.count) return;
+    const uint32_t job = A.list[pos];
+    const sa_job J = A.jobs[job];
+    const Rect R = A.rect[job];
+    const int rows = R.rows;
+    const int dlo = R.d_lo;
+    const int32_t GO = in_reg(A.sc.GO), GE = in_reg(A.sc.GE), sa = in_reg(A.sc.a), sb = in_reg(A.sc.b);
+    uint32_t* out = A.arena + (uint64_t)(pos >> 5) * A.warp_stride + (pos & 31);
+    const uint32_t* rp = A.rpack + (size_t)job * A.rw;
+    const uint32_t* refw = A.ref + kRefFrontPad;
+
+    int32_t Hs[B + 1], Es[B + 1];
+#pragma unroll
+    for (int k = 0; k <= B; k++) {
+        Hs[k] = (k < B && dlo + k >= 0) ? 0 : kNeg32;
+        Es[k] = kNeg32;
+    }
+    for (int j = 1; j <= rows; j++) {
+        const int i0 = j + dlo;
+        const uint64_t rb = (uint64_t)((__ldg(rp + ((j - 1) >> 4)) >> (2 * ((j - 1) & 15))) & 3u);
+        constexpr int NH = B > 32 ? 2 : 1;
+        uint64_t mmh[NH];
+#pragma unroll
+        for (int hh = 0; hh < NH; hh++) {
+            const int64_t ph = (int64_t)J.ref_pos + i0 - 1 + 32 * hh;
+            int64_t qh = ph < (int64_t)J.ref_pos ? (int64_t)J.ref_pos : ph;
+            if (qh > A.ref_len) qh = A.ref_len;
+            const int64_t wi = qh >> 4;
+            const uint32_t sh = (uint32_t)(qh & 15) * 2u;
+            const uint64_t lo = ((uint64_t)__ldg(refw + wi + 1) << 32) | (uint64_t)__ldg(refw + wi);
+            const uint64_t hi = (uint64_t)__ldg(refw + wi + 2);
+            uint64_t wb = sh ? ((lo >> sh) | (hi << (64 - sh))) : lo;
+            const int64_t lead = qh - ph;
+            wb = lead >= 32 ? 0ull : (wb << (2 * lead));
+            const uint64_t x = wb ^ (rb * 0x5555555555555555ull);
+            mmh[hh] = ~(x | (x >> 1)) & 0x5555555555555555ull;
+        }
+        uint32_t words[W];
+#pragma unroll
+        for (int w = 0; w < W; w++) words[w] = 0u;
+        if (i0 >= 1) band_row_h<B, false>(Hs, Es, words, mmh, i0, GO, GE, sa, sb);
+        else band_row_h<B, true>(Hs, Es, words, mmh, i0, GO, GE, sa, sb);
+#pragma unroll
+        for (int w = 0; w < W; w++) out[((uint64_t)(j - 1) * W + w) * 32] = words[w];
+    }
+
+    // the walk from the best cell, deciding from the stored heights
+    const JobState st = A.state[job];
+    auto height = [&](int ii, int jj) -> int32_t {     // band H(ii, jj); kNeg32 outside
+        if (jj == 0) return ii >= 0 ? 0 : kNeg32;       // row 0
+        const int k = ii - jj - dlo;
+        if (k < 0 || k >= B) return kNeg32;
+        const uint32_t v = (out[((uint64_t)(jj - 1) * W + (k >> 2)) * 32] >> (8 * (k & 3))) & 255u;
+        return v == 255u ? kNeg32 : (int32_t)v;
+    };
+    auto base_t = [&](int ii) -> uint32_t {              // window base of column ii >= 1
+        const uint64_t p = J.ref_pos + (uint64_t)(ii - 1);
+        return (__ldg(refw + (p >> 4)) >> (2 * (p & 15))) & 3u;
+    };
+    auto base_r = [&](int jj) -> uint32_t {              // read base of row jj >= 1
+        return (__ldg(rp + ((jj - 1) >> 4)) >> (2 * ((jj - 1) & 15))) & 3u;
+    };
+    uint32_t* ops = A.tmp_ops + (uint64_t)job * A.tmp_stride;
+    const uint32_t cap = A.tmp_stride;
+    int nrev = 0;
+    uint32_t cur_op = 15u, cur_len = 0;
+    auto emit = [&](uint32_t op) {
+        if (op == cur_op) { cur_len++; return; }
+        if (cur_len) ops[nrev++] = (cur_len << 4) | cur_op;
+        cur_op = op;
+        cur_len = 1;
+    };
+    int i = st.i_star, j = st.j_star;
+    int32_t h = st.best, cur = 0;
+    int state = 0;                                       // 0 H, 1 E (insertion), 2 F (deletion)
+    int budget = 2 * (st.i_star + rows) + 4;
+    bool bad = (i < 1 || j < 1 || j > rows || i - j - dlo < 0 || i - j - dlo >= B || height(i, j) != h);
+    while (!bad) {
+        if (--budget < 0 || nrev >= (int)cap - 1) { bad = true; break; }
+        if (state == 0) {
+            if (i == 0 || j == 0 || h <= 0) break;
+            const int32_t hd = height(i - 1, j - 1);
+            if (hd != kNeg32 && hd + (base_t(i) == base_r(j) ? sa : sb) == h) {
+                emit(0u);
+                i--; j--; h = hd;
+                continue;
+            }
+            int32_t f = kNeg32;
+            for (int kk = 1; kk <= i; kk++) {
+                const int32_t hx = height(i - kk, j);
+                if (hx == kNeg32) break;                 // left of the band: the rest is -inf
+                f = max(f, hx + GO + (kk - 1) * GE);
+            }
+            state = (f == h) ? 2 : 1;
+            cur = h;
+        } else if (state == 2) {
+            if (i < 1) { bad = true; break; }
+            emit(2u);
+            const int32_t hn = height(i - 1, j);
+            i--;
+            if (hn != kNeg32 && cur <= hn + GO) { state = 0; h = hn; }
+            else cur -= GE;
+        } else {
+            if (j < 1) { bad = true; break; }
+            emit(1u);
+            const int32_t hn = height(i, j - 1);
+            j--;
+            if (hn != kNeg32 && cur <= hn + GO) { state = 0; h = hn; }
+            else cur -= GE;
+        }
+    }
+    TbOut t;
+    if (bad) {
+        atomicMin(A.err_job, job);
+        t.n_rev = 0;
+        t.read_begin = 0;
+        t.ref_begin_rel = 0;
+    } else {
+        if (cur_len) ops[nrev++] = (cur_len << 4) | cur_op;
+        t.n_rev = nrev;
+        t.read_begin = j;
+        t.ref_begin_rel = i;
+    }
+    A.tb[job] = t;
+}
+
 }  // namespace
 
-void launch_band(int cls, const BandArgs& a, cudaStream_t st) {
+void launch_band(int cls, const BandArgs& a, bool heights, cudaStream_t st) {
     if (!a.count) return;
     const unsigned grid = (a.count + 127) / 128;
     const bool local = a.sc.mode == SA_LOCAL;
+    if (heights) {                     // LOCAL, scores below 255
+        if (cls == kClsBand8) k_band_h<8><<<grid, 128, 0, st>>>(a);
+        else if (cls == kClsBand16) k_band_h<16><<<grid, 128, 0, st>>>(a);
+        else if (cls == kClsBand32) k_band_h<32><<<grid, 128, 0, st>>>(a);
+        else k_band_h<64><<<grid, 128, 0, st>>>(a);
+        return;
+    }
     if (cls == kClsBand8) {
         local ? k_band<8, SA_LOCAL><<<grid, 128, 0, st>>>(a) : k_band<8, SA_GLOCAL><<<grid, 128, 0, st>>>(a);
     } else if (cls == kClsBand16) {

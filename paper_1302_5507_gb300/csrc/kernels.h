@@ -64,7 +64,9 @@ void launch_rect_plan(const sa_job* jobs, const uint32_t* order, uint32_t n_pos,
                       const JobState* state, const Score& sc, int32_t min_score, int allow_band,
                       Rect* rect, uint64_t* sizes, uint32_t* const* lists, uint32_t* cls_count,
                       cudaStream_t st);
-void launch_band(int cls, const BandArgs& a, cudaStream_t st);
+// heights: the byte-height form (LOCAL and every score below 255; the band
+// regions then hold B/4 words a row instead of B/8)
+void launch_band(int cls, const BandArgs& a, bool heights, cudaStream_t st);
 void launch_rect_assign(const uint32_t* order, uint32_t n_pos, const uint64_t* offs,
                         const uint32_t* cfg_begin, uint64_t wave_words, Rect* rect,
                         uint32_t* max_wave, cudaStream_t st);
