@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GCUPS (affine DP incl. traceback) at 1 GB300 vs plain form; p50/p99 request latency"
 WORKLOAD = "mate_rescue: 1M jobs, 150 bp mate (reverse-complemented) vs 800 bp window, 100 Mbp GC41 genome + 5% repeats"
-OPS_PER_CELL = 6          # minimal lane-ops per cell update (roofline)
+OPS_PER_CELL = 6          # lane-ops per cell of the roofline formula: 1 add H+GO, 2 add-max (E, F), 1 add diag+delta, 1 max3, 1 column-max update
 PROBE_S16X2, PROBE_S32 = 6, 0   # operation codes of the DPX throughput probe (viaddmax)
 
 
@@ -46,8 +46,9 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving latency run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
-    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5"],
-                    help="c2 (default): the mate-rescue headline line; c3 uneven lengths, "
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
+                    help="c2 (default): the mate-rescue headline line; c1 plain windows (plain and "
+                         "batched forms, both modes) plus mate rescue in GLOCAL; c3 uneven lengths, "
                          "c4 low similarity, c5 serving sweep: one extra JSON line each (1 GPU)")
     return ap.parse_args()
 
@@ -458,7 +459,7 @@ def serving_run(sa, ref, reqs, ppm, loads, genome: str, plain: bool = False):
     return out
 
 
-def device_line(sa, ref, wl, args, label, widths=(0,), cigar=(True, False)):
+def device_line(sa, ref, wl, args, label, widths=(0,), cigar=(True, False), mode=0, form=0):
     """GCUPS of one workload through sa_align_batch_dev (inputs resident), per
     (width, CIGAR) setting, with the phase times of the library's CUDA events."""
     import torch
@@ -471,7 +472,7 @@ def device_line(sa, ref, wl, args, label, widths=(0,), cigar=(True, False)):
     rows = []
     for width in widths:
         for cg in cigar:
-            p = sa.make_params(width=width, want_cigar=cg, profile=True)
+            p = sa.make_params(width=width, want_cigar=cg, profile=True, mode=mode, form=form)
             for _ in range(max(3, args.warmup)):
                 ref.align_dev(d_jobs, d_reads, d_out, d_cig if cg else None, p)
             torch.cuda.synchronize()
@@ -487,7 +488,8 @@ def device_line(sa, ref, wl, args, label, widths=(0,), cigar=(True, False)):
             ph = {k: float(np.mean([st[k] for st in sts])) for k in
                   ("ms_stage", "ms_fill", "ms_rerun", "ms_rect", "ms_traceback", "ms_finalize")}
             st = sts[-1]
-            rows.append({"width": width or "auto", "cigar": cg, "gcups": wl.cells / (ms / 1e3) / 1e9,
+            rows.append({"mode": "GLOCAL" if mode else "LOCAL", "form": "plain" if form else "batched",
+                         "width": width or "auto", "cigar": cg, "gcups": wl.cells / (ms / 1e3) / 1e9,
                          "ms_per_step": ms, "score_pass_gcups": wl.cells / (ph["ms_fill"] / 1e3) / 1e9,
                          "phases_ms": ph, "jobs16": int(st["jobs16"]), "overflow_reruns": int(st["overflow_reruns"]),
                          "diag_jobs": int(st["diag_jobs"]), "band_jobs": int(st["band_jobs"]),
@@ -503,7 +505,20 @@ def run_config(args):
     import workloads
     torch.cuda.set_device(0)
     __graft_entry__.build()
-    if args.config == "c3":
+    if args.config == "c1":
+        wl = workloads.plain(seed=1, n_jobs=args.jobs or 10_000)
+        rows = []
+        with sa.Reference(wl.ref) as ref:
+            for mode in (0, 1):
+                for form in (1, 0):
+                    rows += device_line(sa, ref, wl, args, "", cigar=(True,), mode=mode, form=form)["rows"]
+        mate = make_workload(0, 1_000_000)
+        with sa.Reference(mate.ref) as ref:
+            glocal = device_line(sa, ref, mate, args, "", cigar=(True, False), mode=1)["rows"]
+        line = {"config": "c1 plain: 10k windows of 400 bp, 100 bp reads (plain and batched forms, both modes)",
+                "jobs": int(wl.n_jobs), "cells": int(wl.cells), "steps": args.steps, "rows": rows,
+                "mate_rescue_glocal": {"jobs": int(mate.n_jobs), "cells": int(mate.cells), "rows": glocal}}
+    elif args.config == "c3":
         wl = workloads.uneven(seed=1, n_jobs=args.jobs or 4_000_000)
         with sa.Reference(wl.ref) as ref:
             line = device_line(sa, ref, wl, args, "c3 uneven: 4M jobs, n U[50,250], m U[1.5n,6n]",
