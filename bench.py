@@ -134,6 +134,20 @@ def traffic_from_profiles():
     return float(m.group(1)) if m.group(2) == kernel_source_sha() else None
 
 
+def direction_bound(stats, wl):
+    """HBM roofline of the traceback's direction data: GCUPS (over all cells of the
+    batch) if only writing its band heights / rectangle nibbles limited the step."""
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        gbs, basis = float(peaks["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        gbs, basis = 6800.0, "fallback"
+    return {"hbm_gbs": gbs, "hbm_basis": basis,
+            "full_matrix_nibbles_gcups": gbs / 0.5,
+            "note": "the band passes write bytes only for cells on the diagonals an optimal path "
+                    "can use, so their data is a small fraction of 0.5 B per cell of the batch"}
+
+
 def dpx_lane_ops_per_sm_clk(local_rank: int):
     """Measured issue rate of the packed 16-bit and the 32-bit add-max (DPX)
     instructions, lane-operations per SM per clock, from the probe library; the
@@ -169,8 +183,16 @@ def cpu_baseline(wl, target_s: float = 8.0):
     t0 = time.perf_counter()
     oracle.align(sample, n_threads=nthreads)
     dt = time.perf_counter() - t0
+    # one thread on a small sample (about 2 s)
+    n1 = int(min(wl.n_jobs, max(50, 2.0 * rate / nthreads / (wl.cells / wl.n_jobs))))
+    one = wl.subset(np.arange(n1))
+    t0 = time.perf_counter()
+    oracle.align(one, n_threads=1)
+    dt1 = time.perf_counter() - t0
     return {"value": sample.cells / dt / 1e9, "unit": "GCUPS", "cores": nthreads, "kind": "oracle",
-            "sample": f"first {n} of {wl.n_jobs} jobs ({sample.cells:.3g} cells, {dt:.1f} s, LOCAL + CIGAR)"}
+            "sample": f"first {n} of {wl.n_jobs} jobs ({sample.cells:.3g} cells, {dt:.1f} s, LOCAL + CIGAR)",
+            "single_thread": {"value": one.cells / dt1 / 1e9, "unit": "GCUPS",
+                              "sample": f"first {n1} jobs ({one.cells:.3g} cells, {dt1:.1f} s)"}}
 
 
 def make_workload(rank: int, n_jobs: int, genome_len: int = 100_000_000):
@@ -344,7 +366,10 @@ def run_ours(args, rank, world, dist):
                 "peak_basis": f"{n_sm} SMs x {lanes:.1f} DPX lane-ops/SM/clk (measured, probe) x "
                               f"{sm_mhz:.0f} MHz (median under load) x {cells_per_op} cells per lane-op "
                               f"/ {OPS_PER_CELL} lane-ops per cell",
-                "dpx_probe": dpx, "kernel_sources_sha1": kernel_source_sha()}
+                "dpx_probe": dpx, "kernel_sources_sha1": kernel_source_sha(),
+                # the traceback's own bound: its direction data (0.5 B per banded cell as
+                # nibbles, 1 B as byte heights) against the measured copy bandwidth
+                "direction_data_bound": direction_bound(stats, wl)}
 
     line = None
     if rank == 0:
