@@ -246,7 +246,6 @@ __global__ void k_rect_plan(const sa_job* __restrict__ jobs, const uint32_t* __r
     while (valid && c + 1 < kNumCfg && cfg_begin[c + 1] <= p) c++;   // the position's bucket
     R.cfg = c;
     if (valid) {
-        const sa_job J = jobs[job];
         const JobState st = state[job];
         if (!(st.flags & kStEmpty) && st.best >= min_score) {
             const int istar = st.i_star, jstar = st.j_star;
@@ -488,7 +487,6 @@ __global__ void k_traceback(const sa_job* __restrict__ jobs, uint32_t job_begin,
     }
     // banded jobs were walked by their band pass
     if (banded || R.w <= 0 || R.wave != wave) return;
-    const sa_job J = jobs[job];
     const JobState st = state[job];
     int si = R.start_i, sj = R.start_j;
     if (plain) {
