@@ -104,6 +104,11 @@ struct Workspace {
     // graph, replayed while a call's launches would be identical (same key)
     cudaGraphExec_t seg_exec = nullptr;
     uint64_t seg_key = 0;
+    // side streams of the band passes (one per band class), forked from and
+    // joined back into the call's stream
+    cudaStream_t side[kNumBand] = {};
+    cudaEvent_t fork = nullptr, join[kNumBand] = {};
+    bool side_ok = false;
     cudaEvent_t ev[16] = {};
     bool ev_ok = false;
     void release() {
@@ -116,6 +121,14 @@ struct Workspace {
         if (seg_exec) cudaGraphExecDestroy(seg_exec);
         seg_exec = nullptr;
         seg_key = 0;
+        if (side_ok) {
+            for (int k = 0; k < kNumBand; k++) {
+                cudaStreamDestroy(side[k]);
+                cudaEventDestroy(join[k]);
+            }
+            cudaEventDestroy(fork);
+        }
+        side_ok = false;
         if (ev_ok)
             for (auto& e : ev) cudaEventDestroy(e);
         ev_ok = false;
@@ -182,6 +195,17 @@ bool use16(const sa_params* P) {
     if (P->mode != SA_LOCAL || P->width == 32 || P->form == SA_FORM_PLAIN) return false;
     const sa_scoring& s = P->sc;
     return s.match <= 2047 && s.mismatch <= 16383 && (int64_t)s.gap_open + s.gap_extend <= 16383;
+}
+
+int ensure_side(Workspace& ws) {
+    if (ws.side_ok) return SA_OK;
+    for (int k = 0; k < kNumBand; k++) {
+        CU(cudaStreamCreateWithFlags(&ws.side[k], cudaStreamNonBlocking));
+        CU(cudaEventCreateWithFlags(&ws.join[k], cudaEventDisableTiming));
+    }
+    CU(cudaEventCreateWithFlags(&ws.fork, cudaEventDisableTiming));
+    ws.side_ok = true;
+    return SA_OK;
 }
 
 int ensure_events(Workspace& ws) {
@@ -532,6 +556,13 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             }
             TRY(ws.band.ensure(std::max<uint64_t>(band_words, 1) * 4, "band arena"));
             bl.arena = ws.band.as<uint32_t>();
+            // the band classes run on side streams, concurrently with each other and
+            // with the rectangle pass (independent jobs); joined before the results
+            const bool fork = !trace.on && (nb[0] || nb[1] || nb[2] || nb[3]);
+            if (fork) {
+                TRY(ensure_side(ws));
+                CU(cudaEventRecord(ws.fork, st));
+            }
             for (int k = 0; k < kNumBand; k++) {
                 BandArgs ba{};
                 ba.ref = X.d_words;
@@ -551,7 +582,9 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
                 ba.tb = ws.tb.as<TbOut>();
                 ba.err_job = &dp->st.bad_walk;
                 if (ba.count) {
-                    launch_band(band_cls(k), ba, heights, st);
+                    if (fork) CU(cudaStreamWaitEvent(ws.side[k], ws.fork, 0));
+                    launch_band(band_cls(k), ba, heights, fork ? ws.side[k] : st);
+                    if (fork) CU(cudaEventRecord(ws.join[k], ws.side[k]));
                     launches++;
                 }
             }
@@ -606,6 +639,9 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
                 CU(cudaGetLastError());
                 trace("traceback");
             }
+            if (fork)
+                for (int k = 0; k < kNumBand; k++)
+                    if (nb[k]) CU(cudaStreamWaitEvent(st, ws.join[k], 0));
             ttb1 = tm.mark();
         } else {
             CU(cudaMemcpyAsync(hp->ovf_count, dp->ovf_count, sizeof(hp->ovf_count), cudaMemcpyDeviceToHost, st));
@@ -693,7 +729,9 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
         stats.ms_stage = tm.ms(t0, t1);
         stats.ms_fill = tm.ms(t1, tfill16 >= 0 ? tfill16 : tfill1);
         stats.ms_rerun = tfill16 >= 0 ? tm.ms(tfill16, tfill1) : 0.f;
-        stats.ms_rect = tm.ms(tfill1, trect1);   // rectangle planning + direction pass
+        // classification and the rectangle pass (the band passes run alongside on
+        // side streams); then the rectangle walks and the join with the band passes
+        stats.ms_rect = tm.ms(tfill1, trect1);
         stats.ms_traceback = tm.ms(trect1, ttb1);
         stats.ms_finalize = tm.ms(tfin0, tfin1);
         stats.ms_total = tm.ms(t0, tfin1);
