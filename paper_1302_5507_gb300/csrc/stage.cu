@@ -182,20 +182,29 @@ __global__ void k_pack_reads(const sa_job* __restrict__ jobs, uint32_t n_jobs,
     const uint8_t* r = reads + J.read_off;
     uint32_t* out = rpack + (size_t)warp * rw;
     bool bad = false;
-    for (uint32_t b = 0; b < n; b += 32) {
-        const uint32_t p = b + (uint32_t)lane;
-        uint32_t c = 0;
-        if (p < n) {
-            int cc = base_code(rc ? r[n - 1 - p] : r[p]);
-            if (cc < 0) { bad = true; cc = 0; }
-            if (rc) cc = 3 - cc;             // complement: A<->T, C<->G
-            c = (uint32_t)cc;
+    // chunks of 32 bases; the loads of up to 8 chunks are issued before any
+    // reduction, so a job waits for one memory latency instead of one per chunk
+    for (uint32_t b0 = 0; b0 < n; b0 += 256) {
+        uint8_t ch[8];
+#pragma unroll
+        for (int t = 0; t < 8; t++) {
+            const uint32_t p = b0 + 32u * t + (uint32_t)lane;
+            ch[t] = p < n ? (rc ? r[n - 1 - p] : r[p]) : (uint8_t)'A';
         }
-        const uint32_t v = c << (2 * (lane & 15));
-        const uint32_t lo = __reduce_or_sync(0xffffffffu, lane < 16 ? v : 0u);
-        const uint32_t hi = __reduce_or_sync(0xffffffffu, lane < 16 ? 0u : v);
-        if (lane == 0) out[b / 16] = lo;
-        if (lane == 1 && b + 16 < n) out[b / 16 + 1] = hi;
+#pragma unroll
+        for (int t = 0; t < 8; t++) {
+            const uint32_t b = b0 + 32u * t;
+            if (b >= n) break;                   // warp-uniform
+            int cc = base_code(ch[t]);
+            if (cc < 0) { bad = true; cc = 0; }
+            if (rc) cc = 3 - cc;                 // complement: A<->T, C<->G
+            const uint32_t c = b + (uint32_t)lane < n ? (uint32_t)cc : 0u;
+            const uint32_t v = c << (2 * (lane & 15));
+            const uint32_t lo = __reduce_or_sync(0xffffffffu, lane < 16 ? v : 0u);
+            const uint32_t hi = __reduce_or_sync(0xffffffffu, lane < 16 ? 0u : v);
+            if (lane == 0) out[b / 16] = lo;
+            if (lane == 1 && b + 16 < n) out[b / 16 + 1] = hi;
+        }
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicMin(bad_job, warp);
 }

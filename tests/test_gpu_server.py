@@ -87,3 +87,28 @@ def test_poll_states_and_budget(sa):
             with pytest.raises(sa.SAError) as e:
                 srv.submit(jobs, r.reads)
             assert e.value.code == sa.SA_EBUSY
+
+
+def test_serving_shaped_requests_and_poll_timeout(sa):
+    """Requests shaped like the serving configuration (n U[50,250], m U[2n,6n]) on a
+    smaller genome match the oracle; a poll with a short timeout on a request that
+    is still running returns SA_ETIMEOUT and the ticket stays valid."""
+    genome = workloads.genome(seed=5, length=2_000_000)
+    reqs = [workloads.serving_request(genome, 5, k, n) for k, n in enumerate((1, 37, 400, 2500))]
+    big = workloads.serving_request(genome, 5, 9, 60_000)
+    with sa.Reference(genome) as ref, sa.Server(ref, max_inflight=1) as srv:
+        tk_big = srv.submit(sa.jobs_array(big.read_off, big.read_len, big.flags, big.ref_pos, big.win_len),
+                            big.reads)
+        rc, _, _ = srv.poll(tk_big, big.n_jobs, sa.cigar_max_ops(big.read_len), timeout_ms=1)
+        assert rc in (sa.SA_ETIMEOUT, sa.SA_OK)
+        if rc == sa.SA_ETIMEOUT:
+            rc, res, cig = srv.poll(tk_big, big.n_jobs, sa.cigar_max_ops(big.read_len))
+            assert rc == sa.SA_OK
+        tickets = [srv.submit(sa.jobs_array(r.read_off, r.read_len, r.flags, r.ref_pos, r.win_len), r.reads)
+                   for r in reqs]
+        for r, tk in zip(reqs, tickets):
+            rc, res, cig = srv.poll(tk, r.n_jobs, sa.cigar_max_ops(r.read_len))
+            assert rc == sa.SA_OK
+            ores, oops = oracle.align(r)
+            bad = compare(res, cig, ores, oops)
+            assert not bad, "\n".join(bad[:10])
