@@ -367,15 +367,29 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
         w16[c] = !plain && cfg_count[c] && use16(P) && want16;
         any16 = any16 || w16[c];
     }
+    // column slots and lane keys for the lane groups / warps the launches below use
+    // (a persistent grid, capped by the items there are)
     int max_groups = 1, max_warps16 = 1;
+    auto blocks_for = [&](int c, int kind, uint64_t jobs, uint32_t jobs_per_warp) {
+        const uint64_t warps = (jobs + jobs_per_warp - 1) / jobs_per_warp;
+        return (int)std::min<uint64_t>(grid_for(c, kind), (warps + 3) / 4);
+    };
     for (int c = 0; c < kNumCfg; c++) {
         if (plain ? c != plain_cfg : !cfg_count[c]) continue;
-        const int kinds[2] = {plain ? (int)kFillPlain : (int)kFillScore, w16[c] ? (int)kFillScore16 : (int)kFillScore};
-        for (int kind : kinds) {
-            const int groups = grid_for(c, kind) * (kBlock / 32) * (32 / cfg_L(c));
-            max_groups = std::max(max_groups, groups);
+        const uint32_t G = 32 / cfg_L(c);
+        const uint64_t count = plain ? std::min<uint64_t>(n_jobs, kPlainBatch) : cfg_count[c];
+        int blocks = 0;
+        if (plain) {
+            blocks = blocks_for(c, kFillPlain, count, G);
+        } else {
+            blocks = blocks_for(c, kFillScore, count, G);      // 32-bit pass or the rerun
+            if (w16[c]) {
+                const int b16 = blocks_for(c, kFillScore16, count, 2 * G);
+                blocks = std::max(blocks, b16);
+                max_warps16 = std::max(max_warps16, b16 * (kBlock / 32));
+            }
         }
-        if (w16[c]) max_warps16 = std::max(max_warps16, grid_for(c, kFillScore16) * (kBlock / 32));
+        max_groups = std::max(max_groups, blocks * (kBlock / 32) * (int)G);
     }
     TRY(ws.colbest.ensure((size_t)max_groups * cb_words(max_m) * 4, "column maxima"));
     if (any16) TRY(ws.lkeys.ensure((size_t)max_warps16 * lane_key_words(max_m) * 4, "lane keys"));

@@ -119,6 +119,22 @@ def test_edge_cases(sa):
                     assert_parity(sa, ref, wl, mode=mode, form=form, scoring=scoring)
 
 
+def test_maximum_sizes(sa):
+    """The largest read (SA_MAX_READ) against the largest window (SA_MAX_WINDOW), and
+    the degenerate extremes around them, in both modes and forms."""
+    rng = np.random.default_rng(17)
+    bases = np.frombuffer(b"ACGT", np.uint8)
+    win = bases[rng.integers(0, 4, sa.SA_MAX_WINDOW)].tobytes().decode()
+    read = win[30000:30000 + sa.SA_MAX_READ]
+    noisy = "".join(c if rng.random() > 0.05 else "ACGT"[rng.integers(0, 4)] for c in read)
+    pairs = [(win, noisy), (win, "A"), ("C", noisy), (win[:sa.SA_MAX_READ], noisy)]
+    wl = _wl_from_pairs(pairs, flags=[0, 1, 0, 1])
+    with sa.Reference(wl.ref) as ref:
+        for mode in (0, 1):
+            for form in (0, 1):
+                assert_parity(sa, ref, wl, mode=mode, form=form)
+
+
 def test_min_score_and_score_only(sa):
     wl = workloads.small(9, 800, n_range=(5, 60), m_range=(5, 120))
     with sa.Reference(wl.ref) as ref:
