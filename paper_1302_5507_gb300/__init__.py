@@ -19,7 +19,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libsa.so")
+# SA_LIBRARY selects another build of the library (the bounds-checked
+# libsa_debug.so in the debug tests); default: the in-tree libsa.so
+LIB_PATH = os.environ.get("SA_LIBRARY") or os.path.join(_HERE, "libsa.so")
 
 SA_OK, SA_PENDING = 0, 1
 SA_EINVAL, SA_ENOMEM, SA_ECUDA, SA_ETIMEOUT, SA_EOVERFLOW, SA_ENOTFOUND, SA_EBUSY = -1, -2, -3, -4, -5, -6, -7

@@ -20,6 +20,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "libsa.so")
+OUT_DEBUG = os.path.join(HERE, "libsa_debug.so")   # SA_DEBUG: bounds-checked stores (tests)
 PROBE = os.path.join(HERE, "libsa_probe.so")   # instruction-throughput probe used by bench.py
 BUILD = os.path.join(HERE, "_build")
 NUM_CFG = 14
@@ -49,22 +50,28 @@ def _deps_mtime() -> float:
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, jobs: int | None = None, verbose: bool = False, debug: bool = False) -> str:
+    """Build libsa.so, or with debug=True libsa_debug.so (-DSA_DEBUG: every indexed
+    global store of the kernels checks its index against its buffer and records the
+    store site instead of writing out of range)."""
+    out = OUT_DEBUG if debug else OUT
+    bdir = BUILD + ("_debug" if debug else "")
+    extra_flags = ["-DSA_DEBUG"] if debug else []
+    os.makedirs(bdir, exist_ok=True)
     dep = _deps_mtime()
     # objects and library built on another machine type are never reused
-    stamp = os.path.join(BUILD, "machine")
+    stamp = os.path.join(bdir, "machine")
     machine = platform.machine()
     if not os.path.exists(stamp) or open(stamp).read().strip() != machine:
         force = True
-    if not force and os.path.exists(OUT) and os.path.getmtime(OUT) >= dep:
-        return OUT
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= dep:
+        return out
     nvcc = _nvcc()
     todo = []
     for src, obj, extra in _units():
-        objp = os.path.join(BUILD, obj)
+        objp = os.path.join(bdir, obj)
         if force or not os.path.exists(objp) or os.path.getmtime(objp) < dep:
-            todo.append([nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", objp])
+            todo.append([nvcc, *ARCH, *FLAGS, *extra_flags, *extra, "-c", src, "-o", objp])
     jobs = jobs or max(1, min(len(todo) or 1, os.cpu_count() or 1))
 
     def run(cmd):
@@ -76,17 +83,18 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
 
     with cf.ThreadPoolExecutor(jobs) as ex:
         list(ex.map(run, todo))
-    objs = [os.path.join(BUILD, obj) for _, obj, _ in _units()]
-    tmp = OUT + ".tmp"
+    objs = [os.path.join(bdir, obj) for _, obj, _ in _units()]
+    tmp = out + ".tmp"
     subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], check=True, capture_output=True)
-    os.replace(tmp, OUT)
-    ptmp = PROBE + ".tmp"
-    subprocess.run([nvcc, *ARCH, *FLAGS, "-shared", "-o", ptmp, os.path.join(CSRC, "dpx_probe.cu")],
-                   check=True, capture_output=True)
-    os.replace(ptmp, PROBE)
+    os.replace(tmp, out)
+    if not debug:
+        ptmp = PROBE + ".tmp"
+        subprocess.run([nvcc, *ARCH, *FLAGS, "-shared", "-o", ptmp, os.path.join(CSRC, "dpx_probe.cu")],
+                       check=True, capture_output=True)
+        os.replace(ptmp, PROBE)
     with open(stamp, "w") as f:
         f.write(machine)
-    return OUT
+    return out
 
 
 if __name__ == "__main__":

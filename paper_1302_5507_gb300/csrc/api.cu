@@ -301,7 +301,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
     PlanBlock* hp = ws.h_plan;
     CU(cudaMemsetAsync(dp, 0, sizeof(PlanBlock), st));
     CU(cudaMemsetAsync(&dp->st.bad_job, 0xff, sizeof(uint32_t) * 2, st));
-    CU(cudaMemsetAsync(&dp->st.bad_walk, 0xff, sizeof(uint32_t), st));
+    CU(cudaMemsetAsync(&dp->st.bad_walk, 0xff, 2 * sizeof(uint32_t), st));   // bad_walk, dbg_site
     TRY(ws.key.ensure((size_t)n_jobs * sizeof(uint16_t), "keys"));
     TRY(ws.counters.ensure(256 * sizeof(uint32_t), "counters"));
     CU(cudaMemsetAsync(ws.counters.p, 0, 256 * sizeof(uint32_t), st));
@@ -407,6 +407,10 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
     base.cb_stride = cb_words(max_m);
     base.lane_keys = any16 ? ws.lkeys.as<uint32_t>() : nullptr;
     base.lk_stride = lane_key_words(max_m);
+    base.n_state = n_jobs;
+    base.cb_cap = ws.colbest.cap / 4;
+    base.lk_cap = any16 ? ws.lkeys.cap / 4 : 0;
+    base.dbg = &dp->st.dbg_site;
     base.rect = ws.rect.as<Rect>();
     base.wave = 0;
     uint32_t* counters = ws.counters.as<uint32_t>();
@@ -595,6 +599,9 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
                 ba.tmp_stride = tmp_stride;
                 ba.tb = ws.tb.as<TbOut>();
                 ba.err_job = &dp->st.bad_walk;
+                ba.region_cap = (uint64_t)((nb[k] + 31) / 32) * bl.warp_stride[k];
+                ba.n_state = n_jobs;
+                ba.dbg = &dp->st.dbg_site;
                 if (ba.count) {
                     if (fork) CU(cudaStreamWaitEvent(ws.side[k], ws.fork, 0));
                     launch_band(band_cls(k), ba, heights, fork ? ws.side[k] : st);
@@ -634,6 +641,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
                     fl.args.pos_count = cfg_count[c];
                     fl.args.item_counter = next_counter();
                     fl.args.arena = ws.arena.as<uint32_t>();
+                    fl.args.arena_cap = ws.arena.cap / 4;
                     fl.args.wave = (int)wv;
                     fl.kind = kFillRect;
                     fl.block = kBlock;
@@ -680,6 +688,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             fl.args.pos_count = nb;
             fl.args.item_counter = next_counter();
             fl.args.arena = ws.arena.as<uint32_t>();
+            fl.args.arena_cap = ws.arena.cap / 4;
             fl.args.plain = 1;
             fl.kind = kFillPlain;
             fl.block = kBlock;
@@ -711,8 +720,11 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
     CU(cudaGetLastError());
     trace("cigar count + scan");
     CU(cudaMemcpyAsync(&hp->totals[1], &dp->totals[1], 8, cudaMemcpyDeviceToHost, st));
-    CU(cudaMemcpyAsync(&hp->st.bad_walk, &dp->st.bad_walk, 4, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(&hp->st.bad_walk, &dp->st.bad_walk, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
+    if (hp->st.dbg_site != 0xffffffffu)
+        return fail(SA_ECUDA, "internal error: a kernel store was out of range (bounds-checked build, "
+                    "store site %u)", hp->st.dbg_site);
     if (hp->st.bad_walk != 0xffffffffu)
         return fail(SA_ECUDA, "internal error: the traceback of job %u left its direction-bit rectangle",
                     hp->st.bad_walk);

@@ -98,7 +98,8 @@ __global__ void __launch_bounds__(128) k_band(BandArgs A) {
     const int rows = R.rows;
     const int dlo = R.d_lo;
     const int32_t GO = in_reg(A.sc.GO), GE = in_reg(A.sc.GE), sa = in_reg(A.sc.a), sb = in_reg(A.sc.b);
-    uint32_t* out = A.arena + (uint64_t)(pos >> 5) * A.warp_stride + (pos & 31);
+    const uint64_t out_base = (uint64_t)(pos >> 5) * A.warp_stride + (pos & 31);
+    uint32_t* out = A.arena + out_base;
     const uint32_t* rp = A.rpack + (size_t)job * A.rw;
     const uint32_t* refw = A.ref + kRefFrontPad;
 
@@ -141,7 +142,10 @@ __global__ void __launch_bounds__(128) k_band(BandArgs A) {
             band_row<B, LOCAL, true>(Hs, Es, words, mmh, i0, border, GO, GE, sa, sb);
         }
 #pragma unroll
-        for (int w = 0; w < W; w++) out[((uint64_t)(j - 1) * W + w) * 32] = words[w];
+        for (int w = 0; w < W; w++) {
+            const uint64_t at = ((uint64_t)(j - 1) * W + w) * 32;
+            if (SA_GUARD(out_base + at < A.region_cap, A.dbg, kSiteBand)) out[at] = words[w];
+        }
     }
 
     const JobState st = A.state[job];
@@ -157,7 +161,7 @@ __global__ void __launch_bounds__(128) k_band(BandArgs A) {
     t.n_rev = e.n_rev;
     t.read_begin = e.bad ? 0 : e.j;
     t.ref_begin_rel = e.bad ? 0 : e.i;
-    A.tb[job] = t;
+    if (SA_GUARD(job < A.n_state, A.dbg, kSiteBandTb)) A.tb[job] = t;
     if (e.bad) atomicMin(A.err_job, job);
 }
 
@@ -202,7 +206,8 @@ __global__ void __launch_bounds__(128) k_band_h(BandArgs A) {
     const int rows = R.rows;
     const int dlo = R.d_lo;
     const int32_t GO = in_reg(A.sc.GO), GE = in_reg(A.sc.GE), sa = in_reg(A.sc.a), sb = in_reg(A.sc.b);
-    uint32_t* out = A.arena + (uint64_t)(pos >> 5) * A.warp_stride + (pos & 31);
+    const uint64_t out_base = (uint64_t)(pos >> 5) * A.warp_stride + (pos & 31);
+    uint32_t* out = A.arena + out_base;
     const uint32_t* rp = A.rpack + (size_t)job * A.rw;
     const uint32_t* refw = A.ref + kRefFrontPad;
 
@@ -238,7 +243,10 @@ __global__ void __launch_bounds__(128) k_band_h(BandArgs A) {
         if (i0 >= 1) band_row_h<B, false>(Hs, Es, words, mmh, i0, GO, GE, sa, sb);
         else band_row_h<B, true>(Hs, Es, words, mmh, i0, GO, GE, sa, sb);
 #pragma unroll
-        for (int w = 0; w < W; w++) out[((uint64_t)(j - 1) * W + w) * 32] = words[w];
+        for (int w = 0; w < W; w++) {
+            const uint64_t at = ((uint64_t)(j - 1) * W + w) * 32;
+            if (SA_GUARD(out_base + at < A.region_cap, A.dbg, kSiteBand)) out[at] = words[w];
+        }
     }
 
     // the walk from the best cell, deciding from the stored heights
@@ -318,7 +326,7 @@ __global__ void __launch_bounds__(128) k_band_h(BandArgs A) {
         t.read_begin = j;
         t.ref_begin_rel = i;
     }
-    A.tb[job] = t;
+    if (SA_GUARD(job < A.n_state, A.dbg, kSiteBandTb)) A.tb[job] = t;
 }
 
 }  // namespace

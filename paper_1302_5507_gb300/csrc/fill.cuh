@@ -68,7 +68,9 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
     const int g = lane % L;
     const int grp = lane / L;
     const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    int32_t* cb = BEST ? A.colbest + (size_t)(gwarp * G + grp) * A.cb_stride + kCbFront : nullptr;
+    const int64_t cb_base = (int64_t)(gwarp * G + grp) * A.cb_stride + kCbFront;     // column 1's slot
+    int32_t* cb = BEST ? A.colbest + cb_base : nullptr;
+    auto cb_ok = [&](int i) { return SA_GUARD((uint64_t)(cb_base + i - 1) < A.cb_cap, A.dbg, kSiteCb32); };
     const Score S = A.sc;
     const uint32_t count = A.count_ptr ? *A.count_ptr : A.pos_count;
     // the score pass and the rectangle direction pass take the match/mismatch term
@@ -306,15 +308,15 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
                         if (LOCAL) {
                             const int32_t cm = __viaddmax_s32(lm, key_shift, cm_up);
                             cm_bot = cm;
-                            if (g == L - 1) cb[i - 1] = cm;
+                            if (g == L - 1 && cb_ok(i)) cb[i - 1] = cm;
                         } else {
-                            if (g == L - 1) cb[i - 1] = HG[K - 1];
+                            if (g == L - 1 && cb_ok(i)) cb[i - 1] = HG[K - 1];
                         }
                     } else if (LOCAL) {
                         const int32_t cm = max(cm_up, lm);
                         cm_bot = cm;
                         if (active) {
-                            if (g == L - 1) cb[i - 1] = cm;
+                            if (g == L - 1 && cb_ok(i)) cb[i - 1] = cm;
                             if (lm > bv) {
                                 bv = lm;
                                 bi = i;
@@ -330,13 +332,15 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
 #pragma unroll
                         for (int r = 1; r < K; r++)
                             if (r == rn) hv = HG[r];
-                        cb[i - 1] = hv - S.GO;
+                        if (cb_ok(i)) cb[i - 1] = hv - S.GO;
                     }
                 }
                 if (DIR && b < nblk) {
 #pragma unroll
-                    for (int k = 0; k < (K + 7) / 8; k++)
-                        A.arena[aoff + ((uint64_t)s * ((K + 7) / 8) + k) * L + g] = dw[k];
+                    for (int k = 0; k < (K + 7) / 8; k++) {
+                        const uint64_t at = aoff + ((uint64_t)s * ((K + 7) / 8) + k) * L + g;
+                        if (SA_GUARD(at < A.arena_cap, A.dbg, kSiteArena)) A.arena[at] = dw[k];
+                    }
                 }
             }
         }
@@ -427,7 +431,7 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
                 st.second = empty ? SA_NO_SCORE : sv;
                 st.second_i = empty ? 0 : si;
                 st.flags = empty ? kStEmpty : 0u;
-                A.state[job] = st;
+                if (SA_GUARD(job < A.n_state, A.dbg, kSiteState32)) A.state[job] = st;
             }
             __syncwarp();
         }

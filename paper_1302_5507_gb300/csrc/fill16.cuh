@@ -59,8 +59,10 @@ __global__ void __launch_bounds__(128) k_fill16(FillArgs A) {
     const int g = lane % L;
     const int grp = lane / L;
     const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    uint32_t* cb = reinterpret_cast<uint32_t*>(A.colbest) + (size_t)(gwarp * G + grp) * A.cb_stride + kCbFront;
-    uint32_t* lk = A.lane_keys + (size_t)gwarp * A.lk_stride + lane;
+    const int64_t cb_base = (int64_t)(gwarp * G + grp) * A.cb_stride + kCbFront;   // column 1's slot
+    uint32_t* cb = reinterpret_cast<uint32_t*>(A.colbest) + cb_base;
+    const uint64_t lk_base = (uint64_t)gwarp * A.lk_stride + lane;
+    uint32_t* lk = A.lane_keys + lk_base;
     const Score S = A.sc;
     const uint32_t count = A.count_ptr ? *A.count_ptr : A.pos_count;
     extern __shared__ __align__(16) int32_t s_prof[];
@@ -205,8 +207,8 @@ __global__ void __launch_bounds__(128) k_fill16(FillArgs A) {
                 const uint32_t cm = __vimax3_s16x2(cm_up, lm, lm);
                 cm_bot = cm;
                 // steps outside the windows land in slack slots / are never read
-                if (g == L - 1) cb[i - 1] = cm;
-                lk[(size_t)s * 32] = lm;
+                if (g == L - 1 && SA_GUARD((uint64_t)(cb_base + i - 1) < A.cb_cap, A.dbg, kSiteCb16)) cb[i - 1] = cm;
+                if (SA_GUARD(lk_base + (uint64_t)s * 32 < A.lk_cap, A.dbg, kSiteLaneKeys)) lk[(size_t)s * 32] = lm;
                 if (8 * b < L && s < g) {      // before this lane's first column
                     reset_col0();
                     h_up_prev = 0u;
@@ -272,7 +274,7 @@ __global__ void __launch_bounds__(128) k_fill16(FillArgs A) {
                 st.second = (empty || si == 0) ? SA_NO_SCORE : sv - beta;
                 st.second_i = empty ? 0 : si;
                 st.flags = (empty ? kStEmpty : 0u) | (ovf ? kStOverflow : 0u);
-                A.state[jobv[h]] = st;
+                if (SA_GUARD(jobv[h] < A.n_state, A.dbg, kSiteState16)) A.state[jobv[h]] = st;
             }
         }
         __syncwarp();

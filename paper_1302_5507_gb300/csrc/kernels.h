@@ -12,6 +12,7 @@ struct PlanStats {                 // filled by the plan kernel (device)
     uint32_t bad_read;             // first job with a non-ACGT base (UINT32_MAX: none)
     uint32_t max_wave;             // last direction-arena wave with work
     uint32_t bad_walk;             // first job whose traceback left its rectangle (internal error)
+    uint32_t dbg_site;             // SA_DEBUG builds: smallest store site that was out of range
     unsigned long long bad_ref_pos;
 };
 
@@ -39,6 +40,9 @@ struct BandArgs {                  // banded direction pass of one class
     uint32_t tmp_stride;
     TbOut* tb;
     unsigned* err_job;             // smallest job whose walk failed (internal error)
+    uint64_t region_cap;           // words of this class's region (SA_DEBUG checks)
+    uint32_t n_state;
+    unsigned* dbg;
 };
 
 struct BandLayout {                // where the traceback finds band nibbles

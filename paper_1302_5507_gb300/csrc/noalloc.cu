@@ -148,6 +148,7 @@ int run(sa_reference* R, const sa_params* P, const sa_job* d_jobs, uint32_t n_jo
     Ctl* ctl = reinterpret_cast<Ctl*>(base);
     CK(cudaMemsetAsync(ctl, 0, sizeof(Ctl), st));
     CK(cudaMemsetAsync(&ctl->st.bad_job, 0xff, 2 * sizeof(uint32_t), st));
+    CK(cudaMemsetAsync(&ctl->st.dbg_site, 0xff, sizeof(uint32_t), st));
     sa::launch_plan(d_jobs, n_jobs, reads_len, (int64_t)V.len, nullptr,
                     reinterpret_cast<uint16_t*>(base + off_key), ctl->hist, &ctl->st, st);
     CK(cudaGetLastError());
@@ -197,6 +198,9 @@ int run(sa_reference* R, const sa_params* P, const sa_job* d_jobs, uint32_t n_jo
     A.state = reinterpret_cast<sa::JobState*>(base + off_state);
     A.colbest = reinterpret_cast<int32_t*>(base + off_cb);
     A.cb_stride = sa::cb_words(hs.max_m);
+    A.n_state = n_jobs;
+    A.cb_cap = (kScratchBytes - off_cb) / 4;
+    A.dbg = &ctl->st.dbg_site;
     fl.kind = sa::kFillScore;
     fl.block = 128;
     int bps = sa::fill_max_blocks_per_sm(c, sa::kFillScore, P->mode);
@@ -210,11 +214,14 @@ int run(sa_reference* R, const sa_params* P, const sa_job* d_jobs, uint32_t n_jo
     sa::launch_fill_cfg(c, fl);
     CK(cudaGetLastError());
 
-    uint32_t bad_read = 0;
+    uint32_t bad_read = 0, dbg_site = 0;
     CK(cudaMemcpyAsync(&bad_read, &ctl->st.bad_read, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&dbg_site, &ctl->st.dbg_site, 4, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (bad_read != 0xffffffffu)
         return err(SA_EINVAL, "job %u: read has a base other than A, C, G, T", bad_read);
+    if (dbg_site != 0xffffffffu)
+        return err(SA_ECUDA, "internal error: a kernel store was out of range (store site %u)", dbg_site);
     k_noalloc_results<<<(n_jobs + 255) / 256, 256, 0, st>>>(
         d_jobs, n_jobs, reinterpret_cast<const sa::JobState*>(base + off_state), P->min_score, d_out);
     CK(cudaGetLastError());

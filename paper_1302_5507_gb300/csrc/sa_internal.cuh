@@ -27,6 +27,20 @@ constexpr int32_t kNeg16 = -16384;
 constexpr int kRefFrontPad = 4;
 constexpr int kRefTailPad = 8;
 
+// SA_DEBUG builds check the index of every indexed global store of the kernels
+// against its buffer; a store out of range is skipped and its site code (the
+// smallest one) recorded in a device word that the call reports as an internal
+// error.  Release builds compile the guard to `true`.
+#ifdef SA_DEBUG
+#define SA_GUARD(ok, word, site) ((ok) || (atomicMin((word), (unsigned)(site)), false))
+#else
+#define SA_GUARD(ok, word, site) true
+#endif
+enum {
+    kSiteCb16 = 1, kSiteLaneKeys = 2, kSiteState16 = 3, kSiteCb32 = 4, kSiteArena = 5, kSiteState32 = 6,
+    kSiteBand = 7, kSiteBandTb = 8, kSiteTraceTb = 9
+};
+
 // Lane-group configurations of the wavefront kernels: a group of L lanes
 // (L divides 32) works on one job (two jobs in the packed 16-bit kernel); each
 // lane owns K consecutive read rows, so a group covers L*K >= n rows.
@@ -163,6 +177,9 @@ struct FillArgs {
     uint32_t cb_stride;           // cb_words(longest window)
     uint32_t* lane_keys;          // 16-bit score pass: per warp scratch, lk_stride words each
     uint32_t lk_stride;
+    // capacities of the buffers above (elements) and the debug word (SA_DEBUG builds)
+    uint64_t n_state, cb_cap, lk_cap, arena_cap;
+    unsigned* dbg;
     const Rect* rect;             // direction pass: per job id
     uint32_t* arena;              // direction bits
     int32_t wave;                 // direction pass: only jobs of this wave
