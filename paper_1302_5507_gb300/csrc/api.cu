@@ -104,10 +104,10 @@ struct Workspace {
     // graph, replayed while a call's launches would be identical (same key)
     cudaGraphExec_t seg_exec = nullptr;
     uint64_t seg_key = 0;
-    // side streams of the band passes (one per band class), forked from and
-    // joined back into the call's stream
-    cudaStream_t side[kNumBand] = {};
-    cudaEvent_t fork = nullptr, join[kNumBand] = {};
+    // side streams (one per length bucket; the band classes use the first four),
+    // forked from and joined back into the call's stream
+    cudaStream_t side[kNumCfg] = {};
+    cudaEvent_t fork = nullptr, join[kNumCfg] = {};
     bool side_ok = false;
     cudaEvent_t ev[16] = {};
     bool ev_ok = false;
@@ -122,7 +122,7 @@ struct Workspace {
         seg_exec = nullptr;
         seg_key = 0;
         if (side_ok) {
-            for (int k = 0; k < kNumBand; k++) {
+            for (int k = 0; k < kNumCfg; k++) {
                 cudaStreamDestroy(side[k]);
                 cudaEventDestroy(join[k]);
             }
@@ -199,7 +199,7 @@ bool use16(const sa_params* P) {
 
 int ensure_side(Workspace& ws) {
     if (ws.side_ok) return SA_OK;
-    for (int k = 0; k < kNumBand; k++) {
+    for (int k = 0; k < kNumCfg; k++) {
         CU(cudaStreamCreateWithFlags(&ws.side[k], cudaStreamNonBlocking));
         CU(cudaEventCreateWithFlags(&ws.join[k], cudaEventDisableTiming));
     }
@@ -368,31 +368,54 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
         any16 = any16 || w16[c];
     }
     // column slots and lane keys for the lane groups / warps the launches below use
-    // (a persistent grid, capped by the items there are)
-    int max_groups = 1, max_warps16 = 1;
+    // (a persistent grid, capped by the items there are).  When the buckets' score
+    // passes together fit about two waves of the GPU, they run concurrently (one
+    // side stream each; a small batch is otherwise a chain of latency-bound
+    // launches) and each bucket gets its own range (cb_group0 / lk_warp0); large
+    // batches run them in turn on one range.  The reruns reuse the first range.
+    int max_groups = 1, max_grid = 1;
+    uint64_t cb_group0[kNumCfg] = {}, lk_warp0[kNumCfg] = {}, groups_total = 0, warps16_total = 0;
     auto blocks_for = [&](int c, int kind, uint64_t jobs, uint32_t jobs_per_warp) {
         const uint64_t warps = (jobs + jobs_per_warp - 1) / jobs_per_warp;
         return (int)std::min<uint64_t>(grid_for(c, kind), (warps + 3) / 4);
     };
+    int n_buckets = 0;
+    uint64_t blocks_sum = 0;
+    for (int c = 0; c < kNumCfg; c++) {
+        if (plain || !cfg_count[c]) continue;
+        n_buckets++;
+        const uint32_t G = 32 / cfg_L(c);
+        blocks_sum += w16[c] ? blocks_for(c, kFillScore16, cfg_count[c], 2 * G)
+                             : blocks_for(c, kFillScore, cfg_count[c], G);
+        max_grid = std::max(max_grid, grid_for(c, w16[c] ? kFillScore16 : kFillScore));
+    }
+    const bool fork_buckets = !plain && !trace.on && n_buckets > 1 && blocks_sum <= 2ull * max_grid;
     for (int c = 0; c < kNumCfg; c++) {
         if (plain ? c != plain_cfg : !cfg_count[c]) continue;
         const uint32_t G = 32 / cfg_L(c);
         const uint64_t count = plain ? std::min<uint64_t>(n_jobs, kPlainBatch) : cfg_count[c];
-        int blocks = 0;
+        int blocks = 0, b_score = 0;
         if (plain) {
-            blocks = blocks_for(c, kFillPlain, count, G);
+            blocks = b_score = blocks_for(c, kFillPlain, count, G);
         } else {
             blocks = blocks_for(c, kFillScore, count, G);      // 32-bit pass or the rerun
+            b_score = blocks;
             if (w16[c]) {
-                const int b16 = blocks_for(c, kFillScore16, count, 2 * G);
-                blocks = std::max(blocks, b16);
-                max_warps16 = std::max(max_warps16, b16 * (kBlock / 32));
+                b_score = blocks_for(c, kFillScore16, count, 2 * G);
+                blocks = std::max(blocks, b_score);
+                const uint64_t w16_warps = (uint64_t)b_score * (kBlock / 32);
+                lk_warp0[c] = fork_buckets ? warps16_total : 0;
+                warps16_total = fork_buckets ? warps16_total + w16_warps : std::max(warps16_total, w16_warps);
             }
         }
+        cb_group0[c] = fork_buckets ? groups_total : 0;
+        if (fork_buckets) groups_total += (uint64_t)b_score * (kBlock / 32) * G;
         max_groups = std::max(max_groups, blocks * (kBlock / 32) * (int)G);
     }
-    TRY(ws.colbest.ensure((size_t)max_groups * cb_words(max_m) * 4, "column maxima"));
-    if (any16) TRY(ws.lkeys.ensure((size_t)max_warps16 * lane_key_words(max_m) * 4, "lane keys"));
+    groups_total = std::max<uint64_t>(groups_total, (uint64_t)max_groups);
+    TRY(ws.colbest.ensure(groups_total * cb_words(max_m) * 4, "column maxima"));
+    if (any16) TRY(ws.lkeys.ensure(std::max<uint64_t>(warps16_total, 1) * lane_key_words(max_m) * 4, "lane keys"));
+    if (fork_buckets) TRY(ensure_side(ws));
 
     FillArgs base{};
     base.ref = X.d_words;
@@ -454,6 +477,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
         CU(cudaGetLastError());
         trace("order + pack reads");
         tm.mark_at(t1);
+        if (fork_buckets) CU(cudaEventRecord(ws.fork, st));
         for (int c = 0; c < kNumCfg; c++) {
             if (!cfg_count[c]) continue;
             FillLaunch fl{};
@@ -461,15 +485,27 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             fl.args.pos_begin = cfg_begin[c];
             fl.args.pos_count = cfg_count[c];
             fl.args.item_counter = next_counter();
+            // this bucket's own column-slot and lane-key ranges
+            fl.args.colbest = base.colbest + cb_group0[c] * base.cb_stride;
+            fl.args.cb_cap = base.cb_cap - cb_group0[c] * base.cb_stride;
+            if (w16[c]) {
+                fl.args.lane_keys = base.lane_keys + lk_warp0[c] * base.lk_stride;
+                fl.args.lk_cap = base.lk_cap - lk_warp0[c] * base.lk_stride;
+            }
             fl.kind = w16[c] ? kFillScore16 : kFillScore;
             fl.block = kBlock;
             const uint32_t per_warp = (32 / cfg_L(c)) * (w16[c] ? 2 : 1);
             const uint64_t warps_needed = (cfg_count[c] + per_warp - 1) / per_warp;
             fl.grid = (int)std::min<uint64_t>(grid_for(c, fl.kind), (warps_needed + 3) / 4);
-            fl.stream = st;
+            fl.stream = fork_buckets ? ws.side[c] : st;
+            if (fork_buckets) CU(cudaStreamWaitEvent(ws.side[c], ws.fork, 0));
             launch_fill_cfg(c, fl);
+            if (fork_buckets) CU(cudaEventRecord(ws.join[c], ws.side[c]));
             if (trace.on) { char b[64]; snprintf(b, sizeof b, "score pass cfg %d (%u jobs)", c, cfg_count[c]); trace(b); }
         }
+        if (fork_buckets)
+            for (int c = 0; c < kNumCfg; c++)
+                if (cfg_count[c]) CU(cudaStreamWaitEvent(st, ws.join[c], 0));
         CU(cudaGetLastError());
         if (any16) {
             tm.mark_at(tfill16);
