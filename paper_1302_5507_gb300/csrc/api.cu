@@ -104,10 +104,13 @@ struct Workspace {
     // graph, replayed while a call's launches would be identical (same key)
     cudaGraphExec_t seg_exec = nullptr;
     uint64_t seg_key = 0;
-    // side streams (one per length bucket; the band classes use the first four),
-    // forked from and joined back into the call's stream
-    cudaStream_t side[kNumCfg] = {};
-    cudaEvent_t fork = nullptr, join[kNumCfg] = {};
+    // side streams, forked from and joined back into the call's stream: one per
+    // length bucket for the score passes ([0, kNumCfg)), one per band class
+    // ([0, kNumBand)) and one per bucket for the rectangle passes, which run beside
+    // the band classes ([kNumBand, kNumBand + kNumCfg))
+    static constexpr int kNumSide = kNumBand + kNumCfg;
+    cudaStream_t side[kNumSide] = {};
+    cudaEvent_t fork = nullptr, join[kNumSide] = {};
     bool side_ok = false;
     cudaEvent_t ev[16] = {};
     bool ev_ok = false;
@@ -122,7 +125,7 @@ struct Workspace {
         seg_exec = nullptr;
         seg_key = 0;
         if (side_ok) {
-            for (int k = 0; k < kNumCfg; k++) {
+            for (int k = 0; k < kNumSide; k++) {
                 cudaStreamDestroy(side[k]);
                 cudaEventDestroy(join[k]);
             }
@@ -199,7 +202,7 @@ bool use16(const sa_params* P) {
 
 int ensure_side(Workspace& ws) {
     if (ws.side_ok) return SA_OK;
-    for (int k = 0; k < kNumCfg; k++) {
+    for (int k = 0; k < Workspace::kNumSide; k++) {
         CU(cudaStreamCreateWithFlags(&ws.side[k], cudaStreamNonBlocking));
         CU(cudaEventCreateWithFlags(&ws.join[k], cudaEventDisableTiming));
     }
@@ -668,7 +671,12 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             launches++;
             const uint32_t waves = wave_words ? (uint32_t)((total_words + wave_words - 1) / wave_words) : 1;
             stats.waves = total_words ? waves : 0;
+            // small batches: the buckets' rectangle passes run concurrently too (each
+            // writes only its jobs' arena ranges); a wave's fork re-records ws.fork,
+            // whose earlier waits were already taken
             for (uint32_t wv = 0; wv < waves; wv++) {
+                const bool rect_fork = fork_buckets && total_words;
+                if (rect_fork) CU(cudaEventRecord(ws.fork, st));
                 for (int c = 0; c < kNumCfg && total_words; c++) {
                     if (!cfg_count[c]) continue;
                     FillLaunch fl{};
@@ -684,11 +692,16 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
                     const uint32_t G = 32 / cfg_L(c);
                     const uint64_t warps_needed = (cfg_count[c] + G - 1) / G;
                     fl.grid = (int)std::min<uint64_t>(grid_for(c, kFillRect), (warps_needed + 3) / 4);
-                    fl.stream = st;
+                    fl.stream = rect_fork ? ws.side[kNumBand + c] : st;
+                    if (rect_fork) CU(cudaStreamWaitEvent(fl.stream, ws.fork, 0));
                     launch_fill_cfg(c, fl);
+                    if (rect_fork) CU(cudaEventRecord(ws.join[kNumBand + c], fl.stream));
                     launches++;
                     if (trace.on) { char b[64]; snprintf(b, sizeof b, "rect pass cfg %d wave %u", c, wv); trace(b); }
                 }
+                if (rect_fork)
+                    for (int c = 0; c < kNumCfg; c++)
+                        if (cfg_count[c]) CU(cudaStreamWaitEvent(st, ws.join[kNumBand + c], 0));
                 if (wv == 0) trect1 = tm.mark();
                 launch_traceback(d_jobs, 0, n_jobs, ws.state.as<JobState>(), ws.rect.as<Rect>(),
                                  ws.arena.as<uint32_t>(), bl, (int)wv, mode, 0, -1, min_score,
