@@ -104,6 +104,7 @@ struct Workspace {
     // graph, replayed while a call's launches would be identical (same key)
     cudaGraphExec_t seg_exec = nullptr;
     uint64_t seg_key = 0;
+    uint64_t seg_seen = 0;         // the previous call's key: a graph is captured on its second sight
     // side streams, forked from and joined back into the call's stream: one per
     // length bucket for the score passes ([0, kNumCfg)), one per band class
     // ([0, kNumBand)) and one per bucket for the rectangle passes, which run beside
@@ -124,6 +125,7 @@ struct Workspace {
         if (seg_exec) cudaGraphExecDestroy(seg_exec);
         seg_exec = nullptr;
         seg_key = 0;
+        seg_seen = 0;
         if (side_ok) {
             for (int k = 0; k < kNumSide; k++) {
                 cudaStreamDestroy(side[k]);
@@ -555,6 +557,11 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
         } else if (ws.seg_exec && ws.seg_key == key) {
             CU(cudaGraphLaunch(ws.seg_exec, st));
             stats.graph_replays++;
+        } else if (ws.seg_seen != key) {
+            // a key seen once (a one-off batch shape, as in serving) runs directly:
+            // capturing and instantiating would cost more than it saves
+            ws.seg_seen = key;
+            TRY(issue_segment());
         } else {
             if (ws.seg_exec) cudaGraphExecDestroy(ws.seg_exec);
             ws.seg_exec = nullptr;

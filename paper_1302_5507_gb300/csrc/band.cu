@@ -3,9 +3,11 @@
 //
 // Every optimal path ending at (i*, j*) with score `best` consumes at most j*
 // read bases, and each insertion costs at least a + e (the match it displaces
-// plus its own extension), each deletion at least e.  With S = a*j* - best this
-// gives #I <= S/(a+e) and #D <= S/e, so the path stays on the diagonals
-// d = i - j in [d* - S/e, d* + S/(a+e)] (d* = i* - j*).  The DP restricted to
+// plus its own extension), each deletion at least e, and a path with gaps of a
+// kind opens at least one of them (o = gap open).  With S = a*j* - best this
+// gives #I <= (S - o)/(a+e) and #D <= (S - o)/e (none when S is below
+// o + a + e, resp. o + e), so the path stays on the diagonals d = i - j in
+// [d* - #D max, d* + #I max] (d* = i* - j*).  The DP restricted to
 // those diagonals (everything else -inf; row 0 and column 0 keep their border
 // values) reproduces every value on such paths and every comparison the
 // traceback makes, so walking its nibbles from (i*, j*) gives the same CIGAR

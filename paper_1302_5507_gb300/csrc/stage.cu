@@ -268,7 +268,11 @@ __global__ void k_rect_plan(const sa_job* __restrict__ jobs, const uint32_t* __r
                 R.cls = kClsDiag;
                 R.d_lo = istar - jstar;
             } else if (e > 0) {
-                const int64_t dmax = slack / e, imax = slack / (sc.a + e);
+                // a path with #D deletions pays at least o + e*#D for them (one
+                // opening at least), one with #I insertions o + (a + e)*#I
+                const int64_t o = (int64_t)sc.GE - sc.GO;                 // gap open magnitude
+                const int64_t dmax = slack >= o + e ? (slack - o) / e : 0;
+                const int64_t imax = slack >= o + sc.a + e ? (slack - o) / (sc.a + e) : 0;
                 const int64_t width = dmax + imax + 1;
                 R.d_lo = (int)((int64_t)(istar - jstar) - dmax);
                 if (allow_band)
