@@ -253,6 +253,91 @@ int sa_server_destroy(sa_server* srv);
 /* Message of the last error on the calling thread ("" if none). */
 const char* sa_last_error(void);
 
+/* ---------------------------------------------------------------------------
+ * Reads with several candidate windows (Methods sections 4 "Effort limit for
+ * dynamic programming" and 5 "Paired-end alignment"; mapping quality from the
+ * Experiments section).
+ *
+ * A read's candidate windows are consecutive jobs of a batch: read r owns jobs
+ * read_first[r] .. read_first[r+1]-1 (read_first: n_reads + 1 ascending uint32
+ * offsets starting at 0; a read may have none).  With paired selection reads
+ * 2p and 2p+1 are the two ends of fragment p.
+ */
+#define SA_NO_JOB   0xFFFFFFFFu
+#define SA_MAPQ_MAX 60
+
+/* sa_read_result.flags */
+#define SA_READ_ALIGNED      1u   /* some candidate aligned (not SA_RES_EMPTY / SA_RES_BELOW_MIN) */
+#define SA_READ_PAIRED       2u   /* selected as one end of a pair */
+#define SA_READ_PROPER       4u   /* properly paired: orientation and fragment length as expected */
+#define SA_READ_MATE_ALIGNED 8u   /* the other end aligned */
+#define SA_READ_REVERSE     16u   /* the chosen job carries SA_RC */
+
+/* orientations of properly paired ends */
+#define SA_PAIR_FR 0   /* one end forward, the other SA_RC; the fragment runs from the forward
+                          end's first reference base to the reverse end's last (Illumina) */
+#define SA_PAIR_FF 1   /* both ends on one strand; forward: end 1 first, SA_RC: end 2 first (SOLiD) */
+
+typedef struct {
+    sa_scoring sc;          /* the scoring the jobs were aligned with (sets the MAPQ scale) */
+    int32_t paired;         /* 0: every read alone; 1: reads 2p, 2p+1 are the ends of pair p */
+    int32_t orientation;    /* SA_PAIR_FR or SA_PAIR_FF */
+    int64_t frag_min;       /* proper fragment lengths, inclusive, 0 <= frag_min <= frag_max */
+    int64_t frag_max;
+} sa_select_params;
+
+typedef struct {            /* 32 bytes, one per read */
+    uint32_t job;           /* chosen job (batch index); SA_NO_JOB if no candidate aligned */
+    int32_t score;          /* its score (0 without one) */
+    int32_t second;         /* best other hit of the read at least n from the chosen reference end
+                               (every aligned candidate's best and its own second), SA_NO_SCORE if none */
+    int32_t mapq;           /* 0..SA_MAPQ_MAX */
+    uint32_t flags;         /* SA_READ_* */
+    uint32_t n_cand;        /* candidates of the read */
+    int64_t frag_len;       /* properly paired: fragment length (both ends); else 0 */
+} sa_read_result;
+
+/* Effort limit: of each read's candidates keep the `ceiling` (>= 1) with the
+ * most supporting seeds (support[j] per job); equal support goes to the
+ * earlier candidate.  Kept jobs are written in their input order to kept
+ * (capacity: all jobs), their batch indices to kept_from, and the per-read
+ * offsets into them to kept_first (n_reads + 1 entries); *n_kept (host) gets
+ * the total.  Device buffers; runs on cuda_stream (NULL: the reference's
+ * stream) and returns when done.  SA_EINVAL for a read_first that is not
+ * ascending from 0 or a zero ceiling.  `ref` only names the device. */
+int sa_effort_limit_dev(sa_reference* ref, const sa_job* jobs, const uint32_t* support,
+                        const uint32_t* read_first, uint32_t n_reads, uint32_t ceiling,
+                        sa_job* kept, uint32_t* kept_from, uint32_t* kept_first,
+                        uint32_t* n_kept, void* cuda_stream);
+/* The same with host buffers (n_jobs = read_first[n_reads]). */
+int sa_effort_limit(sa_reference* ref, const sa_job* jobs, const uint32_t* support,
+                    const uint32_t* read_first, uint32_t n_reads, uint32_t ceiling,
+                    sa_job* kept, uint32_t* kept_from, uint32_t* kept_first, uint32_t* n_kept);
+
+/* Per-read selection from the results of the reads' candidate jobs (results
+ * of sa_align_batch* on jobs[0 .. read_first[n_reads])):
+ *  - best: the aligned candidate with the highest score, then the smallest
+ *    reference end, then the earliest job;
+ *  - second: as in sa_read_result;
+ *  - mapq: SA_MAPQ_MAX without a second hit, 0 if second >= score, else
+ *    20 * (score - second) / (match + mismatch) (integer), at most SA_MAPQ_MAX;
+ *  - paired: among the proper (end 1, end 2) combinations of aligned
+ *    candidates, the highest summed score (then the earliest end-1 job, then
+ *    the earliest end-2 job) is chosen for both ends; the pair's second best is
+ *    the highest proper combination that moves an end by its read length or
+ *    more, and each end's mapq is the larger of the pair's and its own.
+ *    Without a proper combination each end is selected on its own.
+ * Results that ran without a traceback (ref_begin -1) are taken as ungapped:
+ * first base ref_end - n.  Device buffers; runs on cuda_stream (NULL: the
+ * reference's stream) and returns when done. */
+int sa_select_dev(sa_reference* ref, const sa_select_params* sp, const sa_job* jobs,
+                  const sa_result* results, const uint32_t* read_first, uint32_t n_reads,
+                  sa_read_result* out, void* cuda_stream);
+/* The same with host buffers. */
+int sa_select(sa_reference* ref, const sa_select_params* sp, const sa_job* jobs,
+              const sa_result* results, const uint32_t* read_first, uint32_t n_reads,
+              sa_read_result* out);
+
 #ifdef __cplusplus
 }
 #endif

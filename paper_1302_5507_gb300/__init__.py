@@ -32,6 +32,9 @@ SA_RC = 1
 SA_RES_EMPTY, SA_RES_BELOW_MIN = 1, 2
 SA_MAX_READ, SA_MAX_WINDOW = 1024, 65536
 OPS = "MIDNSHP=X"
+SA_NO_JOB, SA_MAPQ_MAX = 0xFFFFFFFF, 60
+SA_READ_ALIGNED, SA_READ_PAIRED, SA_READ_PROPER, SA_READ_MATE_ALIGNED, SA_READ_REVERSE = 1, 2, 4, 8, 16
+SA_PAIR_FR, SA_PAIR_FF = 0, 1
 
 
 class sa_scoring(ctypes.Structure):
@@ -60,13 +63,21 @@ class sa_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class sa_select_params(ctypes.Structure):
+    _fields_ = [("sc", sa_scoring), ("paired", ctypes.c_int32), ("orientation", ctypes.c_int32),
+                ("frag_min", ctypes.c_int64), ("frag_max", ctypes.c_int64)]
+
+
 JOB_DTYPE = np.dtype([("read_off", np.uint64), ("read_len", np.uint32), ("flags", np.uint32),
                       ("ref_pos", np.uint64), ("win_len", np.uint32), ("_pad", np.uint32)])
 RESULT_DTYPE = np.dtype([("score", np.int32), ("second", np.int32), ("read_begin", np.int32),
                          ("read_end", np.int32), ("ref_begin", np.int64), ("ref_end", np.int64),
                          ("second_ref_end", np.int64), ("cigar_off", np.uint32),
                          ("cigar_len", np.uint32), ("flags", np.uint32), ("_pad", np.uint32)])
-assert JOB_DTYPE.itemsize == 32 and RESULT_DTYPE.itemsize == 56
+READ_RESULT_DTYPE = np.dtype([("job", np.uint32), ("score", np.int32), ("second", np.int32),
+                              ("mapq", np.int32), ("flags", np.uint32), ("n_cand", np.uint32),
+                              ("frag_len", np.int64)])
+assert JOB_DTYPE.itemsize == 32 and RESULT_DTYPE.itemsize == 56 and READ_RESULT_DTYPE.itemsize == 32
 
 _lib = None
 _VP, _U32, _U64, _I32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32
@@ -98,11 +109,17 @@ def lib():
         L.sa_tune.argtypes = [_VP, ctypes.POINTER(sa_params), _VP, _U32, _VP, _U64, ctypes.POINTER(_U32)]
         L.sa_plan_get.argtypes = [_VP, _VP, _U64, ctypes.POINTER(_U64)]
         L.sa_plan_set.argtypes = [_VP, _VP, _U64]
+        L.sa_effort_limit_dev.argtypes = [_VP, _VP, _VP, _VP, _U32, _U32, _VP, _VP, _VP,
+                                          ctypes.POINTER(_U32), _VP]
+        L.sa_effort_limit.argtypes = [_VP, _VP, _VP, _VP, _U32, _U32, _VP, _VP, _VP, ctypes.POINTER(_U32)]
+        L.sa_select_dev.argtypes = [_VP, ctypes.POINTER(sa_select_params), _VP, _VP, _VP, _U32, _VP, _VP]
+        L.sa_select.argtypes = [_VP, ctypes.POINTER(sa_select_params), _VP, _VP, _VP, _U32, _VP]
         L.sa_last_error.restype = ctypes.c_char_p
         for name in ("sa_create_reference", "sa_destroy_reference", "sa_align_batch",
                      "sa_align_batch_dev", "sa_align_batch_noalloc", "sa_last_stats",
                      "sa_server_create", "sa_submit",
-                     "sa_poll", "sa_server_destroy", "sa_tune", "sa_plan_get", "sa_plan_set"):
+                     "sa_poll", "sa_server_destroy", "sa_tune", "sa_plan_get", "sa_plan_set",
+                     "sa_effort_limit_dev", "sa_effort_limit", "sa_select_dev", "sa_select"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -204,6 +221,28 @@ def make_params(scoring=(1, 2, 2, 1), mode=SA_LOCAL, want_cigar=True, width=0,
     p.mode, p.want_cigar, p.width = mode, int(bool(want_cigar)), width
     p.min_score, p.form, p.profile = min_score, form, int(bool(profile))
     return p
+
+
+def make_select_params(scoring=(1, 2, 2, 1), paired=False, orientation=SA_PAIR_FR, frag_min=0,
+                       frag_max=0) -> sa_select_params:
+    p = sa_select_params()
+    p.sc.match, p.sc.mismatch, p.sc.gap_open, p.sc.gap_extend = scoring
+    p.paired, p.orientation = int(bool(paired)), orientation
+    p.frag_min, p.frag_max = frag_min, frag_max
+    return p
+
+
+def sa_effort_limit_dev(h, jobs_ptr, support_ptr, first_ptr, n_reads, ceiling, kept_ptr, from_ptr,
+                        kept_first_ptr, stream=None):
+    n = _U32(0)
+    _check(lib().sa_effort_limit_dev(h, jobs_ptr, support_ptr, first_ptr, n_reads, ceiling, kept_ptr,
+                                     from_ptr, kept_first_ptr, ctypes.byref(n), stream))
+    return n.value
+
+
+def sa_select_dev(h, params, jobs_ptr, results_ptr, first_ptr, n_reads, out_ptr, stream=None):
+    return _check(lib().sa_select_dev(h, ctypes.byref(params), jobs_ptr, results_ptr, first_ptr, n_reads,
+                                      out_ptr, stream))
 
 
 def jobs_array(read_off, read_len, flags, ref_pos, win_len) -> np.ndarray:
@@ -309,6 +348,51 @@ class Reference:
                                       cigar.numel() if cigar is not None else 0, st)
         _check(rc)
         return used
+
+
+    # --- reads with several candidate windows (sa_effort_limit*, sa_select*)
+
+    def effort_limit(self, jobs: np.ndarray, support: np.ndarray, read_first: np.ndarray, ceiling: int):
+        """Host buffers: (kept jobs, their batch indices, per-read offsets into them)."""
+        jobs = np.ascontiguousarray(jobs, JOB_DTYPE)
+        support = np.ascontiguousarray(support, np.uint32)
+        first = np.ascontiguousarray(read_first, np.uint32)
+        n_reads = len(first) - 1
+        kept = np.zeros(max(1, len(jobs)), JOB_DTYPE)
+        kept_from = np.zeros(max(1, len(jobs)), np.uint32)
+        kept_first = np.zeros(n_reads + 1, np.uint32)
+        n = _U32(0)
+        _check(lib().sa_effort_limit(self.h, _ptr(jobs), _ptr(support), _ptr(first), n_reads, ceiling,
+                                     _ptr(kept), _ptr(kept_from), _ptr(kept_first), ctypes.byref(n)))
+        return kept[:n.value], kept_from[:n.value], kept_first
+
+    def effort_limit_dev(self, jobs, support, read_first, ceiling, kept, kept_from, kept_first, stream=None):
+        """Device tensors (torch); returns the number of kept jobs."""
+        st = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+        return sa_effort_limit_dev(self.h, ctypes.c_void_p(jobs.data_ptr()), ctypes.c_void_p(support.data_ptr()),
+                                   ctypes.c_void_p(read_first.data_ptr()), read_first.numel() - 1, ceiling,
+                                   ctypes.c_void_p(kept.data_ptr()), ctypes.c_void_p(kept_from.data_ptr()),
+                                   ctypes.c_void_p(kept_first.data_ptr()), st)
+
+    def select(self, jobs: np.ndarray, results: np.ndarray, read_first: np.ndarray,
+               params: sa_select_params | None = None) -> np.ndarray:
+        """Host buffers: per-read results (READ_RESULT_DTYPE)."""
+        params = params or make_select_params()
+        jobs = np.ascontiguousarray(jobs, JOB_DTYPE)
+        results = np.ascontiguousarray(results, RESULT_DTYPE)
+        first = np.ascontiguousarray(read_first, np.uint32)
+        out = np.zeros(len(first) - 1, READ_RESULT_DTYPE)
+        _check(lib().sa_select(self.h, ctypes.byref(params), _ptr(jobs), _ptr(results), _ptr(first),
+                               len(first) - 1, _ptr(out)))
+        return out
+
+    def select_dev(self, jobs, results, read_first, out, params: sa_select_params | None = None, stream=None):
+        """Device tensors (torch) in and out."""
+        params = params or make_select_params()
+        st = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+        return sa_select_dev(self.h, params, ctypes.c_void_p(jobs.data_ptr()), ctypes.c_void_p(results.data_ptr()),
+                             ctypes.c_void_p(read_first.data_ptr()), read_first.numel() - 1,
+                             ctypes.c_void_p(out.data_ptr()), st)
 
 
 class Server:

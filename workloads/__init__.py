@@ -15,6 +15,9 @@ paper's Experiments section and its Methods on paired-end alignment):
 * ``uneven``       n ~ U[50,250], m ~ U[ceil(1.5 n), 6 n] from the mate-rescue genome
 * ``lowsim``       n = 250, m = 1000, divergence {0,5,10,20,30,40} %, geometric indels <= 30
 * ``serving``      3.1 Gbp i.i.d. genome, requests of U[1, 50000] jobs, m ~ U[2n, 6n]
+* ``pairs``        paired 150 bp reads (insert ~ N(500, 50)) on the mate-rescue genome, each
+                   read with its source window, decoy windows and (for some pairs) a planted
+                   copy of end 2's source; per-candidate seed-support counts
 """
 from __future__ import annotations
 
@@ -31,7 +34,7 @@ _SO = os.path.join(_HERE, f"libsynth.{platform.machine()}.so")
 _lib = None
 
 # workload ids (part of the stream keys)
-W_PLAIN, W_MATE, W_UNEVEN, W_LOWSIM, W_SERVE = 1, 2, 3, 4, 5
+W_PLAIN, W_MATE, W_UNEVEN, W_LOWSIM, W_SERVE, W_PAIRS = 1, 2, 3, 4, 5, 6
 # job recipe kinds in synth.c
 _J_PLAIN, _J_MATE, _J_UNEVEN, _J_LOWSIM, _J_SERVE = 1, 2, 3, 4, 5
 FLAG_RC = 1  # job flag: align the reverse complement of the read
@@ -62,6 +65,10 @@ def _load():
                                    u32, u32, u32, u32, u32, u64, u64,
                                    p, p, p, p, p, p, p, i32]
         lib.synth_uniform.argtypes = [u32, u64, u32, u64, u64, u64, p, p]
+        lib.synth_pairs_plant.argtypes = [u32, u64, p, u64, u32, u32, u32, u32, u64, u64]
+        lib.synth_pairs_counts.argtypes = [u32, u64, u64, u32, u32, u32, u64, u64, p]
+        lib.synth_pairs.argtypes = [u32, u64, p, u64, u32, u32, u32, u32, u32, u64, u64, p,
+                                    p, p, p, p, p, p, p, p, i32]
         _lib = lib
     return _lib
 
@@ -247,3 +254,51 @@ def small(seed: int, n_jobs: int, n_range=(1, 40), m_range=(1, 90), ref_len: int
             reads[o:o + nn] = letters[rng.integers(0, alphabet, nn)]
     flags = (rng.random(n_jobs) < 0.25).astype(np.uint32) * FLAG_RC
     return Workload("small", ref, reads, off, n, flags, pos, m, pos.copy(), {"seed": seed})
+
+
+@dataclass
+class PairedWorkload(Workload):
+    """Candidate jobs of paired reads: the jobs of read r are read_first[r] ..
+    read_first[r+1]-1 (reads 2p and 2p+1 are the ends of pair p); every
+    candidate carries its seed support."""
+    read_first: np.ndarray = None      # uint64, n_reads + 1
+    support: np.ndarray = None         # uint32 per job
+    read_truth: np.ndarray = None      # uint64 source position per read
+
+    @property
+    def n_reads(self) -> int:
+        return int(self.read_first.shape[0]) - 1
+
+
+def pairs(seed: int = 1, n_pairs: int = 100_000, genome_len: int = 100_000_000, read: int = 150,
+          decoy_max: int = 40, dup: float = 0.1, first_item: int = 0) -> PairedWorkload:
+    """Paired reads with several candidate windows each (source window, a shifted
+    copy of it for 20 % of reads, U[0, decoy_max] uniform decoys, and for a
+    fraction ``dup`` of pairs a window on a planted copy of end 2's source).
+    The planted copies go into a private copy of the mate-rescue genome."""
+    lib = _load()
+    ref = genome(seed, genome_len).copy()
+    dup_ppm = int(round(dup * 1e6))
+    lib.synth_pairs_plant(W_PAIRS, seed, _ptr(ref), len(ref), read, 500, 50, dup_ppm, first_item,
+                          n_pairs)
+    counts = np.empty(2 * n_pairs, np.uint32)
+    lib.synth_pairs_counts(W_PAIRS, seed, len(ref), read, min(decoy_max, 61), dup_ppm, first_item,
+                           n_pairs, _ptr(counts))
+    read_first = np.zeros(2 * n_pairs + 1, np.uint64)
+    read_first[1:] = np.cumsum(counts.astype(np.uint64))
+    n_jobs = int(read_first[-1])
+    reads = np.empty(2 * n_pairs * read, np.uint8)
+    read_truth = np.empty(2 * n_pairs, np.uint64)
+    off = np.empty(n_jobs, np.uint64)
+    rl = np.empty(n_jobs, np.uint32)
+    fl = np.empty(n_jobs, np.uint32)
+    pos = np.empty(n_jobs, np.uint64)
+    wl = np.empty(n_jobs, np.uint32)
+    sup = np.empty(n_jobs, np.uint32)
+    lib.synth_pairs(W_PAIRS, seed, _ptr(ref), len(ref), read, 500, 50, min(decoy_max, 61), dup_ppm,
+                    first_item, n_pairs, _ptr(read_first), _ptr(reads), _ptr(read_truth), _ptr(off),
+                    _ptr(rl), _ptr(fl), _ptr(pos), _ptr(wl), _ptr(sup), _threads())
+    truth = np.repeat(read_truth, counts.astype(np.int64))
+    return PairedWorkload("pairs", ref, reads, off, rl, fl, pos, wl, truth,
+                          {"seed": seed, "workload": W_PAIRS}, read_first=read_first, support=sup,
+                          read_truth=read_truth)

@@ -21,6 +21,7 @@
  *   W3  uneven:         n ~ U[50,250], m ~ U[ceil(1.5n), 6n]
  *   W4  low similarity: n = 250, m = 1000, divergence 0..40 %
  *   W5  serving:        requests of U[1, 50000] jobs, m ~ U[2n, 6n]
+ *   W6  pairs:          paired 150 bp reads, several candidate windows per read
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -365,4 +366,198 @@ void synth_uniform(uint32_t workload, uint64_t seed, uint32_t purpose, uint64_t 
         if (out_u) out_u[k] = uni(&r, lo, hi);
         if (out_ppm) out_ppm[k] = (uint32_t)uni(&r, 1, 1000000);
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* W6  paired reads with several candidate windows per read                  */
+/*                                                                          */
+/* Pair p: fragment start uniform, insert ~ round(N(mean, sd)); end 1 is the  */
+/* fragment's first n bases (forward), end 2 the reverse complement of its   */
+/* last n bases (flag SA_RC on its candidates), both mutated like the mate-   */
+/* rescue mates.  Each read gets the window around its source (both sides    */
+/* padded by U[8, 40]), with probability 20 % a second window around the     */
+/* same source shifted by U[1, 20], U[0, decoy_max] decoy windows at uniform  */
+/* positions (m = n + U[16, 80]).  For the pairs chosen with probability      */
+/* dup_ppm a copy (0.5 % substitutions) is planted at a uniform position:     */
+/* half of them copy end 2's source only, half the whole fragment (a          */
+/* segmental duplication); the ends whose source was copied get a window      */
+/* around the copy too.                                                       */
+/* Candidates are shuffled; each carries a seed-support count (source and     */
+/* planted copy U[6, 24], shifted U[3, 12], decoys U[1, 16]).                 */
+
+#define W_PAIRS_PURPOSE_COUNT 8
+#define W_PAIRS_PURPOSE_DUP   9
+#define W_PAIRS_PURPOSE_PAIR  10
+#define W_PAIRS_PURPOSE_CAND  11
+
+typedef struct {
+    uint32_t workload; uint64_t seed;
+    uint64_t ref_len; uint32_t n;
+    uint32_t insert_mean, insert_sd;
+    uint32_t decoy_max; uint32_t dup_ppm;
+} pair_recipe;
+
+static void pair_sources(const pair_recipe* pr, uint64_t item, uint64_t* src1, uint64_t* src2) {
+    rng_t r = stream(pr->workload, pr->seed, W_PAIRS_PURPOSE_PAIR, item);
+    uint64_t span = (uint64_t)pr->insert_mean + 4ULL * pr->insert_sd + 200;
+    uint64_t pos1 = uni(&r, 200, pr->ref_len > span + 200 ? pr->ref_len - span : 200);
+    int64_t ins = normal_int(&r, pr->insert_mean, pr->insert_sd);
+    if (ins < (int64_t)pr->n) ins = pr->n;
+    *src1 = pos1;
+    *src2 = pos1 + (uint64_t)ins - pr->n;
+}
+
+/* planted copy for pair item: 0 none, 1 end 2's source, 2 the whole fragment;
+ * *dst is where the copied span starts */
+static int pair_dup(const pair_recipe* pr, uint64_t item, uint64_t* dst) {
+    rng_t r = stream(pr->workload, pr->seed, W_PAIRS_PURPOSE_DUP, item);
+    if (!bern(&r, pr->dup_ppm)) return 0;
+    const int kind = bern(&r, 500000) ? 2 : 1;
+    const uint64_t room = (uint64_t)pr->insert_mean + 4ULL * pr->insert_sd + 400;
+    *dst = uni(&r, 100, pr->ref_len > room + 100 ? pr->ref_len - room : 100);
+    return kind;
+}
+
+/* candidate counts of read (2 item + end): source, shifted, decoys, planted copy */
+static void read_counts(const pair_recipe* pr, uint64_t item, int end, uint32_t* shifted,
+                        uint32_t* decoys, uint32_t* dup) {
+    rng_t r = stream(pr->workload, pr->seed, W_PAIRS_PURPOSE_COUNT, 2 * item + (uint64_t)end);
+    *decoys = (uint32_t)uni(&r, 0, pr->decoy_max);
+    *shifted = (uint32_t)bern(&r, 200000);
+    uint64_t dst;
+    const int kind = pair_dup(pr, item, &dst);
+    *dup = (kind == 2 || (kind == 1 && end == 1)) ? 1u : 0u;
+}
+
+/* Pass 0 (sequential; writes into ref): plant the copies. */
+void synth_pairs_plant(uint32_t workload, uint64_t seed, char* ref, uint64_t ref_len, uint32_t n,
+                       uint32_t insert_mean, uint32_t insert_sd, uint32_t dup_ppm,
+                       uint64_t first_item, uint64_t n_pairs) {
+    pair_recipe pr = { workload, seed, ref_len, n, insert_mean, insert_sd, 0, dup_ppm };
+    for (uint64_t p = 0; p < n_pairs; p++) {
+        uint64_t item = first_item + p, s1, s2, dst;
+        const int kind = pair_dup(&pr, item, &dst);
+        if (!kind) continue;
+        pair_sources(&pr, item, &s1, &s2);
+        const uint64_t from = kind == 2 ? s1 : s2;
+        const uint64_t len = s2 + n + 40 - from;
+        rng_t r = stream(workload, seed, W_PAIRS_PURPOSE_DUP + 100, item);
+        for (uint64_t k = 0; k < len && from + k < ref_len && dst + k < ref_len; k++) {
+            char c = ref[from + k];
+            if (bern(&r, 5000)) c = ACGT[(code_of(c) + 1 + (int)uni(&r, 0, 2)) & 3];
+            ref[dst + k] = c;
+        }
+    }
+}
+
+/* Pass 1: candidates per read (2 n_pairs reads). */
+void synth_pairs_counts(uint32_t workload, uint64_t seed, uint64_t ref_len, uint32_t n,
+                        uint32_t decoy_max, uint32_t dup_ppm, uint64_t first_item, uint64_t n_pairs,
+                        uint32_t* out_count) {
+    if (decoy_max > 61) decoy_max = 61;        /* at most 64 candidates a read */
+    pair_recipe pr = { workload, seed, ref_len, n, 0, 0, decoy_max, dup_ppm };
+    for (uint64_t p = 0; p < n_pairs; p++)
+        for (int e = 0; e < 2; e++) {
+            uint32_t sh, dc, du;
+            read_counts(&pr, first_item + p, e, &sh, &dc, &du);
+            out_count[2 * p + e] = 1 + sh + dc + du;
+        }
+}
+
+typedef struct {
+    const pair_recipe* pr; const char* ref; uint64_t first_item;
+    const uint64_t* read_first;
+    char* reads; uint64_t* truth;
+    uint64_t* read_off; uint32_t* read_len; uint32_t* flags; uint64_t* ref_pos; uint32_t* win_len;
+    uint32_t* support;
+    uint64_t lo, hi;
+} pair_task;
+
+static void window_around(rng_t* r, uint64_t src, uint32_t n, uint64_t ref_len, uint64_t* pos, uint32_t* m) {
+    uint64_t padl = uni(r, 8, 40), padr = uni(r, 8, 40);
+    uint64_t a = src > padl ? src - padl : 0;
+    uint64_t b = src + n + padr;
+    if (b > ref_len) b = ref_len;
+    *pos = a;
+    *m = (uint32_t)(b - a);
+}
+
+static void* pair_worker(void* p) {
+    pair_task* t = (pair_task*)p;
+    const pair_recipe* pr = t->pr;
+    const uint32_t n = pr->n;
+    mut_model mm = { 10000, 3000, 1, 10, 0 };
+    for (uint64_t q = t->lo; q < t->hi; q++) {
+        uint64_t item = t->first_item + q, src[2], dst = 0;
+        pair_sources(pr, item, &src[0], &src[1]);
+        const int kind = pair_dup(pr, item, &dst);
+        const uint64_t from = kind == 2 ? src[0] : src[1];
+        for (int e = 0; e < 2; e++) {
+            const uint64_t rd = 2 * q + (uint64_t)e;
+            rng_t r = stream(pr->workload, pr->seed, W_PAIRS_PURPOSE_CAND, 2 * item + (uint64_t)e);
+            char* out = t->reads + rd * n;
+            mutate(&r, t->ref, pr->ref_len, src[e], n, &mm, out);
+            if (e == 1) revcomp_inplace(out, n);
+            t->truth[rd] = src[e];
+            uint32_t sh, dc, du;
+            read_counts(pr, item, e, &sh, &dc, &du);
+            const uint32_t k_n = 1 + sh + dc + du;
+            uint64_t pos[64]; uint32_t m[64], sup[64];
+            uint32_t k = 0;
+            window_around(&r, src[e], n, pr->ref_len, &pos[k], &m[k]); sup[k++] = (uint32_t)uni(&r, 6, 24);
+            if (sh) {
+                uint64_t s = src[e] + uni(&r, 1, 20);
+                window_around(&r, s, n, pr->ref_len, &pos[k], &m[k]); sup[k++] = (uint32_t)uni(&r, 3, 12);
+            }
+            if (du) {
+                window_around(&r, dst + (src[e] - from), n, pr->ref_len, &pos[k], &m[k]);
+                sup[k++] = (uint32_t)uni(&r, 6, 24);
+            }
+            for (uint32_t d = 0; d < dc && k < 64; d++) {
+                uint32_t mm_len = n + (uint32_t)uni(&r, 16, 80);
+                pos[k] = uni(&r, 0, pr->ref_len - mm_len);
+                m[k] = mm_len;
+                sup[k++] = (uint32_t)uni(&r, 1, 16);
+            }
+            /* Fisher-Yates shuffle of the k_n candidates */
+            for (uint32_t i = k_n; i > 1; i--) {
+                uint32_t j = (uint32_t)uni(&r, 0, i - 1);
+                uint64_t tp = pos[i - 1]; pos[i - 1] = pos[j]; pos[j] = tp;
+                uint32_t tm = m[i - 1]; m[i - 1] = m[j]; m[j] = tm;
+                uint32_t ts = sup[i - 1]; sup[i - 1] = sup[j]; sup[j] = ts;
+            }
+            const uint64_t c0 = t->read_first[rd];
+            for (uint32_t c = 0; c < k_n; c++) {
+                t->read_off[c0 + c] = rd * n;
+                t->read_len[c0 + c] = n;
+                t->flags[c0 + c] = e == 1 ? 1u : 0u;
+                t->ref_pos[c0 + c] = pos[c];
+                t->win_len[c0 + c] = m[c];
+                t->support[c0 + c] = sup[c];
+            }
+        }
+    }
+    return NULL;
+}
+
+/* Pass 2: reads (n bases each, read r at r * n), per-read truth, candidates. */
+void synth_pairs(uint32_t workload, uint64_t seed, const char* ref, uint64_t ref_len, uint32_t n,
+                 uint32_t insert_mean, uint32_t insert_sd, uint32_t decoy_max, uint32_t dup_ppm,
+                 uint64_t first_item, uint64_t n_pairs, const uint64_t* read_first,
+                 char* reads, uint64_t* truth, uint64_t* read_off, uint32_t* read_len,
+                 uint32_t* flags, uint64_t* ref_pos, uint32_t* win_len, uint32_t* support,
+                 int n_threads) {
+    if (decoy_max > 61) decoy_max = 61;
+    pair_recipe pr = { workload, seed, ref_len, n, insert_mean, insert_sd, decoy_max, dup_ppm };
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > 256) n_threads = 256;
+    if ((uint64_t)n_threads > n_pairs) n_threads = n_pairs ? (int)n_pairs : 1;
+    pthread_t th[256]; pair_task tk[256];
+    for (int t = 0; t < n_threads; t++) {
+        tk[t] = (pair_task){ &pr, ref, first_item, read_first, reads, truth, read_off, read_len,
+                             flags, ref_pos, win_len, support,
+                             n_pairs * t / n_threads, n_pairs * (t + 1) / n_threads };
+        pthread_create(&th[t], NULL, pair_worker, &tk[t]);
+    }
+    for (int t = 0; t < n_threads; t++) pthread_join(th[t], NULL);
 }
