@@ -46,10 +46,12 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving latency run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "pairs"],
                     help="c2 (default): the mate-rescue headline line; c1 plain windows (plain and "
                          "batched forms, both modes) plus mate rescue in GLOCAL; c3 uneven lengths, "
-                         "c4 low similarity, c5 serving sweep: one extra JSON line each (1 GPU)")
+                         "c4 low similarity, c5 serving sweep, pairs: paired reads with several "
+                         "candidate windows each (effort limit, alignment, selection): one extra "
+                         "JSON line each (1 GPU)")
     return ap.parse_args()
 
 
@@ -522,6 +524,110 @@ def device_line(sa, ref, wl, args, label, widths=(0,), cigar=(True, False), mode
     return {"config": label, "jobs": int(wl.n_jobs), "cells": int(wl.cells), "steps": args.steps, "rows": rows}
 
 
+def hbm_peak():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def pairs_line(sa, ref, w, args, ceiling=30, frag=(300, 700), min_score=None):
+    """One step = effort limit + alignment (with CIGAR) + paired selection, all on
+    device buffers, timed with CUDA events on the stream the library runs on.
+    min_score: candidates scoring below it get no traceback and count as unaligned."""
+    import torch
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.current_stream()
+    jobs = sa.jobs_array(w.read_off, w.read_len, w.flags, w.ref_pos, w.win_len)
+    n_jobs, n_reads = len(jobs), w.n_reads
+    dj = torch.from_numpy(jobs.view(np.uint8)).to(dev)
+    ds = torch.from_numpy(w.support.view(np.int32)).to(dev)
+    df = torch.from_numpy(w.read_first.astype(np.uint32).view(np.int32)).to(dev)
+    dr = torch.from_numpy(w.reads).to(dev)
+    dk = torch.empty(n_jobs * 32, dtype=torch.uint8, device=dev)
+    dfrom = torch.empty(n_jobs, dtype=torch.int32, device=dev)
+    dkf = torch.empty(n_reads + 1, dtype=torch.int32, device=dev)
+    dres = torch.empty(n_jobs * 56, dtype=torch.uint8, device=dev)
+    dcig = torch.empty(sa.cigar_max_ops(w.read_len), dtype=torch.int32, device=dev)
+    dout = torch.empty(n_reads * 32, dtype=torch.uint8, device=dev)
+    params = sa.make_params(min_score=sa.SA_NO_SCORE if min_score is None else min_score)
+    sel = sa.make_select_params(paired=True, frag_min=frag[0], frag_max=frag[1])
+
+    def step(ev=None):
+        if ev: ev[0].record(st)
+        n = ref.effort_limit_dev(dj, ds, df, ceiling, dk, dfrom, dkf, stream=st)
+        if ev: ev[1].record(st)
+        ref.align_dev(dk[: n * 32], dr, dres[: n * 56], dcig, params, stream=st)
+        if ev: ev[2].record(st)
+        ref.select_dev(dk[: n * 32], dres[: n * 56], dkf, dout, sel, stream=st)
+        if ev: ev[3].record(st)
+        return n
+    for _ in range(max(3, args.warmup)):
+        n_kept = step()
+    torch.cuda.synchronize()
+    kept_np = dk[: n_kept * 32].cpu().numpy().view(sa.JOB_DTYPE)
+    cells = int(np.dot(kept_np["read_len"].astype(np.int64), kept_np["win_len"].astype(np.int64)))
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(st)
+    for k in range(args.steps):
+        step(evs[k])
+    t1.record(st)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / args.steps
+    ph = {name: float(np.mean([e[i].elapsed_time(e[i + 1]) for e in evs]))
+          for i, name in enumerate(("ms_effort_limit", "ms_align", "ms_select"))}
+    out = dout.cpu().numpy().view(sa.READ_RESULT_DTYPE)
+    peak, basis = hbm_peak()
+    # algorithmic bytes: effort limit reads every candidate (job 32 B + support 4 B) and
+    # writes the kept ones (job 32 B + index 4 B) and the offsets; the selection reads
+    # every kept job and result (32 + 56 B) once and writes 32 B a read
+    b_lim = n_jobs * 36 + n_kept * 36 + (n_reads + 1) * 12
+    b_sel = n_kept * 88 + n_reads * 36
+    near = np.abs(kept_np["ref_pos"][np.minimum(out["job"], n_kept - 1)].astype(np.int64) -
+                  w.read_truth.astype(np.int64)) < 100
+    st_align = ref.stats()
+    return {"min_score": min_score, "traced_jobs": int(st_align["diag_jobs"] + st_align["band_jobs"] +
+                                                       st_align["rect_jobs"]),
+            "reads": n_reads, "candidates": n_jobs, "kept_jobs": n_kept, "cells": cells, "steps": args.steps,
+            "ms_per_step": ms, "gcups": cells / (ms / 1e3) / 1e9, "reads_per_s": n_reads / (ms / 1e3),
+            "phases_ms": ph,
+            "select_roofline": {"bound": "hbm", "achieved": b_sel / (ph["ms_select"] / 1e3) / 1e9,
+                                "peak": peak, "peak_basis": basis, "unit": "GB/s",
+                                "frac": b_sel / (ph["ms_select"] / 1e3) / 1e9 / peak, "bytes": b_sel,
+                                "note": "phase time of the sa_select_dev call (check + selection "
+                                        "kernels and the status read)"},
+            "effort_limit_roofline": {"bound": "hbm", "achieved": b_lim / (ph["ms_effort_limit"] / 1e3) / 1e9,
+                                      "peak": peak, "unit": "GB/s",
+                                      "frac": b_lim / (ph["ms_effort_limit"] / 1e3) / 1e9 / peak,
+                                      "bytes": b_lim},
+            "proper_fraction": float((out["flags"] & sa.SA_READ_PROPER > 0).mean()),
+            "chosen_at_source_fraction": float(near.mean()),
+            "mapq_hist": {str(q): int((out["mapq"] == q).sum()) for q in (0, 20, 40, 60)}}
+
+
+def pairs_cpu_baseline(w, ceiling=30, frag=(300, 700), budget_s=10.0):
+    """The oracle's effort limit, alignment and paired selection on the first pairs
+    (bounded sample), GCUPS over the kept cells."""
+    import oracle
+    from oracle import select as S
+    n_pairs = 200
+    while True:
+        r_hi = 2 * n_pairs
+        sub_first = w.read_first[: r_hi + 1].astype(np.int64)
+        t0 = time.perf_counter()
+        kept, kf = S.effort_limit(w.support.astype(np.int64), sub_first, ceiling)
+        sub = w.subset(kept)
+        res, _ = oracle.align(sub)
+        S.select(sub.flags, sub.read_len, res, kf, paired=True, frag_min=frag[0], frag_max=frag[1])
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 4 or 2 * n_pairs > w.n_reads // 2:
+            return {"value": sub.cells / dt / 1e9, "unit": "GCUPS", "cores": oracle.threads(), "kind": "oracle",
+                    "sample": f"first {n_pairs} pairs ({sub.n_jobs} kept jobs, {sub.cells:.3g} cells, {dt:.1f} s)"}
+        n_pairs *= 4
+
+
 def run_config(args):
     """Extra measurement lines of the uneven, low-similarity and serving configurations."""
     import torch
@@ -559,6 +665,16 @@ def run_config(args):
             line["tuned_plan"] = {"classes_tuned": classes, "tune_seconds": tune_s,
                                   "cfg_of_length": {str(n): int(plan[n]) for n in (50, 100, 150, 200, 250)},
                                   "rows": tuned["rows"]}
+    elif args.config == "pairs":
+        w = workloads.pairs(seed=1, n_pairs=(args.jobs or 100_000))
+        with sa.Reference(w.ref) as ref:
+            rows = [pairs_line(sa, ref, w, args, min_score=ms) for ms in (None, 30)]
+        line = {"config": f"pairs: {w.n_reads // 2} read pairs (150 bp, insert N(500,50)), {w.n_jobs} "
+                          f"candidate windows, effort limit 30, FR fragment 300-700; rows without a score "
+                          f"threshold and with min_score 30 (candidates below it are not traced and count "
+                          f"as unaligned)", "rows": rows}
+        if not args.no_cpu:
+            line["cpu_baseline"] = pairs_cpu_baseline(w)
     elif args.config == "c4":
         wl = workloads.lowsim(seed=1, n_jobs=args.jobs or 500_000)
         with sa.Reference(wl.ref) as ref:

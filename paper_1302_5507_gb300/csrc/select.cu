@@ -13,12 +13,11 @@
 // contiguous range of the batch, read_first[r] .. read_first[r+1]-1, so a warp
 // reads them with coalesced loads and reduces with shuffles.
 //
-// Effort limit: the candidate ranking key is (support << 32) | ~index, unique
-// per candidate and larger for more support, then for the earlier candidate.
-// The warp finds the ceiling-th largest key of the read bit by bit from the
-// top (a radix select: keep a bit when at least `ceiling` keys reach the prefix
-// with it set), then keeps exactly the keys at or above it, compacted in input
-// order with ballots.
+// Effort limit: candidates rank by support, then by input order.  The warp
+// finds the ceiling-th largest support of the read bit by bit from the top (a
+// radix select: keep a bit when at least `ceiling` supports reach the prefix
+// with it set), keeps every candidate above it and the earliest ones equal to
+// it up to `ceiling` in all, compacted in input order with ballots.
 //
 // Selection: the best aligned candidate (score, then smallest reference end,
 // then earliest job); the second best is the highest hit of the read (every
@@ -26,7 +25,8 @@
 // least n from the chosen one's; MAPQ 60 without a second hit, 0 when it ties,
 // else 20 per (match + mismatch) score units of the gap, at most 60.  Paired:
 // lanes take the (end 1, end 2) candidate combinations; the proper one with the
-// highest summed score wins (ties: earlier end-1 job, then earlier end-2 job);
+// highest summed score wins (ties: earlier end-1 job, then earlier end-2 job;
+// lanes hold end-2 candidates in registers and end-1 ones are broadcast);
 // the pair's second best is the best proper combination that moves at least
 // one end by its read length or more.
 #include <algorithm>
@@ -74,10 +74,6 @@ __global__ void k_effort_count(const uint32_t* __restrict__ read_first, uint32_t
     count[r] = min(hi - lo, ceiling);
 }
 
-__device__ __forceinline__ uint64_t rank_key(uint32_t support, uint32_t c) {
-    return ((uint64_t)support << 32) | (uint64_t)(0xffffffffu - c);
-}
-
 __global__ void __launch_bounds__(32 * kWarps)
 k_effort_select(const sa_job* __restrict__ jobs, const uint32_t* __restrict__ support,
                 const uint32_t* __restrict__ read_first, uint32_t n_reads, uint32_t ceiling,
@@ -100,26 +96,36 @@ k_effort_select(const sa_job* __restrict__ jobs, const uint32_t* __restrict__ su
         }
         return;
     }
-    // radix select of the ceiling-th largest key
-    uint64_t prefix = 0;
-    const bool small = L <= 32;
-    const uint64_t mine = (small && lane < L) ? rank_key(__ldg(support + lo + lane), lane) : 0ull;
-    for (int bit = 63; bit >= 0; bit--) {
-        const uint64_t cand = prefix | (1ull << bit);
+    // radix select of the ceiling-th largest support (thr); of the candidates
+    // with support thr the earliest `quota` are kept
+    const bool regs = L <= 64;                           // supports held in two registers
+    const uint32_t s0 = (regs && lane < L) ? __ldg(support + lo + lane) : 0u;
+    const uint32_t s1 = (regs && 32 + lane < L) ? __ldg(support + lo + 32 + lane) : 0u;
+    auto count_ge = [&](uint32_t x) -> uint32_t {        // candidates with support >= x
         uint32_t n = 0;
-        if (small) {
-            n = (lane < L && mine >= cand) ? 1u : 0u;
+        if (regs) {
+            n = (lane < L && s0 >= x ? 1u : 0u) + (32 + lane < L && s1 >= x ? 1u : 0u);
         } else {
-            for (uint32_t c = lane; c < L; c += 32) n += rank_key(__ldg(support + lo + c), c) >= cand ? 1u : 0u;
+            for (uint32_t c = lane; c < L; c += 32) n += __ldg(support + lo + c) >= x ? 1u : 0u;
         }
-        n = __reduce_add_sync(0xffffffffu, n);
-        if (n >= ceiling) prefix = cand;
+        return __reduce_add_sync(0xffffffffu, n);
+    };
+    uint32_t thr = 0;
+    for (int bit = 31; bit >= 0; bit--) {
+        const uint32_t cand = thr | (1u << bit);
+        if (count_ge(cand) >= ceiling) thr = cand;
     }
-    // keep the keys >= prefix (exactly `ceiling`), in input order
-    uint32_t written = 0;
+    const uint32_t above = thr == 0xffffffffu ? 0u : count_ge(thr + 1u);
+    const uint32_t quota = ceiling - above;              // >= 1 candidates with support thr
+    // keep support > thr, and the first `quota` with support == thr, in input order
+    uint32_t written = 0, eq_seen = 0;
     for (uint32_t c0 = 0; c0 < L; c0 += 32) {
         const uint32_t c = c0 + lane;
-        const bool keep = c < L && (small ? mine : rank_key(__ldg(support + lo + c), c)) >= prefix;
+        const uint32_t sv = c < L ? (regs ? (c0 == 0 ? s0 : s1) : __ldg(support + lo + c)) : 0u;
+        const bool eq = c < L && sv == thr;
+        const unsigned me = __ballot_sync(0xffffffffu, eq);
+        const uint32_t eq_before = eq_seen + (uint32_t)__popc(me & ((1u << lane) - 1u));
+        const bool keep = c < L && (sv > thr || (eq && eq_before < quota));
         const unsigned m = __ballot_sync(0xffffffffu, keep);
         if (keep) {
             const uint64_t at = base + written + (uint32_t)__popc(m & ((1u << lane) - 1u));
@@ -127,6 +133,7 @@ k_effort_select(const sa_job* __restrict__ jobs, const uint32_t* __restrict__ su
             kept_from[at] = lo + c;
         }
         written += (uint32_t)__popc(m);
+        eq_seen += (uint32_t)__popc(me);
     }
 }
 
@@ -266,6 +273,35 @@ __device__ __forceinline__ int64_t frag_of(const Cand& c1, const Cand& c2, int o
     return (frag >= fmin && frag <= fmax) ? frag : -1;
 }
 
+// Every (end-1 a, end-2 b) combination of aligned candidates, k = a * L2 + b:
+// lane t holds end-2 candidate b0 + t of the current chunk in registers and
+// end-1 candidate a0 + t of the current chunk, which the loop broadcasts to
+// the whole warp one at a time (no memory access per combination).
+template <typename F>
+__device__ __forceinline__ void for_each_combo(const sa_job* jobs, const sa_result* res, uint32_t lo1,
+                                               uint32_t L1, uint32_t lo2, uint32_t L2, uint32_t lane, F&& f) {
+    for (uint32_t b0 = 0; b0 < L2; b0 += 32) {
+        const uint32_t b = b0 + lane;
+        Cand cb = {};
+        if (b < L2) cb = load_cand(jobs, res, lo2 + b);
+        for (uint32_t a0 = 0; a0 < L1; a0 += 32) {
+            Cand mine = {};
+            if (a0 + lane < L1) mine = load_cand(jobs, res, lo1 + a0 + lane);
+            const uint32_t na = min(32u, L1 - a0);
+            for (uint32_t t = 0; t < na; t++) {
+                Cand ca;
+                ca.ok = __shfl_sync(0xffffffffu, (int)mine.ok, (int)t) != 0;
+                ca.rc = __shfl_sync(0xffffffffu, (int)mine.rc, (int)t) != 0;
+                ca.score = __shfl_sync(0xffffffffu, mine.score, (int)t);
+                ca.n = __shfl_sync(0xffffffffu, mine.n, (int)t);
+                ca.end = __shfl_sync(0xffffffffu, mine.end, (int)t);
+                ca.begin = __shfl_sync(0xffffffffu, mine.begin, (int)t);
+                if (ca.ok && cb.ok) f(ca, cb, (uint64_t)(a0 + t) * L2 + b);
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(32 * kWarps) k_select(SelArgs A) {
     const uint32_t unit = blockIdx.x * kWarps + threadIdx.x / 32;
     const uint32_t lane = threadIdx.x & 31u;
@@ -290,17 +326,13 @@ __global__ void __launch_bounds__(32 * kWarps) k_select(SelArgs A) {
     int32_t best_sum = INT32_MIN;
     uint64_t best_k = UINT64_MAX;
     int64_t best_frag = 0;
-    for (uint64_t k = lane; k < combos; k += 32) {
-        const uint32_t j1 = lo1 + (uint32_t)(k / L2), j2 = lo2 + (uint32_t)(k % L2);
-        const Cand c1 = load_cand(A.jobs, A.res, j1);
-        if (!c1.ok) continue;
-        const Cand c2 = load_cand(A.jobs, A.res, j2);
-        if (!c2.ok) continue;
-        const int64_t fr = frag_of(c1, c2, A.orientation, A.frag_min, A.frag_max);
-        if (fr < 0) continue;
-        const int32_t sum = c1.score + c2.score;
-        if (sum > best_sum || (sum == best_sum && k < best_k)) { best_sum = sum; best_k = k; best_frag = fr; }
-    }
+    if (combos)
+        for_each_combo(A.jobs, A.res, lo1, L1, lo2, L2, lane, [&](const Cand& c1, const Cand& c2, uint64_t k) {
+            const int64_t fr = frag_of(c1, c2, A.orientation, A.frag_min, A.frag_max);
+            if (fr < 0) return;
+            const int32_t sum = c1.score + c2.score;
+            if (sum > best_sum || (sum == best_sum && k < best_k)) { best_sum = sum; best_k = k; best_frag = fr; }
+        });
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const int32_t ts = __shfl_xor_sync(0xffffffffu, best_sum, o);
@@ -326,16 +358,11 @@ __global__ void __launch_bounds__(32 * kWarps) k_select(SelArgs A) {
     const Cand c1 = load_cand(A.jobs, A.res, c1j), c2 = load_cand(A.jobs, A.res, c2j);
     // the pair's second best: a proper combination moving an end by its read length or more
     int32_t pair_second = SA_NO_SCORE;
-    for (uint64_t k = lane; k < combos; k += 32) {
-        const uint32_t j1 = lo1 + (uint32_t)(k / L2), j2 = lo2 + (uint32_t)(k % L2);
-        const Cand d1 = load_cand(A.jobs, A.res, j1);
-        if (!d1.ok) continue;
-        const Cand d2 = load_cand(A.jobs, A.res, j2);
-        if (!d2.ok) continue;
-        if (dist(d1.end, c1.end) < c1.n && dist(d2.end, c2.end) < c2.n) continue;
-        if (frag_of(d1, d2, A.orientation, A.frag_min, A.frag_max) < 0) continue;
+    for_each_combo(A.jobs, A.res, lo1, L1, lo2, L2, lane, [&](const Cand& d1, const Cand& d2, uint64_t) {
+        if (dist(d1.end, c1.end) < c1.n && dist(d2.end, c2.end) < c2.n) return;
+        if (frag_of(d1, d2, A.orientation, A.frag_min, A.frag_max) < 0) return;
         pair_second = max(pair_second, d1.score + d2.score);
-    }
+    });
     pair_second = __reduce_max_sync(0xffffffffu, pair_second);
     const int32_t pair_mapq = mapq_of(best_sum, pair_second, A.a, A.b);
     const int32_t s1 = warp_second(A.res, lo1, hi1, c1.end, c1.n, lane);
