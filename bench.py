@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving latency run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--probe-ops", action="store_true",
+                    help="print the measured issue rate (lane-ops per SM per clock) of every "
+                         "operation of the throughput probe and exit")
     ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "pairs"],
                     help="c2 (default): the mate-rescue headline line; c1 plain windows (plain and "
                          "batched forms, both modes) plus mate rescue in GLOCAL; c3 uneven lengths, "
@@ -148,6 +151,36 @@ def direction_bound(stats, wl):
             "full_matrix_nibbles_gcups": gbs / 0.5,
             "note": "the band passes write bytes only for cells on the diagonals an optimal path "
                     "can use, so their data is a small fraction of 0.5 B per cell of the batch"}
+
+
+PROBE_OPS = ("viaddmax_s32", "vimax3_s32", "vimax3_s32_relu", "iadd_s32", "imax_s32", "imad_s32",
+             "viaddmax_s16x2", "vimax3_s16x2", "prmt", "vmaxs4 (s8x4)", "vaddss4 (s8x4)")
+
+
+def probe_all_ops():
+    """Issue rate of every probe operation, lane-ops per SM per clock (median of 5,
+    at the median SM clock sampled meanwhile)."""
+    import ctypes
+    import torch
+    from paper_1302_5507_gb300 import build as sa_build
+    torch.cuda.set_device(0)
+    sa_build.build()
+    lib = ctypes.CDLL(sa_build.PROBE)
+    lib.sa_probe_ops_per_sm_clk.restype = ctypes.c_double
+    lib.sa_probe_ops_per_sm_clk.argtypes = [ctypes.c_int, ctypes.c_double]
+    rates = {op: [] for op in range(len(PROBE_OPS))}
+    with ClockSampler(0) as clk:
+        for _ in range(5):
+            for op in rates:
+                rates[op].append(lib.sa_probe_ops_per_sm_clk(op, 1e-6))
+    mhz = clk.summary()["sm_mhz"] or 2070.0
+    out = {"sm_mhz": mhz, "unit": "lane-ops per SM per clock"}
+    for op, name in enumerate(PROBE_OPS):
+        if name in ("iadd_s32", "imax_s32"):
+            continue                   # their chains are folded by the compiler: not a rate
+        good = [r for r in rates[op] if r > 0]
+        out[name] = round(statistics.median(good) / (mhz * 1e6), 2) if good else None
+    print(json.dumps(out), flush=True)
 
 
 def dpx_lane_ops_per_sm_clk(local_rank: int):
@@ -700,6 +733,10 @@ def main():
     dist = None
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.probe_ops:
+        if rank == 0:
+            probe_all_ops()
         return
     if args.config != "c2":
         if rank == 0:

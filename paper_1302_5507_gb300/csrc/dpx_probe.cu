@@ -15,7 +15,9 @@ constexpr int kChains = 8;
 
 enum Op {
     kViaddmaxS32 = 0, kVimax3S32 = 1, kVimax3ReluS32 = 2, kIaddS32 = 3, kImaxS32 = 4, kImadS32 = 5,
-    kViaddmaxS16x2 = 6, kVimax3S16x2 = 7, kPrmt = 8, kNumOps = 9
+    kViaddmaxS16x2 = 6, kVimax3S16x2 = 7, kPrmt = 8,
+    kVmaxS8x4 = 9, kVaddS8x4 = 10,                 // 4-way byte SIMD (signed max, saturating add)
+    kNumOps = 11
 };
 
 template <int OP>
@@ -38,6 +40,8 @@ __global__ void __launch_bounds__(256) k_probe(int iters, uint32_t seed, uint32_
                 if (OP == kViaddmaxS16x2) x[c] = __viaddmax_s16x2(x[c], y, z);
                 if (OP == kVimax3S16x2) x[c] = __vimax3_s16x2(x[c], y, z + c);
                 if (OP == kPrmt) x[c] = __byte_perm(x[c], y, 0x5410 + c);
+                if (OP == kVmaxS8x4) x[c] = __vmaxs4(x[c], y + c);
+                if (OP == kVaddS8x4) x[c] = __vaddss4(x[c], y);
             }
             y += 1;
         }
@@ -87,6 +91,8 @@ extern "C" double sa_probe_ops_per_sm_clk(int op, double sm_mhz) {
     case kViaddmaxS16x2: ms = run<kViaddmaxS16x2>(blocks, iters, sink); break;
     case kVimax3S16x2: ms = run<kVimax3S16x2>(blocks, iters, sink); break;
     case kPrmt: ms = run<kPrmt>(blocks, iters, sink); break;
+    case kVmaxS8x4: ms = run<kVmaxS8x4>(blocks, iters, sink); break;
+    case kVaddS8x4: ms = run<kVaddS8x4>(blocks, iters, sink); break;
     default: break;
     }
     cudaFree(sink);
