@@ -424,6 +424,8 @@ def run_ours(args, rank, world, dist):
                 "roofline": roofline,
                 "clocks": clocks,
                 "phases_ms": phases,
+                "traceback_classes": {"diagonal": int(stats["diag_jobs"]), "band": int(stats["band_jobs"]),
+                                      "rectangle": int(stats["rect_jobs"])},
                 "plain_form": plain}
 
     # --- serving latency (coalescing server), rank 0 only: a short run on this genome
