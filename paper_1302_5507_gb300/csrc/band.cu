@@ -260,12 +260,43 @@ __global__ void __launch_bounds__(128) k_band_h(BandArgs A) {
         const uint32_t v = (out[((uint64_t)(jj - 1) * W + (k >> 2)) * 32] >> (8 * (k & 3))) & 255u;
         return v == 255u ? kNeg32 : (int32_t)v;
     };
+    // Heights on the walk's diagonal: the walk mostly moves diagonally, staying in
+    // one height word column, so the words of the next kPre rows of that column
+    // are loaded together (independent loads, one latency) and reused until the
+    // walk leaves them.
+    uint32_t p0 = 0, p1 = 0, p2 = 0, p3 = 0, p4 = 0, p5 = 0, p6 = 0, p7 = 0;   // 8 rows (scalars:
+    int pre_col = -1, pre_row = 0;                       // stay in registers) of word column pre_col,
+    auto diag_height = [&](int ii, int jj) -> int32_t {  // rows pre_row, pre_row-1, ...; = height(ii, jj)
+        if (jj == 0) return ii >= 0 ? 0 : kNeg32;
+        const int k = ii - jj - dlo;
+        if (k < 0 || k >= B) return kNeg32;
+        int d = pre_row - jj;
+        if ((k >> 2) != pre_col || d < 0 || d >= 8) {
+            pre_col = k >> 2;
+            pre_row = jj;
+            d = 0;
+            const uint32_t* col = out + (uint64_t)pre_col * 32;
+            auto at = [&](int row) -> uint32_t { return row >= 1 ? col[(uint64_t)(row - 1) * W * 32] : 0u; };
+            p0 = at(jj); p1 = at(jj - 1); p2 = at(jj - 2); p3 = at(jj - 3);
+            p4 = at(jj - 4); p5 = at(jj - 5); p6 = at(jj - 6); p7 = at(jj - 7);
+        }
+        const uint32_t lo = d & 4 ? (d & 2 ? (d & 1 ? p7 : p6) : (d & 1 ? p5 : p4))
+                                  : (d & 2 ? (d & 1 ? p3 : p2) : (d & 1 ? p1 : p0));
+        const uint32_t v = (lo >> (8 * (k & 3))) & 255u;
+        return v == 255u ? kNeg32 : (int32_t)v;
+    };
+    // window and read bases, one cached 16-base word each
+    uint64_t tw_at = ~0ull, rw_at = ~0ull;
+    uint32_t tw = 0, rw_word = 0;
     auto base_t = [&](int ii) -> uint32_t {              // window base of column ii >= 1
         const uint64_t p = J.ref_pos + (uint64_t)(ii - 1);
-        return (__ldg(refw + (p >> 4)) >> (2 * (p & 15))) & 3u;
+        if ((p >> 4) != tw_at) { tw_at = p >> 4; tw = __ldg(refw + tw_at); }
+        return (tw >> (2 * (p & 15))) & 3u;
     };
     auto base_r = [&](int jj) -> uint32_t {              // read base of row jj >= 1
-        return (__ldg(rp + ((jj - 1) >> 4)) >> (2 * ((jj - 1) & 15))) & 3u;
+        const uint64_t q = (uint64_t)(jj - 1) >> 4;
+        if (q != rw_at) { rw_at = q; rw_word = __ldg(rp + q); }
+        return (rw_word >> (2 * ((jj - 1) & 15))) & 3u;
     };
     uint32_t* ops = A.tmp_ops + (uint64_t)job * A.tmp_stride;
     const uint32_t cap = A.tmp_stride;
@@ -286,7 +317,7 @@ __global__ void __launch_bounds__(128) k_band_h(BandArgs A) {
         if (--budget < 0 || nrev >= (int)cap - 1) { bad = true; break; }
         if (state == 0) {
             if (i == 0 || j == 0 || h <= 0) break;
-            const int32_t hd = height(i - 1, j - 1);
+            const int32_t hd = diag_height(i - 1, j - 1);
             if (hd != kNeg32 && hd + (base_t(i) == base_r(j) ? sa : sb) == h) {
                 emit(0u);
                 i--; j--; h = hd;
