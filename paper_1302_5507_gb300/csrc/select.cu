@@ -275,8 +275,9 @@ __device__ __forceinline__ int64_t frag_of(const Cand& c1, const Cand& c2, int o
 
 // Every (end-1 a, end-2 b) combination of aligned candidates, k = a * L2 + b:
 // lane t holds end-2 candidate b0 + t of the current chunk in registers and
-// end-1 candidate a0 + t of the current chunk, which the loop broadcasts to
-// the whole warp one at a time (no memory access per combination).
+// end-1 candidate a0 + t of the current chunk; the aligned ones of the end-1
+// chunk are broadcast to the whole warp one at a time (no memory access per
+// combination; unaligned candidates, e.g. below min_score, cost nothing).
 template <typename F>
 __device__ __forceinline__ void for_each_combo(const sa_job* jobs, const sa_result* res, uint32_t lo1,
                                                uint32_t L1, uint32_t lo2, uint32_t L2, uint32_t lane, F&& f) {
@@ -284,19 +285,22 @@ __device__ __forceinline__ void for_each_combo(const sa_job* jobs, const sa_resu
         const uint32_t b = b0 + lane;
         Cand cb = {};
         if (b < L2) cb = load_cand(jobs, res, lo2 + b);
+        if (!__any_sync(0xffffffffu, cb.ok)) continue;
         for (uint32_t a0 = 0; a0 < L1; a0 += 32) {
             Cand mine = {};
             if (a0 + lane < L1) mine = load_cand(jobs, res, lo1 + a0 + lane);
-            const uint32_t na = min(32u, L1 - a0);
-            for (uint32_t t = 0; t < na; t++) {
+            // only the aligned end-1 candidates of the chunk are broadcast
+            for (unsigned live = __ballot_sync(0xffffffffu, mine.ok); live; live &= live - 1u) {
+                const int t = __ffs(live) - 1;
                 Cand ca;
-                ca.ok = __shfl_sync(0xffffffffu, (int)mine.ok, (int)t) != 0;
-                ca.rc = __shfl_sync(0xffffffffu, (int)mine.rc, (int)t) != 0;
-                ca.score = __shfl_sync(0xffffffffu, mine.score, (int)t);
-                ca.n = __shfl_sync(0xffffffffu, mine.n, (int)t);
-                ca.end = __shfl_sync(0xffffffffu, mine.end, (int)t);
-                ca.begin = __shfl_sync(0xffffffffu, mine.begin, (int)t);
-                if (ca.ok && cb.ok) f(ca, cb, (uint64_t)(a0 + t) * L2 + b);
+                ca.ok = true;
+                const int rcn = __shfl_sync(0xffffffffu, (mine.n << 1) | (int)mine.rc, t);
+                ca.rc = (rcn & 1) != 0;
+                ca.n = rcn >> 1;
+                ca.score = __shfl_sync(0xffffffffu, mine.score, t);
+                ca.end = __shfl_sync(0xffffffffu, mine.end, t);
+                ca.begin = __shfl_sync(0xffffffffu, mine.begin, t);
+                if (cb.ok) f(ca, cb, (uint64_t)(a0 + (uint32_t)t) * L2 + b);
             }
         }
     }
