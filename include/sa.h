@@ -250,6 +250,19 @@ int sa_poll(sa_server* srv, uint64_t ticket, int timeout_ms, sa_result* out, uin
             uint64_t cigar_cap, uint64_t* cigar_used);
 int sa_server_destroy(sa_server* srv);
 
+/* Counters of a server since its creation (host side, exact). */
+typedef struct {
+    uint64_t submitted;         /* requests accepted by sa_submit */
+    uint64_t completed;         /* requests finished with SA_OK */
+    uint64_t failed;            /* requests finished with an error */
+    uint64_t batches;           /* device batches run (a failed batch rerun request by request counts once) */
+    uint64_t coalesced;         /* requests that joined the batch of an earlier queued request */
+    uint64_t admission_stalls;  /* batches whose head request first waited for the memory budget */
+    uint64_t max_queue;         /* longest queue seen at submit */
+    uint64_t jobs;              /* jobs of all batches */
+} sa_server_stats;
+int sa_server_get_stats(sa_server* srv, sa_server_stats* out);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char* sa_last_error(void);
 

@@ -63,6 +63,14 @@ class sa_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class sa_server_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in ("submitted", "completed", "failed", "batches", "coalesced",
+                                                "admission_stalls", "max_queue", "jobs")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class sa_select_params(ctypes.Structure):
     _fields_ = [("sc", sa_scoring), ("paired", ctypes.c_int32), ("orientation", ctypes.c_int32),
                 ("frag_min", ctypes.c_int64), ("frag_max", ctypes.c_int64)]
@@ -106,6 +114,7 @@ def lib():
         L.sa_submit.argtypes = [_VP, _VP, _U32, _VP, _U64, ctypes.POINTER(_U64)]
         L.sa_poll.argtypes = [_VP, _U64, ctypes.c_int, _VP, _VP, _U64, ctypes.POINTER(_U64)]
         L.sa_server_destroy.argtypes = [_VP]
+        L.sa_server_get_stats.argtypes = [_VP, ctypes.POINTER(sa_server_stats)]
         L.sa_tune.argtypes = [_VP, ctypes.POINTER(sa_params), _VP, _U32, _VP, _U64, ctypes.POINTER(_U32)]
         L.sa_plan_get.argtypes = [_VP, _VP, _U64, ctypes.POINTER(_U64)]
         L.sa_plan_set.argtypes = [_VP, _VP, _U64]
@@ -119,7 +128,8 @@ def lib():
                      "sa_align_batch_dev", "sa_align_batch_noalloc", "sa_last_stats",
                      "sa_server_create", "sa_submit",
                      "sa_poll", "sa_server_destroy", "sa_tune", "sa_plan_get", "sa_plan_set",
-                     "sa_effort_limit_dev", "sa_effort_limit", "sa_select_dev", "sa_select"):
+                     "sa_effort_limit_dev", "sa_effort_limit", "sa_select_dev", "sa_select",
+                     "sa_server_get_stats"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -320,6 +330,27 @@ class Reference:
         buf = (ctypes.c_uint8 * len(plan)).from_buffer_copy(plan)
         _check(lib().sa_plan_set(self.h, buf, len(plan)))
 
+    def save_plan(self, path: str) -> None:
+        """Write the plan as a JSON cache: the configuration of every read length and
+        the width of every configuration (readable), and the plan bytes that
+        load_plan installs."""
+        import json
+        raw = self.plan()
+        body = np.frombuffer(raw[8:], np.uint8)
+        with open(path, "w") as f:
+            json.dump({"format": "libsa plan", "cfg_of_read_length": body[:SA_MAX_READ + 1].tolist(),
+                       "width_of_cfg": body[SA_MAX_READ + 1:].astype(np.int8).tolist(),
+                       "plan_hex": raw.hex()}, f)
+
+    def load_plan(self, path: str) -> None:
+        """Install a plan written by save_plan (sa_plan_set validates it)."""
+        import json
+        with open(path) as f:
+            doc = json.load(f)
+        if doc.get("format") != "libsa plan":
+            raise ValueError(f"{path} is not a libsa plan cache")
+        self.set_plan(bytes.fromhex(doc["plan_hex"]))
+
     def align(self, jobs: np.ndarray, reads: np.ndarray, params: sa_params | None = None,
               out: np.ndarray | None = None, cigar: np.ndarray | None = None, stream=None):
         """Host buffers in, host results out (sa_align_batch)."""
@@ -419,6 +450,12 @@ class Server:
             return rc, None, None
         _check(rc)
         return rc, None, None
+
+    def stats(self) -> dict:
+        """sa_server_get_stats: request, batch and admission counters."""
+        st = sa_server_stats()
+        _check(lib().sa_server_get_stats(self.h, ctypes.byref(st)))
+        return st.as_dict()
 
     def close(self):
         if self.h:

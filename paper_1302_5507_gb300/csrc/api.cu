@@ -18,6 +18,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kernels.h"
 
 using namespace sa;
@@ -268,6 +270,22 @@ struct Trace {
 };
 constexpr int kBlock = 128;
 
+// NVTX ranges on the host timeline of a call: one for the call and one per
+// phase (a profiler shows them above the phase's launches; free without one)
+struct NvtxPhases {
+    bool open = false;
+    explicit NvtxPhases(const char* call) { nvtxRangePushA(call); }
+    void next(const char* phase) {
+        if (open) nvtxRangePop();
+        nvtxRangePushA(phase);
+        open = true;
+    }
+    ~NvtxPhases() {
+        if (open) nvtxRangePop();
+        nvtxRangePop();
+    }
+};
+
 int check_bad_read(PlanBlock* dp, PlanBlock* hp, cudaStream_t st) {
     CU(cudaMemcpyAsync(&hp->st.bad_read, &dp->st.bad_read, 4, cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
@@ -296,6 +314,8 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
     if (P->profile) TRY(ensure_events(ws));
     Timer tm(ws, st, P->profile != 0);
     Trace trace(st);
+    NvtxPhases nvtx("sa_align_batch");
+    nvtx.next("plan");
     const int t0 = tm.mark();
     uint32_t launches = 0;
 
@@ -455,6 +475,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
         t1 = tm.mark();
     }
     if (!plain) {
+        nvtx.next("score segment");
         if (any16) TRY(ws.ovf.ensure((size_t)n_jobs * 4, "overflow list"));
         // the score segment: stage (order, packed reads), one persistent score-pass
         // launch per non-empty length bucket (16-bit pairs where chosen), then the
@@ -589,6 +610,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             TRY(ws.blists.ensure((size_t)n_jobs * kNumBand * 4, "band lists"));
             uint32_t* lists[kNumBand];
             for (int k = 0; k < kNumBand; k++) lists[k] = ws.blists.as<uint32_t>() + (size_t)k * n_jobs;
+            nvtx.next("traceback classes");
             launch_rect_plan(d_jobs, ws.order.as<uint32_t>(), n_jobs, dp->cfg_begin, ws.state.as<JobState>(), sc,
                              min_score, 1, ws.rect.as<Rect>(), ws.sizes.as<uint64_t>(), lists,
                              dp->cls_count, st);
@@ -622,6 +644,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             bl.arena = ws.band.as<uint32_t>();
             // the band classes run on side streams, concurrently with each other and
             // with the rectangle pass (independent jobs); joined before the results
+            nvtx.next("band and rectangle passes, walks");
             const bool fork = !trace.on && (nb[0] || nb[1] || nb[2] || nb[3]);
             if (fork) {
                 TRY(ensure_side(ws));
@@ -729,6 +752,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
     } else {
         // --- plain form: fixed-size batches in job order, one configuration for the
         // longest read, whole-window direction bits, one fill + one traceback each
+        nvtx.next("plain form: fill and traceback batches");
         const int c = plain_cfg;
         const int L = cfg_L(c), K = cfg_K(c);
         const uint32_t G = 32 / L;
@@ -767,6 +791,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
     }
 
     // --- results
+    nvtx.next("results");
     const int tfin0 = tm.mark();
     launch_cigar_count(d_jobs, n_jobs, ws.state.as<JobState>(), ws.tb.as<TbOut>(), mode,
                        want_cigar ? 1 : 0, min_score, ws.count.as<uint32_t>(), st);
@@ -882,6 +907,7 @@ struct sa_server {
     std::map<uint64_t, std::shared_ptr<Request>> tickets;
     uint64_t next_ticket = 1;
     bool stop = false;
+    sa_server_stats counters{};        // guarded by mu
     struct Slot {
         Workspace ws;
         sa_stats last{};
@@ -1008,11 +1034,18 @@ void slot_main(sa_server* S, sa_server::Slot* slot) {
             std::unique_lock<std::mutex> lk(S->mu);
             // FIFO admission: the head request starts when the memory budget allows;
             // the requests queued behind it join its device batch while they fit
+            bool stalled = false;      // the head request waited for the memory budget
             S->cv_work.wait(lk, [&] {
-                return S->stop || (!S->queue.empty() &&
-                                   S->in_use + S->queue.front()->est_bytes <= S->budget);
+                if (S->stop) return true;
+                if (S->queue.empty()) return false;
+                if (S->in_use + S->queue.front()->est_bytes > S->budget) {
+                    stalled = true;
+                    return false;
+                }
+                return true;
             });
             if (S->stop) return;
+            if (stalled) S->counters.admission_stalls++;
             uint64_t nj = 0;
             while (!S->queue.empty()) {
                 const auto& q = S->queue.front();
@@ -1025,6 +1058,9 @@ void slot_main(sa_server* S, sa_server::Slot* slot) {
                 S->queue.pop_front();
             }
             S->in_use += est;
+            S->counters.batches++;
+            S->counters.coalesced += batch.size() - 1;
+            S->counters.jobs += nj;
         }
         int rc = run_batch(S, slot, batch, hjobs, hreads, hout, hcig);
         std::vector<int> rcs(batch.size(), rc);
@@ -1044,6 +1080,8 @@ void slot_main(sa_server* S, sa_server::Slot* slot) {
                 Request& rq = *batch[k];
                 rq.err = msgs[k];
                 rq.rc = rcs[k];
+                if (rcs[k] == SA_OK) S->counters.completed++;
+                else S->counters.failed++;
                 rq.jobs.clear();
                 rq.jobs.shrink_to_fit();
                 rq.reads.clear();
@@ -1420,6 +1458,8 @@ int sa_submit(sa_server* S, const sa_job* jobs, uint32_t n_jobs, const char* rea
             S->tickets[rq->ticket] = rq;
             S->queue.push_back(rq);
             *ticket = rq->ticket;
+            S->counters.submitted++;
+            S->counters.max_queue = std::max<uint64_t>(S->counters.max_queue, S->queue.size());
         }
         S->cv_work.notify_all();
         return SA_OK;
@@ -1466,6 +1506,13 @@ int sa_poll(sa_server* S, uint64_t ticket, int timeout_ms, sa_result* out, uint3
     } catch (...) {
         return fail(SA_ENOMEM, "unexpected host exception");
     }
+}
+
+int sa_server_get_stats(sa_server* S, sa_server_stats* out) {
+    if (!S || !out) return fail(SA_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    *out = S->counters;
+    return SA_OK;
 }
 
 int sa_server_destroy(sa_server* S) {

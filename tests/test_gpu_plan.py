@@ -84,3 +84,26 @@ def test_malformed_plans_are_refused(sa):
         with pytest.raises(sa.SAError):
             ref.set_plan(bytes(bad_width))
         assert ref.plan() == bytes(default)
+
+
+def test_plan_json_cache_round_trip(sa, tmp_path):
+    """save_plan / load_plan: the JSON cache shows the tables and reinstalls the
+    exact plan bytes."""
+    wl = workloads.uneven(seed=3, n_jobs=2_000)
+    cfg = [0] + [next(c for c in range(N_CFG) if CFG_ROWS[c] >= n) for n in range(1, MAX_READ + 1)]
+    cfg[150] = 10                                   # a 32-lane configuration for length 150
+    width = [0] * N_CFG
+    width[5] = 32
+    plan = _plan_bytes(cfg, width)
+    with sa.Reference(wl.ref) as ref:
+        ref.set_plan(plan)
+        path = tmp_path / "plan.json"
+        ref.save_plan(str(path))
+        import json
+        doc = json.loads(path.read_text())
+        assert doc["cfg_of_read_length"][150] == 10 and doc["width_of_cfg"][5] == 32
+        ref.set_plan(None)
+        assert ref.plan() != plan
+        ref.load_plan(str(path))
+        assert ref.plan() == plan
+        _parity(sa, ref, wl)

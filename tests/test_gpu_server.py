@@ -44,6 +44,10 @@ def test_coalesced_requests_match_the_oracle(sa):
             # each request's CIGAR buffer is its own, compact, in job order
             assert res["cigar_off"][0] == 0
             assert (np.diff(res["cigar_off"].astype(np.int64)) == res["cigar_len"][:-1]).all()
+        st = srv.stats()
+        assert st["submitted"] == st["completed"] == len(reqs) and st["failed"] == 0
+        assert st["batches"] + st["coalesced"] == len(reqs) and st["coalesced"] > 0
+        assert st["jobs"] == wl.n_jobs and 1 <= st["max_queue"] <= len(reqs)
 
 
 def test_one_bad_request_does_not_fail_its_batch_mates(sa):
@@ -64,6 +68,8 @@ def test_one_bad_request_does_not_fail_its_batch_mates(sa):
             assert rc == sa.SA_OK
             ores, oops = oracle.align(r)
             assert not compare(res, cig, ores, oops)
+        st = srv.stats()
+        assert st["submitted"] == 5 and st["completed"] == 4 and st["failed"] == 1
 
 
 def test_poll_states_and_budget(sa):
