@@ -89,12 +89,15 @@ inline bool plan_valid(const Plan& p) {
 }
 
 // Size classes order jobs inside one configuration (largest windows first).
-constexpr int kNumSizeCls = 40;
+// Eighth-octave classes (8 * floor(log2 m) + the next three bits of m): the
+// jobs that share a warp of the packed score pass (which runs as many steps as
+// the longest of them) differ in window length by at most 9 % in one class.
+constexpr int kNumSizeCls = 8 * 17;       // m <= 65536 = 2^16
 __host__ __device__ inline int size_class(uint32_t m) {
     int lg = 0;
     for (uint32_t v = m; v > 1u; v >>= 1) lg++;
-    int half = (lg > 0) ? (int)((m >> (lg - 1)) & 1u) : 0;
-    int c = 2 * lg + half;
+    const int frac = lg >= 3 ? (int)((m >> (lg - 3)) & 7u) : (int)((m << (3 - lg)) & 7u);
+    const int c = 8 * lg + frac;
     return c < kNumSizeCls ? c : kNumSizeCls - 1;
 }
 constexpr int kNumKeys = kNumCfg * kNumSizeCls;

@@ -100,18 +100,47 @@ __global__ void k_plan(const sa_job* __restrict__ jobs, uint32_t n_jobs, uint64_
         if (sh[k]) atomicAdd(&hist[k], sh[k]);
 }
 
-__global__ void k_plan_scan(const uint32_t* __restrict__ hist, uint32_t* __restrict__ key_off,
-                            uint32_t* __restrict__ cursor) {
-    // one block: exclusive scan of kNumKeys counts (serial per warp is plenty here)
-    if (threadIdx.x == 0) {
-        uint32_t acc = 0;
-        for (int k = 0; k < kNumKeys; k++) {
-            key_off[k] = acc;
-            acc += hist[k];
-        }
-        key_off[kNumKeys] = acc;
+constexpr int kScanKeysThreads = 1024;
+__global__ void __launch_bounds__(kScanKeysThreads)
+k_plan_scan(const uint32_t* __restrict__ hist, uint32_t* __restrict__ key_off, uint32_t* __restrict__ cursor) {
+    // one block: exclusive scan of the kNumKeys counts, kPer consecutive keys a thread
+    constexpr int kPer = (kNumKeys + kScanKeysThreads - 1) / kScanKeysThreads;
+    __shared__ uint32_t warp_tot[32];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    uint32_t v[kPer], sum = 0;
+#pragma unroll
+    for (int q = 0; q < kPer; q++) {
+        const int k = t * kPer + q;
+        v[q] = k < kNumKeys ? hist[k] : 0u;
+        sum += v[q];
     }
-    for (int k = threadIdx.x; k < kNumKeys; k += blockDim.x) cursor[k] = 0;
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += x;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = warp_tot[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += x;
+        }
+        warp_tot[lane] = w;                    // inclusive over warps
+    }
+    __syncthreads();
+    uint32_t acc = incl - sum + (wid ? warp_tot[wid - 1] : 0u);
+#pragma unroll
+    for (int q = 0; q < kPer; q++) {
+        const int k = t * kPer + q;
+        if (k < kNumKeys) key_off[k] = acc;
+        acc += v[q];
+    }
+    if (t == kScanKeysThreads - 1) key_off[kNumKeys] = warp_tot[31];
+    for (int k = t; k < kNumKeys; k += kScanKeysThreads) cursor[k] = 0;
 }
 
 __global__ void k_plan_scatter(const uint16_t* __restrict__ key, uint32_t n_jobs,
@@ -137,7 +166,7 @@ void launch_plan(const sa_job* jobs, uint32_t n_jobs, uint64_t reads_len, int64_
 
 void launch_plan_order(const uint16_t* key, uint32_t n_jobs, const uint32_t* hist,
                        uint32_t* key_off, uint32_t* cursor, uint32_t* order, cudaStream_t st) {
-    k_plan_scan<<<1, 256, 0, st>>>(hist, key_off, cursor);
+    k_plan_scan<<<1, kScanKeysThreads, 0, st>>>(hist, key_off, cursor);
     if (n_jobs)
         k_plan_scatter<<<(n_jobs + 255) / 256, 256, 0, st>>>(key, n_jobs, key_off, cursor, order);
 }
