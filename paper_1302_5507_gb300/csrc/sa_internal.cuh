@@ -89,15 +89,16 @@ inline bool plan_valid(const Plan& p) {
 }
 
 // Size classes order jobs inside one configuration (largest windows first).
-// Eighth-octave classes (8 * floor(log2 m) + the next three bits of m): the
-// jobs that share a warp of the packed score pass (which runs as many steps as
-// the longest of them) differ in window length by at most 9 % in one class.
-constexpr int kNumSizeCls = 8 * 17;       // m <= 65536 = 2^16
+// Sixteenth-octave classes (16 * floor(log2 m) + the next four bits of m):
+// the jobs that share a warp of the packed score pass (which runs as many
+// steps as the longest of them) differ in window length by at most 4.5 % in
+// one class.
+constexpr int kNumSizeCls = 16 * 17;      // m <= 65536 = 2^16
 __host__ __device__ inline int size_class(uint32_t m) {
     int lg = 0;
     for (uint32_t v = m; v > 1u; v >>= 1) lg++;
-    const int frac = lg >= 3 ? (int)((m >> (lg - 3)) & 7u) : (int)((m << (3 - lg)) & 7u);
-    const int c = 8 * lg + frac;
+    const int frac = lg >= 4 ? (int)((m >> (lg - 4)) & 15u) : (int)((m << (4 - lg)) & 15u);
+    const int c = 16 * lg + frac;
     return c < kNumSizeCls ? c : kNumSizeCls - 1;
 }
 constexpr int kNumKeys = kNumCfg * kNumSizeCls;
