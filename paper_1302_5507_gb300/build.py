@@ -23,7 +23,7 @@ OUT = os.path.join(HERE, "libsa.so")
 OUT_DEBUG = os.path.join(HERE, "libsa_debug.so")   # SA_DEBUG: bounds-checked stores (tests)
 PROBE = os.path.join(HERE, "libsa_probe.so")   # instruction-throughput probe used by bench.py
 BUILD = os.path.join(HERE, "_build")
-NUM_CFG = 14
+NUM_CFG = 33                 # wavefront configurations (kNumCfg in csrc/sa_internal.cuh)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", f"-I{INCLUDE}", f"-I{CSRC}",
          "--expt-relaxed-constexpr"]

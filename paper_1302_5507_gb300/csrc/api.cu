@@ -1250,7 +1250,7 @@ int sa_align_batch(sa_reference* R, const sa_params* P, const sa_job* jobs, uint
 namespace {
 
 constexpr uint32_t kPlanMagic = 0x4C504153u;   // "SAPL"
-constexpr uint32_t kPlanVersion = 1u;
+constexpr uint32_t kPlanVersion = 2u;   // 2: 33 configurations
 constexpr uint64_t kPlanBytes = 8 + sizeof(Plan::cfg) + sizeof(Plan::width);
 
 int upload_plan(sa_reference* R) {

@@ -44,22 +44,24 @@ enum {
 // Lane-group configurations of the wavefront kernels: a group of L lanes
 // (L divides 32) works on one job (two jobs in the packed 16-bit kernel); each
 // lane owns K consecutive read rows, so a group covers L*K >= n rows.
+// Groups of 8 lanes take every K from 4 to 32 (reads up to 256 bases in steps of
+// 8 rows, so a read is padded by at most 7 rows); groups of 32 lanes take
+// K = 10, 16, 24, 32 (reads up to 1024 bases).
 struct Cfg { int L, K; };
-constexpr int kNumCfg = 14;
-constexpr Cfg kCfgs[kNumCfg] = {
-    {8, 4}, {8, 7}, {8, 10}, {8, 13}, {8, 16}, {8, 19}, {8, 22}, {8, 25}, {8, 28}, {8, 32},
-    {32, 10}, {32, 16}, {32, 24}, {32, 32}};
-
-// run-time lookups (device code cannot index the host constexpr table)
-__host__ __device__ inline int cfg_L(int c) { return c < 10 ? 8 : 32; }
-__host__ __device__ inline int cfg_K(int c) {
-    switch (c) {
-    case 0: return 4;   case 1: return 7;   case 2: return 10;  case 3: return 13;
-    case 4: return 16;  case 5: return 19;  case 6: return 22;  case 7: return 25;
-    case 8: return 28;  case 9: return 32;  case 10: return 10; case 11: return 16;
-    case 12: return 24; default: return 32;
-    }
+constexpr int kNumCfg8 = 29;               // L = 8, K = 4 .. 32
+constexpr int kNumCfg = kNumCfg8 + 4;
+__host__ __device__ constexpr int cfg_L(int c) { return c < kNumCfg8 ? 8 : 32; }
+__host__ __device__ constexpr int cfg_K(int c) {
+    return c < kNumCfg8 ? c + 4 : (c == kNumCfg8 ? 10 : c == kNumCfg8 + 1 ? 16 : c == kNumCfg8 + 2 ? 24 : 32);
 }
+struct CfgTable {
+    Cfg c[kNumCfg];
+    constexpr CfgTable() : c() {
+        for (int i = 0; i < kNumCfg; i++) c[i] = Cfg{cfg_L(i), cfg_K(i)};
+    }
+    constexpr const Cfg& operator[](int i) const { return c[i]; }
+};
+constexpr CfgTable kCfgs{};
 
 __host__ __device__ inline int cfg_for_rows(int n) {
     for (int c = 0; c < kNumCfg; c++)

@@ -9,9 +9,11 @@ from oracle.compare import compare
 
 pytestmark = pytest.mark.gpu
 
-N_CFG = 14
+N_CFG8 = 29                                       # lane groups of 8, K = 4 .. 32
+N_CFG = N_CFG8 + 4                                # plus lane groups of 32, K = 10, 16, 24, 32
 MAX_READ = 1024
-CFG_ROWS = [8 * k for k in (4, 7, 10, 13, 16, 19, 22, 25, 28, 32)] + [32 * k for k in (10, 16, 24, 32)]
+CFG_ROWS = [8 * k for k in range(4, 33)] + [32 * k for k in (10, 16, 24, 32)]
+FIRST32 = N_CFG8
 
 
 @pytest.fixture(scope="module")
@@ -32,7 +34,7 @@ def _parity(sa, ref, wl, **kw):
 
 
 def _plan_bytes(cfg, width):
-    head = np.array([0x4C504153, 1], np.uint32).tobytes()
+    head = np.array([0x4C504153, 2], np.uint32).tobytes()
     return head + np.asarray(cfg, np.uint8).tobytes() + np.asarray(width, np.int8).tobytes()
 
 
@@ -57,7 +59,8 @@ def test_plan_round_trip_and_explicit_plans(sa):
         ref.set_plan(default)
         assert ref.plan() == default
         # every length on the 32-lane configurations, 32-bit everywhere
-        cfg = [10] + [next(c for c in range(10, N_CFG) if CFG_ROWS[c] >= n) for n in range(1, MAX_READ + 1)]
+        cfg = [FIRST32] + [next(c for c in range(FIRST32, N_CFG) if CFG_ROWS[c] >= n)
+                           for n in range(1, MAX_READ + 1)]
         ref.set_plan(_plan_bytes(cfg, [32] * N_CFG))
         st = _parity(sa, ref, wl)
         assert st["jobs16"] == 0
@@ -91,9 +94,9 @@ def test_plan_json_cache_round_trip(sa, tmp_path):
     exact plan bytes."""
     wl = workloads.uneven(seed=3, n_jobs=2_000)
     cfg = [0] + [next(c for c in range(N_CFG) if CFG_ROWS[c] >= n) for n in range(1, MAX_READ + 1)]
-    cfg[150] = 10                                   # a 32-lane configuration for length 150
+    cfg[150] = FIRST32                              # a 32-lane configuration for length 150
     width = [0] * N_CFG
-    width[5] = 32
+    width[15] = 32
     plan = _plan_bytes(cfg, width)
     with sa.Reference(wl.ref) as ref:
         ref.set_plan(plan)
@@ -101,7 +104,7 @@ def test_plan_json_cache_round_trip(sa, tmp_path):
         ref.save_plan(str(path))
         import json
         doc = json.loads(path.read_text())
-        assert doc["cfg_of_read_length"][150] == 10 and doc["width_of_cfg"][5] == 32
+        assert doc["cfg_of_read_length"][150] == FIRST32 and doc["width_of_cfg"][15] == 32
         ref.set_plan(None)
         assert ref.plan() != plan
         ref.load_plan(str(path))
