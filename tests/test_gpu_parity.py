@@ -230,6 +230,93 @@ def test_full_size_mate_rescue_sampled(sa):
     assert (np.diff(res["cigar_off"].astype(np.int64)) == res["cigar_len"][:-1]).all()
 
 
+def _sampled_compare(wl, res, cig, idx):
+    sub = wl.subset(idx)
+    ores, oops = oracle.align(sub)
+    sres = res[idx].copy()
+    parts, off = [], 0
+    for k, j in enumerate(idx):
+        L = int(res["cigar_len"][j])
+        parts.append(cig[int(res["cigar_off"][j]):int(res["cigar_off"][j]) + L])
+        sres["cigar_off"][k] = off
+        off += L
+    scig = np.concatenate(parts) if parts else np.zeros(0, np.uint32)
+    return compare(sres, scig, ores, oops)
+
+
+def test_full_size_uneven_sampled(sa):
+    """The uneven-length workload at its full size (4M jobs, every length bucket,
+    16-bit pairs) in one device call, as the benchmark runs it; a seeded sample of
+    jobs is recomputed by the oracle one by one."""
+    import torch
+    wl = workloads.uneven(seed=1)
+    jobs = sa.jobs_array(wl.read_off, wl.read_len, wl.flags, wl.ref_pos, wl.win_len)
+    dev = torch.device("cuda", 0)
+    with sa.Reference(wl.ref) as ref:
+        d_out = torch.empty(len(jobs) * 56, dtype=torch.uint8, device=dev)
+        d_cig = torch.empty(sa.cigar_max_ops(wl.read_len), dtype=torch.int32, device=dev)
+        used = ref.align_dev(torch.from_numpy(jobs.view(np.uint8)).to(dev), torch.from_numpy(wl.reads).to(dev),
+                             d_out, d_cig, sa.make_params())
+        torch.cuda.synchronize()
+        assert ref.stats()["jobs16"] == wl.n_jobs
+        res = d_out.cpu().numpy().view(sa.RESULT_DTYPE)
+        cig = d_cig[:used].cpu().numpy().view(np.uint32)
+    rng = np.random.default_rng(321)
+    idx = np.sort(rng.choice(wl.n_jobs, 3000, replace=False))
+    bad = _sampled_compare(wl, res, cig, idx)
+    assert not bad, "\n".join(bad)
+
+
+def test_full_size_pairs_sampled(sa):
+    """The paired multi-candidate workload at the benchmark's size (100k pairs,
+    4.25M candidates): effort limit, alignment and paired selection on the device;
+    a seeded sample of pairs is recomputed by the oracle from their own candidates
+    (every step is per read or per pair)."""
+    import torch
+    from oracle import select as S
+    w = workloads.pairs(seed=1, n_pairs=100_000)
+    jobs = sa.jobs_array(w.read_off, w.read_len, w.flags, w.ref_pos, w.win_len)
+    dev = torch.device("cuda", 0)
+    first = w.read_first.astype(np.uint32)
+    with sa.Reference(w.ref) as ref:
+        dk = torch.empty(len(jobs) * 32, dtype=torch.uint8, device=dev)
+        dfrom = torch.empty(len(jobs), dtype=torch.int32, device=dev)
+        dkf = torch.empty(len(first), dtype=torch.int32, device=dev)
+        n = ref.effort_limit_dev(torch.from_numpy(jobs.view(np.uint8)).to(dev),
+                                 torch.from_numpy(w.support.view(np.int32)).to(dev),
+                                 torch.from_numpy(first.view(np.int32)).to(dev), 30, dk, dfrom, dkf)
+        dres = torch.empty(n * 56, dtype=torch.uint8, device=dev)
+        dcig = torch.empty(sa.cigar_max_ops(w.read_len), dtype=torch.int32, device=dev)
+        ref.align_dev(dk[: n * 32], torch.from_numpy(w.reads).to(dev), dres, dcig, sa.make_params())
+        dout = torch.empty(w.n_reads * 32, dtype=torch.uint8, device=dev)
+        ref.select_dev(dk[: n * 32], dres, dkf, dout,
+                       sa.make_select_params(paired=True, frag_min=300, frag_max=700))
+        torch.cuda.synchronize()
+        kept_from = dfrom.cpu().numpy()[:n].astype(np.int64)
+        kept_first = dkf.cpu().numpy().astype(np.int64)
+        got = dout.cpu().numpy().view(sa.READ_RESULT_DTYPE)
+    rng = np.random.default_rng(99)
+    pairs = np.sort(rng.choice(w.n_reads // 2, 400, replace=False))
+    reads = np.stack([2 * pairs, 2 * pairs + 1], 1).ravel()
+    # the oracle on the sampled reads' own candidates
+    cand = np.concatenate([np.arange(int(w.read_first[r]), int(w.read_first[r + 1])) for r in reads])
+    sfirst = np.zeros(len(reads) + 1, np.int64)
+    sfirst[1:] = np.cumsum([int(w.read_first[r + 1] - w.read_first[r]) for r in reads])
+    kept, kf = S.effort_limit(w.support[cand].astype(np.int64), sfirst, 30)
+    sub = w.subset(cand[kept])
+    ores, _ = oracle.align(sub)
+    exp = S.select(sub.flags, sub.read_len, ores, kf, paired=True, frag_min=300, frag_max=700)
+    # the device's choices, mapped back to batch candidates, must be the same
+    for k, r in enumerate(reads):
+        g, e = got[r], exp[k]
+        assert (int(kept_first[r + 1]) - int(kept_first[r])) == int(kf[k + 1] - kf[k])
+        gj = -1 if g["job"] == sa.SA_NO_JOB else int(kept_from[g["job"]])
+        ej = -1 if e["job"] == S.NO_JOB else int(cand[kept[e["job"]]])
+        assert gj == ej, (r, gj, ej)
+        for f in ("score", "second", "mapq", "flags", "n_cand", "frag_len"):
+            assert int(g[f]) == int(e[f]), (r, f, int(g[f]), int(e[f]))
+
+
 def test_every_direction_pass_class_is_exercised(sa):
     """The low-similarity sweep puts traced jobs in every traceback class: the
     all-match diagonal (no direction pass), the banded passes and the
