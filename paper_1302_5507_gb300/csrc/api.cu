@@ -151,7 +151,26 @@ struct Ctx {
     sa_stats* last;
     const Plan* plan;
     const uint8_t* d_plan_cfg;    // device copy of plan->cfg
+    // the default plan on fewer lane-group configurations, for batches below
+    // kFinePlanJobs (or null: always d_plan_cfg).  Each non-empty configuration
+    // is one persistent launch of each pass, run in turn; below about a million
+    // jobs the finer row steps split the batch into launches of less than a
+    // wave each, whose tails cost more than the padding rows they save.
+    const uint8_t* d_plan_coarse = nullptr;
 };
+constexpr uint32_t kFinePlanJobs = 1u << 20;
+
+// Every read length on the smallest of the configurations with K = 4, 7, 10, ...,
+// 28 (8 lanes) or 32 (8 lanes, n <= 256) or the 32-lane ones: the earlier set
+// of 14 configurations.
+void coarse_plan(Plan* p) {
+    default_plan(p);
+    for (int n = 1; n <= (int)SA_MAX_READ; n++) {
+        int c = p->cfg[n];
+        while (cfg_L(c) == 8 && cfg_K(c) != 32 && (cfg_K(c) - 4) % 3 != 0) c++;
+        p->cfg[n] = (uint8_t)c;
+    }
+}
 
 }  // namespace
 
@@ -166,7 +185,11 @@ struct sa_reference {
     sa_stats last{};
     Plan plan;
     uint8_t* d_plan_cfg = nullptr;
-    Ctx ctx() { return Ctx{d_words, len, num_sms, &ws, &last, &plan, d_plan_cfg}; }
+    uint8_t* d_plan_coarse = nullptr;  // the coarse default plan (small batches)
+    bool plan_default = true;          // no plan installed: small batches use d_plan_coarse
+    Ctx ctx() {
+        return Ctx{d_words, len, num_sms, &ws, &last, &plan, d_plan_cfg, plan_default ? d_plan_coarse : nullptr};
+    }
 };
 
 // ---------------------------------------------------------------------------
@@ -331,7 +354,8 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
     TRY(ws.counters.ensure(256 * sizeof(uint32_t), "counters"));
     CU(cudaMemsetAsync(ws.counters.p, 0, 256 * sizeof(uint32_t), st));
     int counter_next = 0;
-    launch_plan(d_jobs, n_jobs, reads_len, (int64_t)X.len, X.d_plan_cfg, ws.key.as<uint16_t>(), dp->hist,
+    const uint8_t* plan_tab = (X.d_plan_coarse && n_jobs < kFinePlanJobs) ? X.d_plan_coarse : X.d_plan_cfg;
+    launch_plan(d_jobs, n_jobs, reads_len, (int64_t)X.len, plan_tab, ws.key.as<uint16_t>(), dp->hist,
                 &dp->st, st);
     launches++;
     CU(cudaGetLastError());
@@ -991,7 +1015,7 @@ int run_batch(sa_server* S, sa_server::Slot* slot, std::vector<std::shared_ptr<R
     Workspace& ws = slot->ws;
     const cudaStream_t st = slot->stream;
     Ctx X{S->ref->d_words, S->ref->len, S->ref->num_sms, &ws, &slot->last, &S->ref->plan,
-          S->ref->d_plan_cfg};
+          S->ref->d_plan_cfg, S->ref->plan_default ? S->ref->d_plan_coarse : nullptr};
     uint64_t used = 0;
     if (nj) {
         TRY(ws.jobs.ensure(nj * sizeof(sa_job), "jobs"));
@@ -1139,6 +1163,12 @@ int sa_create_reference(const char* acgt, uint64_t len, int device, sa_reference
         default_plan(&R->plan);
         CU(cudaMalloc(&R->d_plan_cfg, sizeof(R->plan.cfg)));
         CU(cudaMemcpy(R->d_plan_cfg, R->plan.cfg, sizeof(R->plan.cfg), cudaMemcpyHostToDevice));
+        {
+            Plan coarse;
+            coarse_plan(&coarse);
+            CU(cudaMalloc(&R->d_plan_coarse, sizeof(coarse.cfg)));
+            CU(cudaMemcpy(R->d_plan_coarse, coarse.cfg, sizeof(coarse.cfg), cudaMemcpyHostToDevice));
+        }
         CU(cudaMemsetAsync(R->d_words, 0, words * 4, R->own));
         const uint64_t chunk = 256ull << 20;  // multiple of 16
         uint8_t* stage = nullptr;
@@ -1187,6 +1217,7 @@ int sa_destroy_reference(sa_reference* R) {
             R->ws.release();
             cudaFree(R->d_words);
             cudaFree(R->d_plan_cfg);
+            cudaFree(R->d_plan_coarse);
             cudaStreamDestroy(R->own);
         }
         delete R;
@@ -1351,6 +1382,7 @@ int sa_tune(sa_reference* R, const sa_params* P, const sa_job* jobs, uint32_t n_
             R->plan.width[best_c] = (int8_t)(local16 ? best_w : 0);
             tuned++;
         }
+        R->plan_default = false;           // the tuned plan serves every batch size
         TRY(upload_plan(R));
         if (classes_tuned) *classes_tuned = tuned;
         return SA_OK;
@@ -1379,6 +1411,7 @@ int sa_plan_set(sa_reference* R, const void* plan, uint64_t size) {
             std::lock_guard<std::mutex> lk(R->mu);
             CU(cudaSetDevice(R->device));
             default_plan(&R->plan);
+            R->plan_default = true;
             return upload_plan(R);
         }
         if (size != kPlanBytes) return fail(SA_EINVAL, "a plan has %llu bytes, got %llu",
@@ -1397,6 +1430,7 @@ int sa_plan_set(sa_reference* R, const void* plan, uint64_t size) {
         std::lock_guard<std::mutex> lk(R->mu);
         CU(cudaSetDevice(R->device));
         R->plan = p;
+        R->plan_default = false;
         return upload_plan(R);
     } catch (...) {
         return fail(SA_ENOMEM, "unexpected host exception");
