@@ -990,6 +990,33 @@ constexpr uint64_t kCoalesceJobs = 1ull << 20;
 // Runs the requests of `batch` as one device batch: jobs concatenated (read
 // offsets rebased) in pinned staging, results and CIGAR ops split back per
 // request.  The CIGAR staging is sized by the ops actually produced.
+// Runs fn(k) for k in [0, n) on up to `threads` host threads (the calling one
+// included); the staging copies of a large coalesced batch are memory-bandwidth
+// bound and one thread leaves most of the host's bandwidth idle.
+template <typename F>
+void parallel_for(size_t n, unsigned threads, F&& fn) {
+    threads = (unsigned)std::min<size_t>(threads, n);
+    if (threads <= 1) {
+        for (size_t k = 0; k < n; k++) fn(k);
+        return;
+    }
+    std::atomic<size_t> next{0};
+    auto worker = [&] {
+        for (size_t k = next++; k < n; k = next++) fn(k);
+    };
+    std::vector<std::thread> pool;
+    pool.reserve(threads - 1);
+    for (unsigned t = 1; t < threads; t++) pool.emplace_back(worker);
+    worker();
+    for (auto& th : pool) th.join();
+}
+
+unsigned staging_threads(uint64_t bytes) {
+    if (bytes < (16ull << 20)) return 1;                       // small batches: one thread
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    return std::min(8u, std::max(1u, hw / 2));
+}
+
 int run_batch(sa_server* S, sa_server::Slot* slot, std::vector<std::shared_ptr<Request>>& batch,
               PinnedBuf& hjobs, PinnedBuf& hreads, PinnedBuf& hout, PinnedBuf& hcig) {
     uint64_t nj = 0, nr = 0, cap = 0;
@@ -1002,16 +1029,27 @@ int run_batch(sa_server* S, sa_server::Slot* slot, std::vector<std::shared_ptr<R
         return fail(SA_ENOMEM, "pinned staging allocation failed");
     sa_job* J = hjobs.as<sa_job>();
     char* Rd = hreads.as<char>();
-    uint64_t jo = 0, ro = 0;
-    for (auto& rq : batch) {
-        for (const sa_job& j : rq->jobs) {
-            J[jo] = j;
-            J[jo].read_off += ro;
-            jo++;
+    // each request's jobs and reads go to their own ranges of the staging buffers
+    std::vector<uint64_t> job0(batch.size()), read0(batch.size());
+    {
+        uint64_t jo = 0, ro = 0;
+        for (size_t k = 0; k < batch.size(); k++) {
+            job0[k] = jo;
+            read0[k] = ro;
+            jo += batch[k]->jobs.size();
+            ro += batch[k]->reads.size();
         }
-        if (!rq->reads.empty()) std::memcpy(Rd + ro, rq->reads.data(), rq->reads.size());
-        ro += rq->reads.size();
     }
+    const unsigned nthreads = staging_threads(nj * sizeof(sa_job) + nr);
+    parallel_for(batch.size(), nthreads, [&](size_t k) {
+        const Request& rq = *batch[k];
+        sa_job* dst = J + job0[k];
+        for (size_t q = 0; q < rq.jobs.size(); q++) {
+            dst[q] = rq.jobs[q];
+            dst[q].read_off += read0[k];
+        }
+        if (!rq.reads.empty()) std::memcpy(Rd + read0[k], rq.reads.data(), rq.reads.size());
+    });
     Workspace& ws = slot->ws;
     const cudaStream_t st = slot->stream;
     Ctx X{S->ref->d_words, S->ref->len, S->ref->num_sms, &ws, &slot->last, &S->ref->plan,
@@ -1032,19 +1070,18 @@ int run_batch(sa_server* S, sa_server::Slot* slot, std::vector<std::shared_ptr<R
     }
     const sa_result* O = hout.as<sa_result>();
     const uint32_t* C = hcig.as<uint32_t>();
-    uint64_t b = 0;
-    for (auto& rq : batch) {
-        const uint64_t n = rq->jobs.size();
-        rq->out.assign(O + b, O + b + n);
+    parallel_for(batch.size(), staging_threads(nj * sizeof(sa_result) + used * 4), [&](size_t k) {
+        Request& rq = *batch[k];
+        const uint64_t b = job0[k], n = rq.jobs.size();
+        rq.out.assign(O + b, O + b + n);
         uint64_t c0 = 0, c1 = 0;
         if (n) {
             c0 = O[b].cigar_off;
             c1 = (uint64_t)O[b + n - 1].cigar_off + O[b + n - 1].cigar_len;
         }
-        rq->cigar.assign(C + c0, C + c1);
-        for (sa_result& r : rq->out) r.cigar_off -= (uint32_t)c0;
-        b += n;
-    }
+        rq.cigar.assign(C + c0, C + c1);
+        for (sa_result& r : rq.out) r.cigar_off -= (uint32_t)c0;
+    });
     return SA_OK;
 }
 
