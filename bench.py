@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving latency run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--slots", type=int, default=2, help="in-flight slots of the serving runs")
     ap.add_argument("--probe-ops", action="store_true",
                     help="print the measured issue rate (lane-ops per SM per clock) of every "
                          "operation of the throughput probe and exit")
@@ -433,7 +434,8 @@ def run_ours(args, rank, world, dist):
         import workloads
         sizes, ppm = workloads.serving_arrivals(seed=3, n_requests=40)
         reqs = [workloads.serving_request(wl.ref, 3, k, int(sizes[k])) for k in range(40)]
-        line["serving"] = serving_run(sa, ref, reqs, ppm, (0.8,), genome="the mate-rescue genome (100 Mbp)")
+        line["serving"] = serving_run(sa, ref, reqs, ppm, (0.8,), genome="the mate-rescue genome (100 Mbp)",
+                                      slots=args.slots)
     ref.close()
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(wl)
@@ -453,7 +455,7 @@ def concat(reqs):
         np.concatenate([r.truth for r in reqs]), dict(reqs[0].meta))
 
 
-def serving_run(sa, ref, reqs, ppm, loads, genome: str, plain: bool = False):
+def serving_run(sa, ref, reqs, ppm, loads, genome: str, plain: bool = False, slots: int = 2):
     """Open-loop Poisson arrivals of `reqs` at each offered load (a fraction of the
     offline batched throughput of the same jobs); p50/p99 submit -> result."""
     allj = concat(reqs)
@@ -465,7 +467,7 @@ def serving_run(sa, ref, reqs, ppm, loads, genome: str, plain: bool = False):
     out = {"requests": len(reqs), "jobs": int(allj.n_jobs), "cells": int(allj.cells), "genome": genome,
            "offline_batched_gcups": offline / 1e9,
            "offline_form": "all jobs of the requests in one sa_align_batch call (host buffers)",
-           "server": "2 slots; queued requests coalesce into one device batch (<= 1M jobs)",
+           "server": f"{slots} slots; queued requests coalesce into one device batch (<= 1M jobs)",
            "poll": "one poller thread in submit order", "loads": []}
     if plain:
         pp = sa.make_params(form=sa.SA_FORM_PLAIN)
@@ -482,7 +484,7 @@ def serving_run(sa, ref, reqs, ppm, loads, genome: str, plain: bool = False):
         gaps = -np.log(np.maximum(ppm.astype(np.float64), 1.0) / 1e6) / rate
         lat, done_cells = [], 0
         pending = _queue.Queue()
-        with sa.Server(ref, sa.make_params(), max_inflight=2) as srv:
+        with sa.Server(ref, sa.make_params(), max_inflight=slots) as srv:
             # warm-up: each slot runs one batch as large as a coalesced batch can get
             # (device workspace and pinned staging reach their largest size before
             # the timed arrivals)
@@ -721,7 +723,7 @@ def run_config(args):
         sizes, ppm = workloads.serving_arrivals(seed=3, n_requests=n_req)
         reqs = [workloads.serving_request(ref_acgt, 3, k, int(sizes[k])) for k in range(n_req)]
         with sa.Reference(ref_acgt) as ref:
-            line = serving_run(sa, ref, reqs, ppm, (0.5, 0.8, 0.95),
+            line = serving_run(sa, ref, reqs, ppm, (0.5, 0.8, 0.95), slots=args.slots,
                                genome="3.1 Gbp i.i.d. reference (775 MB packed, device-resident)", plain=True)
         line["config"] = "c5 serving: requests of U[1,50000] jobs, n U[50,250], m U[2n,6n]"
     line["data"] = "synthetic"
