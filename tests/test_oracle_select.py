@@ -228,3 +228,61 @@ def test_gapped_begin_without_traceback_uses_the_read_length(seed):
     out = S.select(np.array([0, 1], np.uint32), np.array([100, 100], np.uint32), res,
                    np.array([0, 1, 2]), paired=True, frag_min=600, frag_max=600)
     assert out[0]["frag_len"] == 600 and out[0]["flags"] & S.PROPER
+
+
+# --- invariants on random result tables -----------------------------------------
+
+def _random_results(rng, n_reads, paired):
+    """Per-read candidate lists with random scores, ends, seconds and flags."""
+    sizes = rng.integers(0, 6, n_reads)
+    first = np.zeros(n_reads + 1, np.int64)
+    first[1:] = np.cumsum(sizes)
+    n = int(first[-1])
+    res = np.zeros(n, oracle.RESULT_DTYPE)
+    res["score"] = rng.integers(1, 60, n)
+    res["ref_end"] = rng.integers(100, 3000, n)
+    res["ref_begin"] = np.where(rng.random(n) < 0.5, res["ref_end"] - rng.integers(20, 60, n), -1)
+    has2 = rng.random(n) < 0.6
+    res["second"] = np.where(has2, np.minimum(res["score"], rng.integers(0, 60, n)), S.NO_SCORE)
+    res["second_ref_end"] = np.where(has2, rng.integers(100, 3000, n), -1)
+    res["flags"] = np.where(rng.random(n) < 0.15, S.EMPTY, 0)
+    flags = (rng.random(n) < 0.5).astype(np.uint32)
+    read_len = np.full(n, 50, np.uint32)
+    return flags, read_len, res, first
+
+
+@pytest.mark.parametrize("paired", [False, True])
+def test_selection_invariants(paired):
+    rng = np.random.default_rng(17 + paired)
+    for _ in range(40):
+        n_reads = 2 * int(rng.integers(1, 8))
+        flags, read_len, res, first = _random_results(rng, n_reads, paired)
+        out = S.select(flags, read_len, res, first, paired=paired, frag_min=50, frag_max=400)
+        for r in range(n_reads):
+            o = out[r]
+            lo, hi = int(first[r]), int(first[r + 1])
+            assert o["n_cand"] == hi - lo
+            aligned = [j for j in range(lo, hi) if not res["flags"][j] & (S.EMPTY | S.BELOW_MIN)]
+            if not aligned:
+                assert o["job"] == S.NO_JOB and not o["flags"] & S.ALIGNED and o["mapq"] == 0
+                continue
+            assert lo <= o["job"] < hi and o["job"] in aligned and o["flags"] & S.ALIGNED
+            assert o["score"] == res["score"][o["job"]]
+            assert 0 <= o["mapq"] <= S.MAPQ_MAX
+            assert bool(o["flags"] & S.REVERSE) == bool(flags[o["job"]] & 1)
+            if o["flags"] & S.PROPER:
+                assert paired and o["flags"] & S.PAIRED and o["flags"] & S.MATE_ALIGNED
+                assert 50 <= o["frag_len"] <= 400
+            else:
+                assert o["frag_len"] == 0
+                # on its own: the best aligned candidate and a second that is not better
+                best = max(int(res["score"][j]) for j in aligned)
+                assert o["score"] == best
+                assert o["second"] == S.NO_SCORE or o["second"] <= best
+            assert bool(o["flags"] & S.PAIRED) == paired
+        if paired:
+            for p in range(n_reads // 2):
+                a, b = out[2 * p], out[2 * p + 1]
+                assert bool(a["flags"] & S.PROPER) == bool(b["flags"] & S.PROPER)
+                if a["flags"] & S.PROPER:
+                    assert a["frag_len"] == b["frag_len"]
