@@ -43,7 +43,7 @@ def build(force: bool = False, src: str | None = None, out: str | None = None,
     src = src or os.path.join(_HERE, "oracle.c")
     out = out or _SO
     if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
-        tmp = out + ".tmp"
+        tmp = out + f".{os.getpid()}.tmp"       # per process: concurrent builds never share a file
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
                                *[f"-D{d}" for d in defines], src, "-o", tmp])
         os.replace(tmp, out)

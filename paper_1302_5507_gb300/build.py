@@ -8,6 +8,7 @@ file and are reused while their sources are unchanged.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import glob
 import os
 import platform
@@ -53,11 +54,23 @@ def _deps_mtime() -> float:
 def build(force: bool = False, jobs: int | None = None, verbose: bool = False, debug: bool = False) -> str:
     """Build libsa.so, or with debug=True libsa_debug.so (-DSA_DEBUG: every indexed
     global store of the kernels checks its index against its buffer and records the
-    store site instead of writing out of range)."""
+    store site instead of writing out of range).  Processes that build at the same
+    time (the ranks of a multi-GPU run) take turns on a lock file; the later ones
+    find the library up to date."""
+    bdir = BUILD + ("_debug" if debug else "")
+    os.makedirs(bdir, exist_ok=True)
+    with open(os.path.join(bdir, "lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build_locked(force, jobs, verbose, debug)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(force: bool, jobs: int | None, verbose: bool, debug: bool) -> str:
     out = OUT_DEBUG if debug else OUT
     bdir = BUILD + ("_debug" if debug else "")
     extra_flags = ["-DSA_DEBUG"] if debug else []
-    os.makedirs(bdir, exist_ok=True)
     dep = _deps_mtime()
     # objects and library built on another machine type are never reused
     stamp = os.path.join(bdir, "machine")

@@ -43,7 +43,7 @@ FLAG_RC = 1  # job flag: align the reverse complement of the read
 def build(force: bool = False) -> str:
     src = os.path.join(_HERE, "synth.c")
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
-        tmp = _SO + ".tmp"
+        tmp = _SO + f".{os.getpid()}.tmp"       # per process: concurrent builds never share a file
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
                                src, "-o", tmp])
         os.replace(tmp, _SO)
