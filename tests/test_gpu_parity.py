@@ -368,3 +368,33 @@ def test_results_do_not_depend_on_pairing_or_run(sa):
             if first is None:
                 first = (res.copy(), cig.copy())
             assert (res == first[0]).all() and np.array_equal(cig, first[1])
+
+
+def test_page_locked_host_buffers(sa):
+    """sa_align_batch with page-locked host buffers, mixed with pageable ones,
+    matches the oracle; a page-locked CIGAR buffer that is too small is refused."""
+    import torch
+    wl = workloads.small(77, 2000, n_range=(1, 200), m_range=(1, 600), alphabet=4)
+    jobs = sa.jobs_array(wl.read_off, wl.read_len, wl.flags, wl.ref_pos, wl.win_len)
+    ores, oops = oracle.align(wl)
+
+    def pinned(a):
+        t = torch.empty(a.nbytes, dtype=torch.uint8, pin_memory=True)
+        v = t.numpy().view(a.dtype)
+        v[:] = a
+        return t, v
+
+    cap = sa.cigar_max_ops(wl.read_len)
+    with sa.Reference(wl.ref) as ref:
+        tj, pj = pinned(jobs)
+        tr, pr = pinned(wl.reads)
+        for out_pinned, cig_pinned in ((True, True), (True, False), (False, True), (False, False)):
+            to, out = pinned(np.zeros(len(jobs), sa.RESULT_DTYPE)) if out_pinned else (None, np.zeros(len(jobs), sa.RESULT_DTYPE))
+            tc, cig = pinned(np.zeros(cap, np.uint32)) if cig_pinned else (None, np.zeros(cap, np.uint32))
+            res, ops = ref.align(pj, pr, sa.make_params(), out=out, cigar=cig)
+            bad = compare(res, ops, ores, oops)
+            assert not bad, "\n".join([f"out pinned {out_pinned} cigar pinned {cig_pinned}"] + bad[:10])
+        tc, small_cig = pinned(np.zeros(8, np.uint32))
+        with pytest.raises(sa.SAError) as e:
+            ref.align(pj, pr, sa.make_params(), out=np.zeros(len(jobs), sa.RESULT_DTYPE), cigar=small_cig)
+        assert e.value.code == sa.SA_EOVERFLOW
