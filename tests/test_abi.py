@@ -54,3 +54,18 @@ def test_invalid_arguments_fail_without_gpu(libsa):
     p.mode = 7
     rc, _ = sa.sa_align_batch(None, p, None, 0, None, 0, None, None, 0)
     assert rc == sa.SA_EINVAL
+
+
+def test_read_level_layouts_and_null_handles(libsa):
+    import paper_1302_5507_gb300 as sa
+    assert sa.READ_RESULT_DTYPE.itemsize == 32
+    assert ctypes.sizeof(sa.sa_select_params) == 4 * 4 + 4 + 4 + 8 + 8
+    assert ctypes.sizeof(sa.sa_server_stats) == 8 * 8
+    L = sa.lib()
+    sp = sa.make_select_params(paired=True, frag_min=300, frag_max=700)
+    assert L.sa_select(None, ctypes.byref(sp), None, None, None, 0, None) == sa.SA_EINVAL
+    assert L.sa_select_dev(None, ctypes.byref(sp), None, None, None, 0, None, None) == sa.SA_EINVAL
+    n = ctypes.c_uint32(0)
+    assert L.sa_effort_limit(None, None, None, None, 0, 30, None, None, None, ctypes.byref(n)) == sa.SA_EINVAL
+    assert L.sa_server_get_stats(None, None) == sa.SA_EINVAL
+    assert "NULL" in sa.sa_last_error()
