@@ -1001,14 +1001,21 @@ void parallel_for(size_t n, unsigned threads, F&& fn) {
         return;
     }
     std::atomic<size_t> next{0};
+    std::atomic<bool> failed{false};
     auto worker = [&] {
-        for (size_t k = next++; k < n; k = next++) fn(k);
+        try {
+            for (size_t k = next++; k < n; k = next++) fn(k);
+        } catch (...) {
+            failed = true;                 // reported to the caller after the join
+            next = n;
+        }
     };
     std::vector<std::thread> pool;
     pool.reserve(threads - 1);
     for (unsigned t = 1; t < threads; t++) pool.emplace_back(worker);
     worker();
     for (auto& th : pool) th.join();
+    if (failed) throw std::bad_alloc();
 }
 
 unsigned staging_threads(uint64_t bytes) {
@@ -1123,14 +1130,23 @@ void slot_main(sa_server* S, sa_server::Slot* slot) {
             S->counters.coalesced += batch.size() - 1;
             S->counters.jobs += nj;
         }
-        int rc = run_batch(S, slot, batch, hjobs, hreads, hout, hcig);
+        int rc;
+        try {
+            rc = run_batch(S, slot, batch, hjobs, hreads, hout, hcig);
+        } catch (...) {
+            rc = fail(SA_ENOMEM, "host memory exhausted while staging a batch");
+        }
         std::vector<int> rcs(batch.size(), rc);
         std::vector<std::string> msgs(batch.size(), rc == SA_OK ? std::string() : std::string(g_err));
         if (rc != SA_OK && batch.size() > 1) {
             // one request's error (an invalid job) must not fail its batch mates
             for (size_t k = 0; k < batch.size(); k++) {
                 std::vector<std::shared_ptr<Request>> one{batch[k]};
-                rcs[k] = run_batch(S, slot, one, hjobs, hreads, hout, hcig);
+                try {
+                    rcs[k] = run_batch(S, slot, one, hjobs, hreads, hout, hcig);
+                } catch (...) {
+                    rcs[k] = fail(SA_ENOMEM, "host memory exhausted while staging a request");
+                }
                 msgs[k] = rcs[k] == SA_OK ? std::string() : std::string(g_err);
             }
         }
