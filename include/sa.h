@@ -183,7 +183,8 @@ int sa_align_batch_dev(sa_reference* ref, const sa_params* params, const sa_job*
  *
  * It computes what sa_align_batch_dev computes with want_cigar = 0 (score,
  * read/reference ends, second best and its end, flags; begins -1, no CIGAR;
- * params->want_cigar, width and form are ignored) on device buffers d_jobs,
+ * params->want_cigar, width and form are ignored; the scores and mode are
+ * checked with the same limits as sa_align_batch) on device buffers d_jobs,
  * d_reads and d_out of the reference's device, and calls no cudaMalloc,
  * cudaFree or allocating library routine.  Its intermediate arrays live in one
  * file-scope device array of SA_NOALLOC_SCRATCH_BYTES that every device which
@@ -198,7 +199,9 @@ int sa_align_batch_dev(sa_reference* ref, const sa_params* params, const sa_job*
  * contents (the call clears what must start at zero), so calls whose work
  * overlaps on the GPU -- on different streams or from different host threads
  * -- race on it and must not be issued.  The work runs on cuda_stream (NULL:
- * the reference's own stream) and the call returns when it has completed. */
+ * the reference's own stream); the call reads the batch's validation status
+ * back to the host between its kernels and returns only when all of its work
+ * has completed. */
 #define SA_NOALLOC_SCRATCH_BYTES (32u << 20)
 int sa_align_batch_noalloc(sa_reference* ref, const sa_params* params, const sa_job* d_jobs,
                            uint32_t n_jobs, const char* d_reads, uint64_t reads_len,

@@ -198,22 +198,9 @@ struct sa_reference {
 namespace {
 
 int check_params(const sa_params* p, Score* sc) {
-    if (!p) return fail(SA_EINVAL, "params is NULL");
-    const sa_scoring& s = p->sc;
-    if (s.match < 0 || s.mismatch < 0 || s.gap_open < 0 || s.gap_extend < 0)
-        return fail(SA_EINVAL, "scores are magnitudes and must be >= 0");
-    if (s.match > 2047 || s.mismatch > 16383 || (int64_t)s.gap_open + s.gap_extend > 16383)
-        return fail(SA_EINVAL, "match must be <= 2047, mismatch and gap_open + gap_extend <= 16383");
-    if (p->mode != SA_LOCAL && p->mode != SA_GLOCAL) return fail(SA_EINVAL, "mode must be SA_LOCAL or SA_GLOCAL");
+    TRY(sa::check_scoring(p, sc));
     if (p->width != 0 && p->width != 16 && p->width != 32) return fail(SA_EINVAL, "width must be 0, 16 or 32");
     if (p->form != SA_FORM_BATCHED && p->form != SA_FORM_PLAIN) return fail(SA_EINVAL, "unknown form");
-    sc->a = s.match;
-    sc->b = -s.mismatch;
-    sc->GO = -(s.gap_open + s.gap_extend);
-    sc->GE = -s.gap_extend;
-    sc->dm = sc->a - sc->GO;
-    sc->dx = sc->b - sc->GO;
-    sc->mode = p->mode;
     return SA_OK;
 }
 
@@ -1639,6 +1626,28 @@ int sa_server_destroy(sa_server* S) {
 namespace sa {
 RefView ref_view(const sa_reference* R) {
     return RefView{R->d_words, R->len, R->device, R->num_sms, R->own};
+}
+
+// Scores and mode of every alignment entry point.  The limits keep each kernel
+// exact: a LOCAL best score must fit 21 bits (the 32-bit score pass forms keys
+// H * 1024 + row tag in an int32), and every 16-bit value below the overflow
+// threshold of the packed pass must fit a signed half.
+int check_scoring(const sa_params* p, Score* sc) {
+    if (!p) return fail(SA_EINVAL, "params is NULL");
+    const sa_scoring& s = p->sc;
+    if (s.match < 0 || s.mismatch < 0 || s.gap_open < 0 || s.gap_extend < 0)
+        return fail(SA_EINVAL, "scores are magnitudes and must be >= 0");
+    if (s.match > 2047 || s.mismatch > 16383 || (int64_t)s.gap_open + s.gap_extend > 16383)
+        return fail(SA_EINVAL, "match must be <= 2047, mismatch and gap_open + gap_extend <= 16383");
+    if (p->mode != SA_LOCAL && p->mode != SA_GLOCAL) return fail(SA_EINVAL, "mode must be SA_LOCAL or SA_GLOCAL");
+    sc->a = s.match;
+    sc->b = -s.mismatch;
+    sc->GO = -(s.gap_open + s.gap_extend);
+    sc->GE = -s.gap_extend;
+    sc->dm = sc->a - sc->GO;
+    sc->dx = sc->b - sc->GO;
+    sc->mode = p->mode;
+    return SA_OK;
 }
 
 // the calling thread's sa_last_error() message, for the other translation units

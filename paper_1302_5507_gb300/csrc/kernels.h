@@ -107,6 +107,8 @@ struct RefView {
 };
 RefView ref_view(const sa_reference* R);
 int set_error(int code, const char* msg);   // sets sa_last_error() for the calling thread
+// validates params->sc and params->mode (SA_EINVAL with a message) and fills *sc
+int check_scoring(const sa_params* p, Score* sc);
 
 // scan scratch: number of uint64 block sums needed for n elements
 inline uint64_t scan_bsum_len(uint64_t n) { return (n + 1023) / 1024 + 1; }

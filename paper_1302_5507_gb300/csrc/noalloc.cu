@@ -75,38 +75,14 @@ struct Ctl {
 
 inline size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// JobState -> sa_result for a score-only call (the same fields and rules as the
-// finalisation of sa_align_batch_dev with want_cigar = 0)
+// JobState -> sa_result for a score-only call: the row sa_align_batch_dev's
+// finalisation writes with want_cigar = 0 (one helper serves both)
 __global__ void k_noalloc_results(const sa_job* __restrict__ jobs, uint32_t n_jobs,
                                   const sa::JobState* __restrict__ state, int32_t min_score,
                                   sa_result* __restrict__ out) {
     const uint32_t job = blockIdx.x * blockDim.x + threadIdx.x;
     if (job >= n_jobs) return;
-    const sa_job J = jobs[job];
-    const sa::JobState st = state[job];
-    sa_result r;
-    r.score = st.best;
-    r.second = SA_NO_SCORE;
-    r.read_begin = -1;
-    r.read_end = -1;
-    r.ref_begin = -1;
-    r.ref_end = -1;
-    r.second_ref_end = -1;
-    r.cigar_off = 0;
-    r.cigar_len = 0;
-    r.flags = 0;
-    r._pad = 0;
-    if (st.best < min_score) r.flags |= SA_RES_BELOW_MIN;
-    if (st.flags & sa::kStEmpty) {
-        r.flags |= SA_RES_EMPTY;
-        r.score = 0;
-    } else {
-        r.second = st.second;
-        r.second_ref_end = st.second_i ? (int64_t)J.ref_pos + st.second_i : -1;
-        r.read_end = st.j_star;
-        r.ref_end = (int64_t)J.ref_pos + st.i_star;
-    }
-    out[job] = r;
+    out[job] = sa::score_result(jobs[job], state[job], min_score);
 }
 
 #define CK(expr)                                                                              \
@@ -120,12 +96,12 @@ __global__ void k_noalloc_results(const sa_job* __restrict__ jobs, uint32_t n_jo
 
 int run(sa_reference* R, const sa_params* P, const sa_job* d_jobs, uint32_t n_jobs,
         const char* d_reads, uint64_t reads_len, sa_result* d_out, void* stream) {
-    if (!R || !P) return err(SA_EINVAL, "NULL reference or params");
-    const sa_scoring& s = P->sc;
-    if (s.match < 0 || s.mismatch < 0 || s.gap_open < 0 || s.gap_extend < 0 || s.match > 16383 ||
-        s.mismatch > 16383 || (int64_t)s.gap_open + s.gap_extend > 16383)
-        return err(SA_EINVAL, "scores must be magnitudes in 0..16383 (gap_open + gap_extend too)");
-    if (P->mode != SA_LOCAL && P->mode != SA_GLOCAL) return err(SA_EINVAL, "mode must be SA_LOCAL or SA_GLOCAL");
+    if (!R) return err(SA_EINVAL, "reference is NULL");
+    // the same limits as every other alignment entry point (a LOCAL best score
+    // must fit the 21 bits of the 32-bit score pass's keys: match <= 2047)
+    sa::Score sc;
+    const int prc = sa::check_scoring(P, &sc);
+    if (prc != SA_OK) return prc;
     if (n_jobs == 0) return SA_OK;
     if (!d_jobs || !d_reads || !d_out) return err(SA_EINVAL, "NULL job, read or result buffer");
     const sa::RefView V = sa::ref_view(R);
@@ -188,13 +164,7 @@ int run(sa_reference* R, const sa_params* P, const sa_job* d_jobs, uint32_t n_jo
     A.pos_begin = 0;
     A.pos_count = n_jobs;
     A.item_counter = &ctl->item_counter;
-    A.sc.a = s.match;
-    A.sc.b = -s.mismatch;
-    A.sc.GO = -(s.gap_open + s.gap_extend);
-    A.sc.GE = -s.gap_extend;
-    A.sc.dm = A.sc.a - A.sc.GO;
-    A.sc.dx = A.sc.b - A.sc.GO;
-    A.sc.mode = P->mode;
+    A.sc = sc;
     A.state = reinterpret_cast<sa::JobState*>(base + off_state);
     A.colbest = reinterpret_cast<int32_t*>(base + off_cb);
     A.cb_stride = sa::cb_words(hs.max_m);

@@ -124,6 +124,37 @@ struct JobState {
 constexpr uint32_t kStEmpty = 1u;      // LOCAL: no positive cell
 constexpr uint32_t kStOverflow = 2u;   // 16-bit pass may have overflowed: recompute in 32-bit
 
+// The fields of a result row that the score pass alone decides: score, ends,
+// second best and flags (SA_RES_BELOW_MIN when best < min_score, then
+// SA_RES_EMPTY with score 0 and no ends or second when no cell was positive);
+// begins -1 and no CIGAR.  Every entry point that writes sa_result rows starts
+// from this row.
+__device__ __forceinline__ sa_result score_result(const sa_job& J, const JobState& st, int32_t min_score) {
+    sa_result r;
+    r.score = st.best;
+    r.second = SA_NO_SCORE;
+    r.read_begin = -1;
+    r.read_end = -1;
+    r.ref_begin = -1;
+    r.ref_end = -1;
+    r.second_ref_end = -1;
+    r.cigar_off = 0;
+    r.cigar_len = 0;
+    r.flags = 0;
+    r._pad = 0;
+    if (st.best < min_score) r.flags |= SA_RES_BELOW_MIN;
+    if (st.flags & kStEmpty) {
+        r.flags |= SA_RES_EMPTY;
+        r.score = 0;
+    } else {
+        r.second = st.second;
+        r.second_ref_end = st.second_i ? (int64_t)J.ref_pos + st.second_i : -1;
+        r.read_end = st.j_star;
+        r.ref_end = (int64_t)J.ref_pos + st.i_star;
+    }
+    return r;
+}
+
 // Sub-problem of the direction-bit pass: rows 1..rows of the read against the
 // window columns i_lo..i_lo+w-1 (1-based); w == 0 means "no traceback".
 struct Rect {

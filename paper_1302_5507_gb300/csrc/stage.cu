@@ -661,27 +661,10 @@ __global__ void k_finalize(const sa_job* __restrict__ jobs, uint32_t n_jobs,
     if (job >= n_jobs) return;
     const sa_job J = jobs[job];
     const JobState st = state[job];
-    sa_result r;
-    r.score = st.best;
-    r.second = SA_NO_SCORE;
-    r.read_begin = -1;
-    r.read_end = -1;
-    r.ref_begin = -1;
-    r.ref_end = -1;
-    r.second_ref_end = -1;
+    sa_result r = score_result(J, st, min_score);
     r.cigar_off = (uint32_t)coff[job];
     r.cigar_len = count[job];
-    r.flags = 0;
-    r._pad = 0;
-    if (st.best < min_score) r.flags |= SA_RES_BELOW_MIN;
-    if (st.flags & kStEmpty) {
-        r.flags |= SA_RES_EMPTY;
-        r.score = 0;
-    } else {
-        r.second = st.second;
-        r.second_ref_end = st.second_i ? (int64_t)J.ref_pos + st.second_i : -1;
-        r.read_end = st.j_star;
-        r.ref_end = (int64_t)J.ref_pos + st.i_star;
+    if (!(st.flags & kStEmpty)) {
         const bool tb_done = want_cigar && st.best >= min_score;
         if (tb_done) {
             const TbOut t = tb[job];
