@@ -1,23 +1,29 @@
 """Benchmark: GCUPS of batched affine-gap alignment (score + traceback + CIGAR)
-on one GB300, on the mate-rescue workload (1M unaligned 150 bp mates, each
-against an 800 bp window placed from its mate; synthetic 100 Mbp genome).
+on one GB300.  The headline line is the uneven-length batch: 4M jobs, reads of
+50-250 bp against windows of 1.5-6x their length on a synthetic 100 Mbp genome,
+16-bit packed scores with exact overflow detection and a 32-bit rerun, the
+length-bucket plan picked by the library's autotuner (sa_tune), and the score
+segment replayed as a CUDA graph.  The same line carries the mate-rescue batch
+(1M 150 bp mates against 800 bp windows) in 32-bit scores, with its 16-bit
+figure beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 One step = one call of the library on the whole batch: staging (read packing,
-bucketing), the score pass, the reduced direction pass, traceback, CIGAR
-compaction and results.  `value` times steps whose inputs already sit in device
-memory (sa_align_batch_dev); `e2e` times sa_align_batch from pinned host
-buffers, host<->device copies included.  Cells = sum of n*m (full matrices).
-With --impl reference the CPU oracle is timed instead, on a bounded sample.
+bucketing), the score pass, the overflow rerun, the reduced direction pass,
+traceback, CIGAR compaction and results.  `value` times steps whose inputs
+already sit in device memory (sa_align_batch_dev); `e2e` times sa_align_batch
+from pinned host buffers, host<->device copies included.  Cells = sum of n*m
+(full matrices).  With --impl reference the CPU oracle is timed instead, on a
+bounded sample of the same workload.
 """
 from __future__ import annotations
 
 import argparse
+import csv
 import hashlib
 import json
 import os
-import re
 import statistics
 import subprocess
 import sys
@@ -30,9 +36,20 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "GCUPS (affine DP incl. traceback) at 1 GB300 vs plain form; p50/p99 request latency"
-WORKLOAD = "mate_rescue: 1M jobs, 150 bp mate (reverse-complemented) vs 800 bp window, 100 Mbp GC41 genome + 5% repeats"
+WORKLOADS = {
+    "c3": "uneven (C3): 4M jobs, n U[50,250], m U[1.5n,6n], windows in a 100 Mbp GC41 genome + 5% repeats; "
+          "int16 packed + exact int32 rerun, autotuned plan, score segment replayed as a CUDA graph",
+    "c2": "mate_rescue (C2): 1M jobs, 150 bp mate (reverse-complemented) vs 800 bp window, 100 Mbp GC41 genome "
+          "+ 5% repeats; int32 scores",
+}
+DEFAULT_JOBS = {"c3": 4_000_000, "c2": 1_000_000}
 OPS_PER_CELL = 6          # lane-ops per cell of the roofline formula: 1 add H+GO, 2 add-max (E, F), 1 add diag+delta, 1 max3, 1 column-max update
-PROBE_S16X2, PROBE_S32 = 6, 0   # operation codes of the DPX throughput probe (viaddmax)
+# pipe-aware bound: the ALU-pipe operations the recurrence cannot do without, per
+# register of two 16-bit cells (or one 32-bit cell): the add-maxima of G (with the
+# zero floor), E and F and the three-way maximum of H; the adds that form H + S_GO
+# and the cell keys run on the FMA pipe, which issues beside the ALU pipe
+ALU_OPS_PER_REG = 4
+PROBE_S16X2, PROBE_S32, PROBE_IMAD = 6, 0, 5   # operation codes of the throughput probe
 
 
 def parse():
@@ -42,7 +59,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--jobs", type=int, default=None,
-                    help="jobs per GPU (default: the configuration's size, 1M for c2)")
+                    help="jobs per GPU (default: the configuration's size, 4M for c3, 1M for c2)")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default plan (skip sa_tune)")
+    ap.add_argument("--no-c2", action="store_true", help="skip the mate-rescue object of the headline line")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving latency run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
@@ -50,12 +69,13 @@ def parse():
     ap.add_argument("--probe-ops", action="store_true",
                     help="print the measured issue rate (lane-ops per SM per clock) of every "
                          "operation of the throughput probe and exit")
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "pairs"],
-                    help="c2 (default): the mate-rescue headline line; c1 plain windows (plain and "
-                         "batched forms, both modes) plus mate rescue in GLOCAL; c3 uneven lengths, "
-                         "c4 low similarity, c5 serving sweep, pairs: paired reads with several "
-                         "candidate windows each (effort limit, alignment, selection): one extra "
-                         "JSON line each (1 GPU)")
+    ap.add_argument("--config", default="c3", choices=["c1", "c2", "c3", "c3-detail", "c4", "c5", "pairs"],
+                    help="c3 (default): the headline line on the uneven 4M-job batch; c2: the same "
+                         "line on the mate-rescue batch; c1 plain windows (plain and batched forms, "
+                         "both modes) plus mate rescue in GLOCAL; c3-detail: the uneven batch per "
+                         "width and plan; c4 low similarity, c5 serving sweep, pairs: paired reads "
+                         "with several candidate windows each (effort limit, alignment, selection): "
+                         "one extra JSON line each (1 GPU)")
     return ap.parse_args()
 
 
@@ -127,17 +147,21 @@ def kernel_source_sha():
     return h.hexdigest()[:12]
 
 
-def traffic_from_profiles():
-    """DRAM bytes per launch of the score-pass kernel from the committed ncu
-    summary, if it was taken on the current kernel sources (else None)."""
-    path = os.path.join(ROOT, "profiles", "fill16_score_mate_rescue.md")
-    if not os.path.exists(path):
+TRAFFIC_CSV = os.path.join(ROOT, "profiles", "score_pass_traffic.csv")
+
+
+def traffic_per_step(config: str, jobs: int):
+    """DRAM read + write bytes of the score-pass kernels in one step of `config`
+    with `jobs` jobs, from the committed ncu figures (profiles/score_pass_traffic.csv:
+    bytes of the captured step scaled by jobs), if they were taken on the current
+    kernel sources; else None."""
+    if not os.path.exists(TRAFFIC_CSV):
         return None
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s*\(kernel sources sha1 ([0-9a-f]+)\)",
-                  open(path).read())
-    if not m:
-        return None
-    return float(m.group(1)) if m.group(2) == kernel_source_sha() else None
+    with open(TRAFFIC_CSV) as f:
+        for row in csv.DictReader(f):
+            if row["config"] == config and row["kernel_sources_sha1"] == kernel_source_sha():
+                return float(row["dram_bytes"]) * jobs / float(row["jobs"])
+    return None
 
 
 def direction_bound(stats, wl):
@@ -186,14 +210,15 @@ def probe_all_ops():
 
 def dpx_lane_ops_per_sm_clk(local_rank: int):
     """Measured issue rate of the packed 16-bit and the 32-bit add-max (DPX)
-    instructions, lane-operations per SM per clock, from the probe library; the
-    clock is the median SM clock sampled while the probe runs."""
+    instructions and of the integer multiply-add, lane-operations per SM per
+    clock, from the probe library; the clock is the median SM clock sampled
+    while the probe runs."""
     import ctypes
     from paper_1302_5507_gb300 import build as sa_build
     lib = ctypes.CDLL(sa_build.PROBE)
     lib.sa_probe_ops_per_sm_clk.restype = ctypes.c_double
     lib.sa_probe_ops_per_sm_clk.argtypes = [ctypes.c_int, ctypes.c_double]
-    rates = {PROBE_S16X2: [], PROBE_S32: []}
+    rates = {PROBE_S16X2: [], PROBE_S32: [], PROBE_IMAD: []}
     with ClockSampler(local_rank) as clk:
         t0 = time.perf_counter()
         while time.perf_counter() - t0 < 1.5:
@@ -201,7 +226,7 @@ def dpx_lane_ops_per_sm_clk(local_rank: int):
                 rates[op].append(lib.sa_probe_ops_per_sm_clk(op, 1e-6))   # ops per second per SM
     mhz = clk.summary()["sm_mhz"] or 2070.0
     out = {"sm_mhz": mhz}
-    for op, key in ((PROBE_S16X2, "viaddmax_s16x2"), (PROBE_S32, "viaddmax_s32")):
+    for op, key in ((PROBE_S16X2, "viaddmax_s16x2"), (PROBE_S32, "viaddmax_s32"), (PROBE_IMAD, "imad_s32")):
         good = [r for r in rates[op] if r > 0]
         out[key] = statistics.median(good) / (mhz * 1e6) if good else None
     return out
@@ -231,11 +256,21 @@ def cpu_baseline(wl, target_s: float = 8.0):
                               "sample": f"first {n1} jobs ({one.cells:.3g} cells, {dt1:.1f} s)"}}
 
 
-def make_workload(rank: int, n_jobs: int, genome_len: int = 100_000_000):
-    """This rank's shard: jobs rank*n_jobs .. (rank+1)*n_jobs-1 of the mate-rescue
-    stream on the shared genome (independent jobs, no exchange between ranks)."""
+def make_workload(config: str, rank: int, n_jobs: int, genome_len: int = 100_000_000):
+    """This rank's shard of `config`: jobs rank*n_jobs .. (rank+1)*n_jobs-1 of the
+    workload's stream on the shared genome (independent jobs, no exchange between
+    ranks)."""
     import workloads
-    return workloads.mate_rescue(seed=1, n_pairs=n_jobs, genome_len=genome_len, first_item=rank * n_jobs)
+    if config == "c2":
+        return workloads.mate_rescue(seed=1, n_pairs=n_jobs, genome_len=genome_len, first_item=rank * n_jobs)
+    return workloads.uneven(seed=1, n_jobs=n_jobs, genome_len=genome_len, first_item=rank * n_jobs)
+
+
+def tune_sample():
+    """The autotuner's sample: 200k jobs of the uneven distribution, drawn from
+    another part of its stream than the timed batch."""
+    import workloads
+    return workloads.uneven(seed=1, n_jobs=200_000, first_item=1 << 28)
 
 
 def max_over_ranks(x: float, dist, device) -> float:
@@ -252,7 +287,8 @@ def run_reference(args, rank, world):
     import workloads  # noqa: F401
     if rank != 0:
         return
-    wl = make_workload(0, args.jobs or 1_000_000)
+    config = args.config if args.config in WORKLOADS else "c3"
+    wl = make_workload(config, 0, args.jobs or DEFAULT_JOBS[config])
     import oracle
     nthreads = oracle.threads()
     # each step: a bounded sample (about 2 s of oracle work), same workload and metric
@@ -263,7 +299,8 @@ def run_reference(args, rank, world):
     n = int(max(1000, 2.0 * rate / (wl.cells / wl.n_jobs)))
     times, cells = [], 0
     for step in range(args.warmup + args.steps):
-        sub = wl.subset(np.arange(step * 997 % max(1, wl.n_jobs - n), step * 997 % max(1, wl.n_jobs - n) + n))
+        lo = step * 997 % max(1, wl.n_jobs - n)
+        sub = wl.subset(np.arange(lo, lo + n))
         t0 = time.perf_counter()
         oracle.align(sub, n_threads=nthreads)
         dt = time.perf_counter() - t0
@@ -275,7 +312,7 @@ def run_reference(args, rank, world):
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "jobs_per_step": n, "mode": "LOCAL", "scoring": "1/2/2/1",
+            "config": {"workload": WORKLOADS[config], "jobs_per_step": n, "mode": "LOCAL", "scoring": "1/2/2/1",
                        "cache": "oracle on host cores"},
             "cpu_baseline": {"value": value, "unit": "GCUPS", "cores": nthreads, "kind": "oracle",
                              "sample": f"{n} consecutive jobs per step of {wl.n_jobs}"},
@@ -283,19 +320,71 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def roofline_of(cells, fill_ms, packed, dpx, sm_mhz, n_sm, config, jobs):
+    """Roofline of the score pass (the dominant kernel family): achieved cells per
+    second over the score-pass phase, against (1) the survey's formula, 6 DPX
+    lane-ops per cell at the measured DPX rate, and (2) a pipe-aware bound: the
+    four ALU-pipe operations per register of cells that the recurrence needs, at
+    the same rate, with the FMA-pipe adds (H + S_GO, keys, the 32-bit diagonal
+    term) bounded separately at the measured multiply-add rate."""
+    lanes = dpx["viaddmax_s16x2" if packed else "viaddmax_s32"] or 64.0
+    imad = dpx.get("imad_s32") or 64.0
+    cells_per_op = 2 if packed else 1
+    clk = n_sm * sm_mhz * 1e6
+    peak = clk * lanes * cells_per_op / OPS_PER_CELL / 1e9
+    alu_bound = clk * lanes * cells_per_op / ALU_OPS_PER_REG / 1e9
+    fma_ops = 2 if packed else 3          # per register: H+S_GO and the key (+ the diagonal add in 32-bit)
+    fma_bound = clk * imad * cells_per_op / fma_ops / 1e9
+    pipe_peak = min(alu_bound, fma_bound)
+    achieved = cells / (fill_ms / 1e3) / 1e9 if fill_ms > 0 else None
+    traffic = traffic_per_step(config, jobs)
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GCUPS",
+            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+            "kernel": ("k_fill16 packed 16-bit score pass" if packed else "k_fill32 score pass")
+                      + " (score, ends, colbest, second best), all length buckets of one step; "
+                        "CUDA events around the score-pass phase on the launching stream",
+            "peak_basis": f"{n_sm} SMs x {lanes:.1f} DPX lane-ops/SM/clk (measured, probe) x "
+                          f"{sm_mhz:.0f} MHz (median under load) x {cells_per_op} cells per lane-op "
+                          f"/ {OPS_PER_CELL} lane-ops per cell",
+            "pipe_aware": {"peak": pipe_peak, "frac": (achieved / pipe_peak) if achieved else None,
+                           "alu_bound": alu_bound, "fma_bound": fma_bound,
+                           "basis": f"ALU pipe: {ALU_OPS_PER_REG} essential ALU-pipe ops (add-max G with the "
+                                    f"floor, E, F; max3 H) per register of {cells_per_op} cell(s) at "
+                                    f"{lanes:.1f} lane-ops/SM/clk; FMA pipe: {fma_ops} multiply-adds per "
+                                    f"register at {imad:.1f} lane-ops/SM/clk (measured)"},
+            "traffic_basis": "DRAM read+write bytes per step of the score-pass kernels from one ncu capture "
+                             "of a smaller batch of the same workload, scaled by jobs "
+                             "(profiles/score_pass_traffic.csv); null when the kernel sources changed since",
+            "dpx_probe": dpx, "kernel_sources_sha1": kernel_source_sha()}
+
+
 def run_ours(args, rank, world, dist):
     import torch
     import paper_1302_5507_gb300 as sa
     import __graft_entry__
+    config = args.config
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     __graft_entry__.build()
-    wl = make_workload(rank, args.jobs or 1_000_000)
+    wl = make_workload(config, rank, args.jobs or DEFAULT_JOBS[config])
     jobs = sa.jobs_array(wl.read_off, wl.read_len, wl.flags, wl.ref_pos, wl.win_len)
     ref = sa.Reference(wl.ref, device=local_rank)
-    params = sa.make_params()                       # no phase events: the score segment replays as a graph
-    params_prof = sa.make_params(profile=True)      # phase timing (CUDA events per phase)
+    width = 32 if config == "c2" else 0           # C2's scores are int32; C3 packs 16-bit pairs
+    tuned = None
+    if config == "c3" and not args.no_tune:
+        # the plan (configuration per read length, width per configuration) from the
+        # library's autotuner on a separate sample of the same distribution
+        smp = tune_sample()
+        t0 = time.perf_counter()
+        classes = ref.tune(sa.jobs_array(smp.read_off, smp.read_len, smp.flags, smp.ref_pos, smp.win_len),
+                           smp.reads)
+        plan = np.frombuffer(ref.plan()[8:], np.uint8)
+        tuned = {"classes_tuned": int(classes), "seconds": time.perf_counter() - t0,
+                 "sample": "200k jobs of the same distribution (another part of its stream)",
+                 "cfg_of_length": {str(n): int(plan[n]) for n in (50, 100, 150, 200, 250)}}
+    params = sa.make_params(width=width)                    # no phase events: the score segment replays as a graph
+    params_prof = sa.make_params(width=width, profile=True)  # phase timing (CUDA events per phase)
     cap = sa.cigar_max_ops(wl.read_len)
     stream = torch.cuda.Stream(device=dev)
     d_jobs = torch.from_numpy(jobs.view(np.uint8)).to(dev)
@@ -318,12 +407,10 @@ def run_ours(args, rank, world, dist):
     with ClockSampler(local_rank) as clk:
         barrier()
         ev0.record(stream)
-        t_host = time.perf_counter()
         for _ in range(args.steps):
             ref.align_dev(d_jobs, d_reads, d_out, d_cig, params, stream=stream)
         ev1.record(stream)
         barrier()
-        t_host = time.perf_counter() - t_host
         stats = ref.stats()
         # the same steps again with per-phase CUDA events (score-pass time for the roofline)
         step_stats = []
@@ -349,7 +436,7 @@ def run_ours(args, rank, world, dist):
     cig_np = h_cig.numpy().view(np.uint32)
     jobs_np = h_jobs.numpy().view(sa.JOB_DTYPE)
     reads_np = h_reads.numpy()
-    e2e_params = sa.make_params()
+    e2e_params = sa.make_params(width=width)
     for _ in range(max(1, args.warmup - 1)):
         ref.align(jobs_np, reads_np, e2e_params, out=out_np, cigar=cig_np, stream=None)
     barrier()
@@ -378,10 +465,11 @@ def run_ours(args, rank, world, dist):
         barrier()
         pms = e0.elapsed_time(e1) / nplain
         plain = {"value": cells_rank / (pms / 1e3) / 1e9, "unit": "GCUPS", "ms_per_step": pms,
-                 "form": "plain: 65,536-job batches, one whole-window direction fill + one traceback launch each"}
+                 "form": "plain: 65,536-job batches in input order, one configuration for the longest "
+                         "read, one whole-window direction fill + one traceback launch each (int32)"}
 
     phases = {k: float(np.mean([st[k] for st in step_stats]))
-              for k in ("ms_stage", "ms_fill", "ms_rect", "ms_traceback", "ms_finalize", "ms_total")}
+              for k in ("ms_stage", "ms_fill", "ms_rerun", "ms_rect", "ms_traceback", "ms_finalize", "ms_total")}
     clocks = clk.summary()
     sm_mhz = clocks["sm_mhz"] or 2070.0
     props = torch.cuda.get_device_properties(dev)
@@ -390,22 +478,10 @@ def run_ours(args, rank, world, dist):
     packed = int(stats["jobs16"]) == wl.n_jobs
     graph_replays = int(stats["graph_replays"])
     dpx = dpx_lane_ops_per_sm_clk(local_rank)
-    lanes = dpx["viaddmax_s16x2" if packed else "viaddmax_s32"] or 64.0
-    cells_per_op = 2 if packed else 1
-    peak = n_sm * lanes * sm_mhz * 1e6 * cells_per_op / OPS_PER_CELL / 1e9
     fill_avg = float(np.mean(fill_ms)) if fill_ms else 0.0
-    achieved = cells_rank / (fill_avg / 1e3) / 1e9 if fill_avg > 0 else None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GCUPS",
-                "frac": (achieved / peak) if achieved else None, "traffic": traffic_from_profiles(),
-                "kernel": ("k_fill16 packed 16-bit score pass" if packed else "k_fill32 score pass")
-                          + " (score, ends, colbest, second best); CUDA events around the score-pass phase",
-                "peak_basis": f"{n_sm} SMs x {lanes:.1f} DPX lane-ops/SM/clk (measured, probe) x "
-                              f"{sm_mhz:.0f} MHz (median under load) x {cells_per_op} cells per lane-op "
-                              f"/ {OPS_PER_CELL} lane-ops per cell",
-                "dpx_probe": dpx, "kernel_sources_sha1": kernel_source_sha(),
-                # the traceback's own bound: its direction data (0.5 B per banded cell as
-                # nibbles, 1 B as byte heights) against the measured copy bandwidth
-                "direction_data_bound": direction_bound(stats, wl)}
+    roofline = roofline_of(cells_rank, fill_avg, packed, dpx, sm_mhz, n_sm, config, wl.n_jobs)
+    # the traceback's own bound: its direction data against the measured copy bandwidth
+    roofline["direction_data_bound"] = direction_bound(stats, wl)
 
     line = None
     if rank == 0:
@@ -413,15 +489,20 @@ def run_ours(args, rank, world, dist):
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "s16x2" if packed else "int32",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "jobs_per_gpu": wl.n_jobs, "cells_per_gpu": cells_rank,
+                "config": {"workload": WORKLOADS[config], "jobs_per_gpu": wl.n_jobs, "cells_per_gpu": cells_rank,
                            "mode": "LOCAL", "scoring": "match 1, mismatch 2, gap open 2, gap extend 1",
-                           "form": "batched", "cache": "inputs + direction arena larger than L2 (no flush)",
+                           "width": width or "auto (16-bit pairs where no job of a bucket can overflow)",
+                           "plan": "autotuned (sa_tune)" if tuned else "default",
+                           "form": "batched", "cache": "inputs, lane-key scratch and direction data larger "
+                                                       "than L2 (no flush)",
                            "parallelism": f"independent shards x{world}"},
                 "e2e": {"value": e2e_value, "unit": "GCUPS",
                         "h2d_bytes_per_step": int(jobs.nbytes + wl.reads.nbytes),
                         "d2h_bytes_per_step": int(len(jobs) * 56 + used * 4)},
                 "gpu_launches": launches,
                 "score_segment_graph_replayed": bool(graph_replays),
+                "overflow_reruns": int(stats["overflow_reruns"]),
+                "autotune": tuned,
                 "roofline": roofline,
                 "clocks": clocks,
                 "phases_ms": phases,
@@ -429,12 +510,30 @@ def run_ours(args, rank, world, dist):
                                       "rectangle": int(stats["rect_jobs"])},
                 "plain_form": plain}
 
+    # --- the mate-rescue batch (C2) at its own width (int32), 16-bit beside it
+    if rank == 0 and config == "c3" and not args.no_c2:
+        mate = make_workload("c2", 0, DEFAULT_JOBS["c2"])
+        with sa.Reference(mate.ref, device=local_rank) as mref:
+            c2 = device_line(sa, mref, mate, args, WORKLOADS["c2"], widths=(32, 0), cigar=(True,))
+        r32, r16 = c2["rows"]
+        line["c2_mate_rescue"] = {
+            "value": r32["gcups"], "unit": "GCUPS", "dtype": "int32", "ms_per_step": r32["ms_per_step"],
+            "score_pass_gcups": r32["score_pass_gcups"], "jobs": c2["jobs"], "cells": c2["cells"],
+            "phases_ms": r32["phases_ms"],
+            "note_s16x2": {"value": r16["gcups"], "score_pass_gcups": r16["score_pass_gcups"],
+                           "ms_per_step": r16["ms_per_step"],
+                           "what": "the same batch with the default width (16-bit packed pairs, exact)"},
+            "timing": "CUDA events around the steps (phase events on)"}
+
     # --- serving latency (coalescing server), rank 0 only: a short run on this genome
+    # (with the default plan, whose coarser buckets suit the server's smaller batches)
     if rank == 0 and not args.no_serving:
         import workloads
+        if tuned:
+            ref.set_plan(None)
         sizes, ppm = workloads.serving_arrivals(seed=3, n_requests=40)
         reqs = [workloads.serving_request(wl.ref, 3, k, int(sizes[k])) for k in range(40)]
-        line["serving"] = serving_run(sa, ref, reqs, ppm, (0.8,), genome="the mate-rescue genome (100 Mbp)",
+        line["serving"] = serving_run(sa, ref, reqs, ppm, (0.8,), genome="the uneven batch's genome (100 Mbp)",
                                       slots=args.slots)
     ref.close()
     if rank == 0 and not args.no_cpu:
@@ -455,15 +554,20 @@ def concat(reqs):
         np.concatenate([r.truth for r in reqs]), dict(reqs[0].meta))
 
 
-def serving_run(sa, ref, reqs, ppm, loads, genome: str, plain: bool = False, slots: int = 2):
+def serving_run(sa, ref, reqs, ppm, loads, genome: str, plain: bool = False, slots: int = 2,
+                check: bool = False):
     """Open-loop Poisson arrivals of `reqs` at each offered load (a fraction of the
-    offline batched throughput of the same jobs); p50/p99 submit -> result."""
+    offline batched throughput of the same jobs); p50/p99 submit -> result.
+    check: every served result (all fields and the CIGAR) must equal the offline
+    batched result of the same job, and a seeded sample of the offline results
+    must equal the oracle's."""
     allj = concat(reqs)
     jobs_all = sa.jobs_array(allj.read_off, allj.read_len, allj.flags, allj.ref_pos, allj.win_len)
     ref.align(jobs_all, allj.reads)                       # warm-up (workspace growth)
     t0 = time.perf_counter()
-    ref.align(jobs_all, allj.reads)
+    off_res, off_cig = ref.align(jobs_all, allj.reads)
     offline = allj.cells / (time.perf_counter() - t0)
+    first_job = np.cumsum([0] + [r.n_jobs for r in reqs])
     out = {"requests": len(reqs), "jobs": int(allj.n_jobs), "cells": int(allj.cells), "genome": genome,
            "offline_batched_gcups": offline / 1e9,
            "offline_form": "all jobs of the requests in one sa_align_batch call (host buffers)",
@@ -483,6 +587,7 @@ def serving_run(sa, ref, reqs, ppm, loads, genome: str, plain: bool = False, slo
         rate = load * offline / mean_cells            # requests per second
         gaps = -np.log(np.maximum(ppm.astype(np.float64), 1.0) / 1e6) / rate
         lat, done_cells = [], 0
+        served = {}
         pending = _queue.Queue()
         with sa.Server(ref, sa.make_params(), max_inflight=slots) as srv:
             # warm-up: each slot runs one batch as large as a coalesced batch can get
@@ -497,9 +602,11 @@ def serving_run(sa, ref, reqs, ppm, loads, genome: str, plain: bool = False, slo
                     item = pending.get()
                     if item is None:
                         return
-                    tk, ts, r = item
-                    srv.poll(tk, r.n_jobs, sa.cigar_max_ops(r.read_len), timeout_ms=-1)
+                    tk, ts, r, k = item
+                    _, res, cig = srv.poll(tk, r.n_jobs, sa.cigar_max_ops(r.read_len), timeout_ms=-1)
                     lat.append(time.perf_counter() - ts)
+                    if check:
+                        served[k] = (res, cig)
             th = threading.Thread(target=poller)
             th.start()
             t_start = time.perf_counter()
@@ -508,18 +615,51 @@ def serving_run(sa, ref, reqs, ppm, loads, genome: str, plain: bool = False, slo
                 t_next += gaps[k]
                 while time.perf_counter() < t_next:
                     time.sleep(min(0.001, max(0.0, t_next - time.perf_counter())))
-                pending.put((srv.submit(arrays[k], r.reads), time.perf_counter(), r))
+                pending.put((srv.submit(arrays[k], r.reads), time.perf_counter(), r, k))
                 done_cells += r.cells
             pending.put(None)
             th.join()
             wall = time.perf_counter() - t_start
+            sst = srv.stats()
         lat_ms = np.array(lat) * 1e3
         row = {"offered_load": load, "p50_ms": float(np.percentile(lat_ms, 50)),
-               "p99_ms": float(np.percentile(lat_ms, 99)), "gcups": done_cells / wall / 1e9}
+               "p99_ms": float(np.percentile(lat_ms, 99)), "gcups": done_cells / wall / 1e9,
+               "server": {k: int(sst[k]) for k in ("batches", "coalesced", "admission_stalls", "max_queue")}}
         row["vs_offline"] = row["gcups"] / out["offline_batched_gcups"]
         if plain:
             row["vs_plain"] = row["gcups"] / out["plain_gcups"]
+        if check:
+            bad = 0
+            for k, r in enumerate(reqs):
+                res, cig = served[k]
+                exp = off_res[first_job[k]:first_job[k + 1]]
+                c0 = int(exp["cigar_off"][0]) if r.n_jobs else 0
+                c1 = int(exp["cigar_off"][-1]) + int(exp["cigar_len"][-1]) if r.n_jobs else 0
+                same = all((res[f] == exp[f]).all() for f in ("score", "second", "read_begin", "read_end",
+                                                              "ref_begin", "ref_end", "second_ref_end",
+                                                              "cigar_len", "flags"))
+                same = same and (res["cigar_off"].astype(np.int64) == exp["cigar_off"].astype(np.int64) - c0).all()
+                if not (same and np.array_equal(cig, off_cig[c0:c1])):
+                    bad += 1
+            row["served_equal_offline"] = {"requests": len(reqs), "jobs": int(allj.n_jobs), "differing_requests": bad}
         out["loads"].append(row)
+    if check:
+        import oracle
+        from oracle.compare import compare
+        rng = np.random.default_rng(2024)
+        idx = np.sort(rng.choice(allj.n_jobs, min(allj.n_jobs, 4000), replace=False))
+        sub = allj.subset(idx)
+        ores, oops = oracle.align(sub)
+        sres = off_res[idx].copy()
+        parts, o = [], 0
+        for k, j in enumerate(idx):
+            L = int(off_res["cigar_len"][j])
+            parts.append(off_cig[int(off_res["cigar_off"][j]):int(off_res["cigar_off"][j]) + L])
+            sres["cigar_off"][k] = o
+            o += L
+        bad = compare(sres, np.concatenate(parts), ores, oops)
+        out["oracle_check"] = {"jobs": len(idx), "windows_past_2^31": int((sub.ref_pos >= 2 ** 31).sum()),
+                               "mismatches": len(bad), "first": bad[:3]}
     return out
 
 
@@ -680,13 +820,13 @@ def run_config(args):
             for mode in (0, 1):
                 for form in (1, 0):
                     rows += device_line(sa, ref, wl, args, "", cigar=(True,), mode=mode, form=form)["rows"]
-        mate = make_workload(0, 1_000_000)
+        mate = make_workload("c2", 0, 1_000_000)
         with sa.Reference(mate.ref) as ref:
             glocal = device_line(sa, ref, mate, args, "", cigar=(True, False), mode=1)["rows"]
         line = {"config": "c1 plain: 10k windows of 400 bp, 100 bp reads (plain and batched forms, both modes)",
                 "jobs": int(wl.n_jobs), "cells": int(wl.cells), "steps": args.steps, "rows": rows,
                 "mate_rescue_glocal": {"jobs": int(mate.n_jobs), "cells": int(mate.cells), "rows": glocal}}
-    elif args.config == "c3":
+    elif args.config == "c3-detail":
         wl = workloads.uneven(seed=1, n_jobs=args.jobs or 4_000_000)
         with sa.Reference(wl.ref) as ref:
             line = device_line(sa, ref, wl, args, "c3 uneven: 4M jobs, n U[50,250], m U[1.5n,6n]",
@@ -724,7 +864,8 @@ def run_config(args):
         reqs = [workloads.serving_request(ref_acgt, 3, k, int(sizes[k])) for k in range(n_req)]
         with sa.Reference(ref_acgt) as ref:
             line = serving_run(sa, ref, reqs, ppm, (0.5, 0.8, 0.95), slots=args.slots,
-                               genome="3.1 Gbp i.i.d. reference (775 MB packed, device-resident)", plain=True)
+                               genome="3.1 Gbp i.i.d. reference (775 MB packed, device-resident)", plain=True,
+                               check=True)
         line["config"] = "c5 serving: requests of U[1,50000] jobs, n U[50,250], m U[2n,6n]"
     line["data"] = "synthetic"
     print(json.dumps(line), flush=True)
@@ -742,7 +883,7 @@ def main():
         if rank == 0:
             probe_all_ops()
         return
-    if args.config != "c2":
+    if args.config not in WORKLOADS:
         if rank == 0:
             run_config(args)
         return

@@ -99,7 +99,10 @@ typedef struct {
     int32_t min_score;     /* results below it get SA_RES_BELOW_MIN and no traceback; INT32_MIN disables */
     int32_t form;          /* sa_form */
     int32_t profile;       /* nonzero: time each phase with CUDA events (sa_last_stats) */
-    int32_t _reserved[2];
+    int32_t arena_mb;      /* cap on the traceback's rectangle direction arena in MiB (0: 60 % of
+                              free device memory); a batch whose rectangles exceed it runs their
+                              direction pass in waves (sa_stats.waves); results never depend on it */
+    int32_t _reserved;
 } sa_params;
 
 typedef struct {           /* 32 bytes */

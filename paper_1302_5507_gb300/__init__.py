@@ -45,7 +45,7 @@ class sa_scoring(ctypes.Structure):
 class sa_params(ctypes.Structure):
     _fields_ = [("sc", sa_scoring), ("mode", ctypes.c_int32), ("want_cigar", ctypes.c_int32),
                 ("width", ctypes.c_int32), ("min_score", ctypes.c_int32), ("form", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("_reserved", ctypes.c_int32 * 2)]
+                ("profile", ctypes.c_int32), ("arena_mb", ctypes.c_int32), ("_reserved", ctypes.c_int32)]
 
 
 class sa_stats(ctypes.Structure):
@@ -225,11 +225,12 @@ def sa_server_destroy(s):
 # numpy / torch conveniences
 
 def make_params(scoring=(1, 2, 2, 1), mode=SA_LOCAL, want_cigar=True, width=0,
-                min_score=SA_NO_SCORE, form=SA_FORM_BATCHED, profile=False) -> sa_params:
+                min_score=SA_NO_SCORE, form=SA_FORM_BATCHED, profile=False, arena_mb=0) -> sa_params:
     p = sa_default_params()
     p.sc.match, p.sc.mismatch, p.sc.gap_open, p.sc.gap_extend = scoring
     p.mode, p.want_cigar, p.width = mode, int(bool(want_cigar)), width
     p.min_score, p.form, p.profile = min_score, form, int(bool(profile))
+    p.arena_mb = arena_mb
     return p
 
 

@@ -20,6 +20,7 @@
 
 #include <nvtx3/nvToolsExt.h>
 
+#include "admission.h"
 #include "kernels.h"
 
 using namespace sa;
@@ -117,11 +118,28 @@ struct Workspace {
     bool side_ok = false;
     cudaEvent_t ev[16] = {};
     bool ev_ok = false;
+    DevBuf* all_[24] = {};
+    DevBuf* const* bufs(size_t* n) {
+        all_[0] = &jobs; all_[1] = &reads; all_[2] = &out; all_[3] = &cigar; all_[4] = &key;
+        all_[5] = &order; all_[6] = &rpack; all_[7] = &state; all_[8] = &rect; all_[9] = &tb;
+        all_[10] = &count; all_[11] = &coff; all_[12] = &sizes; all_[13] = &offs; all_[14] = &bsum;
+        all_[15] = &colbest; all_[16] = &lkeys; all_[17] = &tmp_ops; all_[18] = &arena;
+        all_[19] = &plan; all_[20] = &counters; all_[21] = &blists; all_[22] = &band; all_[23] = &ovf;
+        *n = 24;
+        return all_;
+    }
+    // device bytes the workspace holds
+    uint64_t bytes() {
+        size_t n = 0;
+        DevBuf* const* b = bufs(&n);
+        uint64_t t = 0;
+        for (size_t k = 0; k < n; k++) t += b[k]->cap;
+        return t;
+    }
     void release() {
-        DevBuf* all[] = {&jobs, &reads, &out, &cigar, &key, &order, &rpack, &state, &rect, &tb,
-                         &count, &coff, &sizes, &offs, &bsum, &colbest, &lkeys, &tmp_ops, &arena,
-                         &plan, &counters, &blists, &band, &ovf};
-        for (DevBuf* b : all) b->release();
+        size_t n = 0;
+        DevBuf* const* all = bufs(&n);
+        for (size_t k = 0; k < n; k++) all[k]->release();
         if (h_plan) cudaFreeHost(h_plan);
         h_plan = nullptr;
         if (seg_exec) cudaGraphExecDestroy(seg_exec);
@@ -201,6 +219,7 @@ int check_params(const sa_params* p, Score* sc) {
     TRY(sa::check_scoring(p, sc));
     if (p->width != 0 && p->width != 16 && p->width != 32) return fail(SA_EINVAL, "width must be 0, 16 or 32");
     if (p->form != SA_FORM_BATCHED && p->form != SA_FORM_PLAIN) return fail(SA_EINVAL, "unknown form");
+    if (p->arena_mb < 0) return fail(SA_EINVAL, "arena_mb must be >= 0");
     return SA_OK;
 }
 
@@ -699,7 +718,8 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
                                                       dir_words(cfg_L(c), cfg_K(c), (int)max_m));
             size_t free_b = 0, tot_b = 0;
             CU(cudaMemGetInfo(&free_b, &tot_b));
-            const uint64_t avail = (uint64_t)((double)(free_b + ws.arena.cap) * 0.6) / 4;
+            uint64_t avail = (uint64_t)((double)(free_b + ws.arena.cap) * 0.6) / 4;
+            if (P->arena_mb > 0) avail = std::min<uint64_t>(avail, ((uint64_t)P->arena_mb << 20) / 4);
             uint64_t arena_words = total_words ? total_words : 1;
             uint64_t wave_words = 0;   // 0: everything in one wave
             if (arena_words > avail) {
@@ -924,6 +944,7 @@ struct sa_server {
         sa_stats last{};
         cudaStream_t stream = nullptr;
         std::thread th;
+        uint64_t held = 0;             // device bytes its workspace holds (guarded by mu)
     };
     std::vector<std::unique_ptr<Slot>> slots;
 };
@@ -1087,29 +1108,40 @@ void slot_main(sa_server* S, sa_server::Slot* slot) {
         uint64_t est = 0;
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            // FIFO admission: the head request starts when the memory budget allows;
-            // the requests queued behind it join its device batch while they fit
-            bool stalled = false;      // the head request waited for the memory budget
-            S->cv_work.wait(lk, [&] {
-                if (S->stop) return true;
-                if (S->queue.empty()) return false;
-                if (S->in_use + S->queue.front()->est_bytes > S->budget) {
-                    stalled = true;
-                    return false;
+            // FIFO admission (admission.h): the head request starts when the memory
+            // it needs fits; the requests queued behind it join its device batch
+            // while they fit.  The memory is re-read for every decision, and a head
+            // request that does not fit looks again every few milliseconds (device
+            // memory can come free outside the server, with no notification).
+            bool stalled = false;      // the head request waited for memory
+            size_t take = 0;
+            auto view = [](const std::shared_ptr<Request>& q) {
+                return std::make_pair((uint64_t)q->jobs.size(), q->est_bytes);
+            };
+            for (;;) {
+                if (S->stop) return;
+                if (S->queue.empty()) {
+                    S->cv_work.wait(lk);
+                    continue;
                 }
-                return true;
-            });
-            if (S->stop) return;
+                size_t fr = 0, tot = 0;
+                if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+                    cudaGetLastError();
+                    fr = 0;
+                }
+                uint64_t held = 0;
+                for (auto& sl : S->slots) held += sl->held;
+                const uint64_t cap = admission_cap(S->budget, (uint64_t)fr, held);
+                take = admit_front(S->queue, view, S->in_use, cap, kCoalesceJobs, &est);
+                if (take) break;
+                stalled = true;
+                S->cv_work.wait_for(lk, std::chrono::milliseconds(2));
+            }
             if (stalled) S->counters.admission_stalls++;
             uint64_t nj = 0;
-            while (!S->queue.empty()) {
-                const auto& q = S->queue.front();
-                if (!batch.empty() && (nj + q->jobs.size() > kCoalesceJobs ||
-                                       S->in_use + est + q->est_bytes > S->budget))
-                    break;
-                nj += q->jobs.size();
-                est += q->est_bytes;
-                batch.push_back(q);
+            for (size_t k = 0; k < take; k++) {
+                nj += S->queue.front()->jobs.size();
+                batch.push_back(S->queue.front());
                 S->queue.pop_front();
             }
             S->in_use += est;
@@ -1137,9 +1169,11 @@ void slot_main(sa_server* S, sa_server::Slot* slot) {
                 msgs[k] = rcs[k] == SA_OK ? std::string() : std::string(g_err);
             }
         }
+        const uint64_t held_now = slot->ws.bytes();
         {
             std::lock_guard<std::mutex> lk(S->mu);
             S->in_use -= est;
+            slot->held = held_now;
             for (size_t k = 0; k < batch.size(); k++) {
                 Request& rq = *batch[k];
                 rq.err = msgs[k];

@@ -24,10 +24,10 @@ def sa():
 
 
 def run_pair(sa, ref, wl, *, scoring=(1, 2, 2, 1), mode=0, form=0, width=0, want_cigar=True,
-             min_score=oracle.NO_SCORE):
+             min_score=oracle.NO_SCORE, arena_mb=0):
     jobs = sa.jobs_array(wl.read_off, wl.read_len, wl.flags, wl.ref_pos, wl.win_len)
     p = sa.make_params(scoring=scoring, mode=mode, form=form, width=width, want_cigar=want_cigar,
-                       min_score=min_score)
+                       min_score=min_score, arena_mb=arena_mb)
     res, cig = ref.align(jobs, wl.reads, p)
     ores, oops = oracle.align(wl, scoring=scoring, mode=mode, want_cigar=want_cigar,
                               min_score=min_score)
@@ -265,6 +265,55 @@ def test_full_size_uneven_sampled(sa):
     idx = np.sort(rng.choice(wl.n_jobs, 3000, replace=False))
     bad = _sampled_compare(wl, res, cig, idx)
     assert not bad, "\n".join(bad)
+
+
+def test_full_size_low_similarity_sampled(sa):
+    """The low-similarity workload at its full size (500k jobs of 250 bp against
+    1,000 bp windows, divergence 0-40 %) in one device call, with and without a
+    traceback (most jobs take the wavefront rectangle pass); a seeded sample of
+    jobs is recomputed by the oracle one by one."""
+    import torch
+    wl = workloads.lowsim(seed=1)
+    jobs = sa.jobs_array(wl.read_off, wl.read_len, wl.flags, wl.ref_pos, wl.win_len)
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(555)
+    idx = np.sort(rng.choice(wl.n_jobs, 3000, replace=False))
+    with sa.Reference(wl.ref) as ref:
+        d_jobs = torch.from_numpy(jobs.view(np.uint8)).to(dev)
+        d_reads = torch.from_numpy(wl.reads).to(dev)
+        d_out = torch.empty(len(jobs) * 56, dtype=torch.uint8, device=dev)
+        d_cig = torch.empty(sa.cigar_max_ops(wl.read_len), dtype=torch.int32, device=dev)
+        used = ref.align_dev(d_jobs, d_reads, d_out, d_cig, sa.make_params())
+        torch.cuda.synchronize()
+        st = ref.stats()
+        assert st["rect_jobs"] > wl.n_jobs // 2 and st["band_jobs"] > 0 and st["diag_jobs"] > 0, st
+        res = d_out.cpu().numpy().view(sa.RESULT_DTYPE).copy()
+        cig = d_cig[:used].cpu().numpy().view(np.uint32).copy()
+        ref.align_dev(d_jobs, d_reads, d_out, None, sa.make_params(want_cigar=False))
+        torch.cuda.synchronize()
+        res_score = d_out.cpu().numpy().view(sa.RESULT_DTYPE).copy()
+    bad = _sampled_compare(wl, res, cig, idx)
+    assert not bad, "\n".join(bad)
+    ores, _ = oracle.align(wl.subset(idx), want_cigar=False)
+    bad = compare(res_score[idx], None, ores, None)
+    assert not bad, "\n".join(bad)
+
+
+def test_direction_arena_in_waves(sa):
+    """A direction arena capped far below the batch's rectangles (arena_mb) makes
+    the rectangle direction pass and its walks run in several waves; the results
+    stay identical to the oracle's, and to the single-wave run."""
+    wl = workloads.lowsim(seed=4, n_jobs=3_000)
+    with sa.Reference(wl.ref) as ref:
+        jobs = sa.jobs_array(wl.read_off, wl.read_len, wl.flags, wl.ref_pos, wl.win_len)
+        one, one_cig = ref.align(jobs, wl.reads)
+        assert ref.stats()["waves"] == 1
+        for mode in (0, 1):
+            res, ores = assert_parity(sa, ref, wl, mode=mode, arena_mb=16)
+            st = ref.stats()
+            assert st["waves"] >= (3 if mode == 0 else 2) and st["rect_jobs"] > 500, st
+        res, cig = ref.align(jobs, wl.reads, sa.make_params(arena_mb=16))
+        assert (res == one).all() and np.array_equal(cig, one_cig)
 
 
 def test_full_size_pairs_sampled(sa):

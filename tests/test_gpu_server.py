@@ -118,3 +118,40 @@ def test_serving_shaped_requests_and_poll_timeout(sa):
             ores, oops = oracle.align(r)
             bad = compare(res, cig, ores, oops)
             assert not bad, "\n".join(bad[:10])
+
+
+def test_full_size_serving_reference(sa):
+    """The serving configuration's own reference: 3.1 Gbp, 2-bit packed and
+    device-resident (775 MB), so window starts pass 2^31 and the packed word
+    index passes 2^27.  Serving-shaped requests (n U[50,250], m U[2n,6n]) run
+    through sa_align_batch as one batch and through a server as separate
+    requests; every job of both is compared with the oracle."""
+    genome = workloads.serving_reference(seed=1)
+    reqs = [workloads.serving_request(genome, 3, k, n) for k, n in enumerate((2500, 1, 1800, 2700))]
+    allj = workloads.Workload(
+        "serving", genome, np.concatenate([r.reads for r in reqs]),
+        np.concatenate([r.read_off + np.uint64(o) for r, o in
+                        zip(reqs, np.cumsum([0] + [r.reads.size for r in reqs[:-1]]))]),
+        np.concatenate([r.read_len for r in reqs]), np.concatenate([r.flags for r in reqs]),
+        np.concatenate([r.ref_pos for r in reqs]), np.concatenate([r.win_len for r in reqs]),
+        np.concatenate([r.truth for r in reqs]))
+    assert (allj.ref_pos.astype(np.int64) >= 2 ** 31).sum() > 1000
+    assert int(allj.ref_pos.max()) + int(allj.win_len.max()) > 3_000_000_000
+    ores, oops = oracle.align(allj)
+    with sa.Reference(genome) as ref:
+        assert len(ref) == 3_100_000_000
+        res, cig = ref.align(sa.jobs_array(allj.read_off, allj.read_len, allj.flags, allj.ref_pos,
+                                           allj.win_len), allj.reads)
+        bad = compare(res, cig, ores, oops)
+        assert not bad, "\n".join(bad[:10])
+        with sa.Server(ref, max_inflight=2) as srv:
+            tickets = [srv.submit(sa.jobs_array(r.read_off, r.read_len, r.flags, r.ref_pos, r.win_len),
+                                  r.reads) for r in reqs]
+            first = 0
+            for r, tk in zip(reqs, tickets):
+                rc, res, cig = srv.poll(tk, r.n_jobs, sa.cigar_max_ops(r.read_len))
+                assert rc == sa.SA_OK
+                sl = slice(first, first + r.n_jobs)
+                bad = compare(res, cig, ores[sl], oops[sl])
+                assert not bad, "\n".join(bad[:10])
+                first += r.n_jobs

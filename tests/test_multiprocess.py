@@ -22,7 +22,7 @@ def _rank_main(rank, world, port, out):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         import bench
-        wl = bench.make_workload(rank, 300, genome_len=2_000_000)
+        wl = bench.make_workload("c3", rank, 300, genome_len=2_000_000)
         # each rank's own (fake) timed region; the reported one is the slowest
         ms = bench.max_over_ranks(10.0 + 5.0 * rank, dist, "cpu")
         out[rank] = (wl.truth.copy(), int(wl.cells), ms)
