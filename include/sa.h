@@ -357,6 +357,76 @@ int sa_select(sa_reference* ref, const sa_select_params* sp, const sa_job* jobs,
               const sa_result* results, const uint32_t* read_first, uint32_t n_reads,
               sa_read_result* out);
 
+/* ---------------------------------------------------------------------------
+ * Seeding front end: candidate windows of whole reads (the paper's step 3:
+ * Methods, "Implementation details of SOAP3-dp", and "Effort limit for
+ * dynamic programming").  Seeds -- substrings of fixed length -- are taken at
+ * regular intervals along each read and along its reverse complement and
+ * matched exactly against the reference with an FM index on the device; the
+ * regions their hits point to become candidate windows, each with its number
+ * of supporting seeds, in the layout sa_effort_limit[_dev] takes.
+ *
+ * Definitions (the paper leaves these values to its supplementary material):
+ *  - seeds of a read of length n, per strand (the read, then its reverse
+ *    complement): offsets 0, seed_step, 2*seed_step, ... while offset +
+ *    seed_len <= n; a seed occurring more than max_occ times is repetitive
+ *    and contributes nothing;
+ *  - a hit of the seed at offset o on reference position p implies the
+ *    strand's sequence starts at d = p - o (its diagonal); a read strand's hits
+ *    sorted by diagonal form one region while neighbouring diagonals differ by
+ *    at most `join`;
+ *  - a region's window is [max(0, d_min - pad), min(L, d_max + n + pad)), at
+ *    most SA_MAX_WINDOW long; its support is the number of distinct seeds with
+ *    a hit in it;
+ *  - a read's candidates are its forward regions by d_min, then its
+ *    reverse-complement regions (job flag SA_RC) by d_min.
+ */
+typedef struct {
+    uint32_t seed_len;     /* 12..32 */
+    uint32_t seed_step;    /* >= 1; at most 128 seeds per strand */
+    uint32_t max_occ;      /* >= 1; seeds per strand x max_occ <= 8192 */
+    uint32_t pad;          /* <= 65536 */
+    uint32_t join;         /* <= 65536 */
+    uint32_t _reserved;
+} sa_seed_params;
+
+typedef struct sa_seed_index sa_seed_index;
+
+/* Defaults: seed_len 20, seed_step 10, max_occ 256, pad 24, join 16. */
+void sa_default_seed_params(sa_seed_params* p);
+
+/* Build the seed index of a reference (its packed bases are read back from the
+ * device): the suffix order of the reference, its BWT in 64-byte chunks (the
+ * counts of A, C, G, T before the chunk and 192 two-bit BWT entries, so one
+ * backward-search step reads one chunk per interval end), the row interval of
+ * every 12-base pattern, and the full suffix array (4 bytes a row) on the
+ * reference's device.  Built on the host with all cores, once per reference;
+ * about 12 bytes a base of host memory while it runs.  References of up to
+ * 2^32 - 33 bases (SA_EINVAL beyond).  The reference must outlive the index. */
+int sa_seed_index_create(sa_reference* ref, sa_seed_index** out);
+int sa_seed_index_destroy(sa_seed_index* idx);
+/* Reference length and device bytes the index holds (either pointer may be NULL). */
+int sa_seed_index_info(const sa_seed_index* idx, uint64_t* ref_len, uint64_t* device_bytes);
+
+/* Candidate windows of n_reads reads: read r is reads[read_off[r] ..
+ * read_off[r] + read_len[r]) (ASCII A/C/G/T, 1..SA_MAX_READ bases; anything
+ * else is SA_EINVAL).  Writes the candidates as jobs (read_off, read_len of the
+ * read; flags 0 or SA_RC; ref_pos, win_len of the window) to cand and their
+ * support to support (capacity cand_cap each), read r's candidates being
+ * read_first[r] .. read_first[r+1]-1 (n_reads + 1 entries).  *n_cand (host)
+ * receives the number of candidates; if it exceeds cand_cap the call returns
+ * SA_EOVERFLOW and writes no candidate.  Device buffers; runs on cuda_stream
+ * (NULL: the reference's stream) and returns when done.  Calls on one index
+ * are serialised. */
+int sa_seed_candidates_dev(sa_seed_index* idx, const sa_seed_params* params, const char* d_reads,
+                           uint64_t reads_len, const uint64_t* d_read_off, const uint32_t* d_read_len,
+                           uint32_t n_reads, sa_job* d_cand, uint32_t* d_support, uint32_t* d_read_first,
+                           uint64_t cand_cap, uint64_t* n_cand, void* cuda_stream);
+/* The same with host buffers. */
+int sa_seed_candidates(sa_seed_index* idx, const sa_seed_params* params, const char* reads, uint64_t reads_len,
+                       const uint64_t* read_off, const uint32_t* read_len, uint32_t n_reads, sa_job* cand,
+                       uint32_t* support, uint32_t* read_first, uint64_t cand_cap, uint64_t* n_cand);
+
 #ifdef __cplusplus
 }
 #endif

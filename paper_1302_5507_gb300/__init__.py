@@ -71,6 +71,10 @@ class sa_server_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class sa_seed_params(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint32) for k in ("seed_len", "seed_step", "max_occ", "pad", "join", "_reserved")]
+
+
 class sa_select_params(ctypes.Structure):
     _fields_ = [("sc", sa_scoring), ("paired", ctypes.c_int32), ("orientation", ctypes.c_int32),
                 ("frag_min", ctypes.c_int64), ("frag_max", ctypes.c_int64)]
@@ -123,13 +127,23 @@ def lib():
         L.sa_effort_limit.argtypes = [_VP, _VP, _VP, _VP, _U32, _U32, _VP, _VP, _VP, ctypes.POINTER(_U32)]
         L.sa_select_dev.argtypes = [_VP, ctypes.POINTER(sa_select_params), _VP, _VP, _VP, _U32, _VP, _VP]
         L.sa_select.argtypes = [_VP, ctypes.POINTER(sa_select_params), _VP, _VP, _VP, _U32, _VP]
+        L.sa_default_seed_params.argtypes = [ctypes.POINTER(sa_seed_params)]
+        L.sa_default_seed_params.restype = None
+        L.sa_seed_index_create.argtypes = [_VP, ctypes.POINTER(_VP)]
+        L.sa_seed_index_destroy.argtypes = [_VP]
+        L.sa_seed_index_info.argtypes = [_VP, ctypes.POINTER(_U64), ctypes.POINTER(_U64)]
+        L.sa_seed_candidates_dev.argtypes = [_VP, ctypes.POINTER(sa_seed_params), _VP, _U64, _VP, _VP, _U32,
+                                             _VP, _VP, _VP, _U64, ctypes.POINTER(_U64), _VP]
+        L.sa_seed_candidates.argtypes = [_VP, ctypes.POINTER(sa_seed_params), _VP, _U64, _VP, _VP, _U32,
+                                         _VP, _VP, _VP, _U64, ctypes.POINTER(_U64)]
         L.sa_last_error.restype = ctypes.c_char_p
         for name in ("sa_create_reference", "sa_destroy_reference", "sa_align_batch",
                      "sa_align_batch_dev", "sa_align_batch_noalloc", "sa_last_stats",
                      "sa_server_create", "sa_submit",
                      "sa_poll", "sa_server_destroy", "sa_tune", "sa_plan_get", "sa_plan_set",
                      "sa_effort_limit_dev", "sa_effort_limit", "sa_select_dev", "sa_select",
-                     "sa_server_get_stats"):
+                     "sa_server_get_stats", "sa_seed_index_create", "sa_seed_index_destroy",
+                     "sa_seed_index_info", "sa_seed_candidates_dev", "sa_seed_candidates"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -425,6 +439,84 @@ class Reference:
         return sa_select_dev(self.h, params, ctypes.c_void_p(jobs.data_ptr()), ctypes.c_void_p(results.data_ptr()),
                              ctypes.c_void_p(read_first.data_ptr()), read_first.numel() - 1,
                              ctypes.c_void_p(out.data_ptr()), st)
+
+
+def make_seed_params(seed_len=20, seed_step=10, max_occ=256, pad=24, join=16) -> sa_seed_params:
+    p = sa_seed_params()
+    lib().sa_default_seed_params(ctypes.byref(p))
+    p.seed_len, p.seed_step, p.max_occ, p.pad, p.join = seed_len, seed_step, max_occ, pad, join
+    return p
+
+
+class SeedIndex:
+    """Seeding front end of a reference (sa_seed_index_create / sa_seed_candidates*)."""
+
+    def __init__(self, ref: "Reference"):
+        self.ref = ref
+        h = _VP()
+        _check(lib().sa_seed_index_create(ref.h, ctypes.byref(h)))
+        self.h = h
+
+    def info(self) -> dict:
+        L, b = _U64(0), _U64(0)
+        _check(lib().sa_seed_index_info(self.h, ctypes.byref(L), ctypes.byref(b)))
+        return {"ref_len": L.value, "device_bytes": b.value}
+
+    def candidates(self, reads: np.ndarray, read_off: np.ndarray, read_len: np.ndarray,
+                   params: sa_seed_params | None = None, cap: int | None = None):
+        """Host buffers: (candidate jobs, support, read_first)."""
+        params = params or make_seed_params()
+        reads = np.ascontiguousarray(reads, np.uint8)
+        off = np.ascontiguousarray(read_off, np.uint64)
+        ln = np.ascontiguousarray(read_len, np.uint32)
+        n_reads = len(ln)
+        first = np.zeros(n_reads + 1, np.uint32)
+        n = _U64(0)
+        if cap is None:
+            # size by a first call that only counts
+            rc = lib().sa_seed_candidates(self.h, ctypes.byref(params), _ptr(reads), reads.size, _ptr(off),
+                                          _ptr(ln), n_reads, None, None, _ptr(first), 0, ctypes.byref(n))
+            if rc not in (SA_OK, SA_EOVERFLOW):
+                _check(rc)
+            cap = n.value
+        jobs = np.zeros(max(1, cap), JOB_DTYPE)
+        sup = np.zeros(max(1, cap), np.uint32)
+        _check(lib().sa_seed_candidates(self.h, ctypes.byref(params), _ptr(reads), reads.size, _ptr(off),
+                                        _ptr(ln), n_reads, _ptr(jobs), _ptr(sup), _ptr(first), cap,
+                                        ctypes.byref(n)))
+        return jobs[:n.value], sup[:n.value], first
+
+    def candidates_dev(self, reads, read_off, read_len, cand, support, read_first,
+                       params: sa_seed_params | None = None, stream=None) -> int:
+        """Device tensors (torch); returns the number of candidates (SAError
+        SA_EOVERFLOW when they do not fit `cand`)."""
+        params = params or make_seed_params()
+        st = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+        n = _U64(0)
+        _check(lib().sa_seed_candidates_dev(self.h, ctypes.byref(params), ctypes.c_void_p(reads.data_ptr()),
+                                            reads.numel(), ctypes.c_void_p(read_off.data_ptr()),
+                                            ctypes.c_void_p(read_len.data_ptr()), read_len.numel(),
+                                            ctypes.c_void_p(cand.data_ptr()), ctypes.c_void_p(support.data_ptr()),
+                                            ctypes.c_void_p(read_first.data_ptr()), cand.numel() // 32,
+                                            ctypes.byref(n), st))
+        return n.value
+
+    def close(self):
+        if self.h:
+            lib().sa_seed_index_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

@@ -40,7 +40,7 @@ def _nvcc() -> str:
 def _units():
     units = [(os.path.join(CSRC, "fill_cfg.cu"), f"fill_cfg{c}.o", [f"-DSA_CFG={c}"])
              for c in range(NUM_CFG)]
-    for name in ("fill_dispatch.cu", "stage.cu", "band.cu", "api.cu", "noalloc.cu", "select.cu"):
+    for name in ("fill_dispatch.cu", "stage.cu", "band.cu", "api.cu", "noalloc.cu", "select.cu", "seed.cu"):
         units.append((os.path.join(CSRC, name), name.replace(".cu", ".o"), []))
     return units
 

@@ -69,3 +69,20 @@ def test_read_level_layouts_and_null_handles(libsa):
     assert L.sa_effort_limit(None, None, None, None, 0, 30, None, None, None, ctypes.byref(n)) == sa.SA_EINVAL
     assert L.sa_server_get_stats(None, None) == sa.SA_EINVAL
     assert "NULL" in sa.sa_last_error()
+
+
+def test_seeding_layouts_and_null_handles(libsa):
+    import paper_1302_5507_gb300 as sa
+    assert ctypes.sizeof(sa.sa_seed_params) == 6 * 4
+    p = sa.make_seed_params()
+    assert (p.seed_len, p.seed_step, p.max_occ, p.pad, p.join) == (20, 10, 256, 24, 16)
+    L = sa.lib()
+    n = ctypes.c_uint64(7)
+    assert L.sa_seed_index_create(None, None) == sa.SA_EINVAL
+    assert L.sa_seed_index_destroy(None) == sa.SA_EINVAL
+    assert L.sa_seed_index_info(None, None, None) == sa.SA_EINVAL
+    assert L.sa_seed_candidates_dev(None, ctypes.byref(p), None, 0, None, None, 0, None, None, None, 0,
+                                    ctypes.byref(n), None) == sa.SA_EINVAL
+    assert L.sa_seed_candidates(None, ctypes.byref(p), None, 0, None, None, 0, None, None, None, 0,
+                                ctypes.byref(n)) == sa.SA_EINVAL
+    assert "NULL" in sa.sa_last_error()
