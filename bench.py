@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--probe-ops", action="store_true",
                     help="print the measured issue rate (lane-ops per SM per clock) of every "
                          "operation of the throughput probe and exit")
-    ap.add_argument("--config", default="c3", choices=["c1", "c2", "c3", "c3-detail", "c4", "c5", "pairs"],
+    ap.add_argument("--config", default="c3", choices=["c1", "c2", "c3", "c3-detail", "c4", "c5", "pairs", "seeds"],
                     help="c3 (default): the headline line on the uneven 4M-job batch; c2: the same "
                          "line on the mate-rescue batch; c1 plain windows (plain and batched forms, "
                          "both modes) plus mate rescue in GLOCAL; c3-detail: the uneven batch per "
@@ -784,6 +784,121 @@ def pairs_line(sa, ref, w, args, ceiling=30, frag=(300, 700), min_score=None):
             "mapq_hist": {str(q): int((out["mapq"] == q).sum()) for q in (0, 20, 40, 60)}}
 
 
+def seeds_line(sa, args, ceiling=30, frag=(300, 700)):
+    """Paired reads from sequence to placement on the device: seeds and candidate
+    windows (sa_seed_candidates_dev), effort limit, alignment with CIGAR, paired
+    selection.  One step = the four calls on the whole batch, timed with CUDA
+    events on the library's stream; the index is built once, before."""
+    import torch
+    import workloads
+    n_pairs = args.jobs or 100_000
+    w = workloads.pairs(seed=1, n_pairs=n_pairs)
+    first = w.read_first.astype(np.int64)
+    off = w.read_off[first[:-1]].astype(np.uint64)
+    ln = w.read_len[first[:-1]].astype(np.uint32)
+    n_reads = len(ln)
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.current_stream()
+    out = {"config": f"seeds: {n_pairs} read pairs (150 bp, insert N(500,50)) on the 100 Mbp genome with "
+                     f"planted segmental duplicates; seeds of 20 bases every 10 on both strands, max_occ 256, "
+                     f"pad 24, join 16; effort limit {ceiling}; FR fragment {frag[0]}-{frag[1]}",
+           "reads": n_reads}
+    with sa.Reference(w.ref) as ref:
+        t0 = time.perf_counter()
+        idx = sa.SeedIndex(ref)
+        out["index_build_s"] = time.perf_counter() - t0
+        out["index_device_bytes"] = idx.info()["device_bytes"]
+        dr = torch.from_numpy(w.reads).to(dev)
+        doff = torch.from_numpy(off.view(np.int64)).to(dev)
+        dln = torch.from_numpy(ln.view(np.int32)).to(dev)
+        cap = 64 * n_reads
+        dc = torch.empty(cap * 32, dtype=torch.uint8, device=dev)
+        ds = torch.empty(cap, dtype=torch.int32, device=dev)
+        df = torch.empty(n_reads + 1, dtype=torch.int32, device=dev)
+        dk = torch.empty(cap * 32, dtype=torch.uint8, device=dev)
+        dfrom = torch.empty(cap, dtype=torch.int32, device=dev)
+        dkf = torch.empty(n_reads + 1, dtype=torch.int32, device=dev)
+        dres = torch.empty(cap * 56, dtype=torch.uint8, device=dev)
+        dcig = torch.empty(sa.cigar_max_ops(ln) * ceiling, dtype=torch.int32, device=dev)
+        dout = torch.empty(n_reads * 32, dtype=torch.uint8, device=dev)
+        params = sa.make_params()
+        selp = sa.make_select_params(paired=True, frag_min=frag[0], frag_max=frag[1])
+
+        def step(ev=None):
+            if ev: ev[0].record(st)
+            nc = idx.candidates_dev(dr, doff, dln, dc, ds, df, stream=st)
+            if ev: ev[1].record(st)
+            nk = ref.effort_limit_dev(dc[: nc * 32], ds[:nc], df, ceiling, dk, dfrom, dkf, stream=st)
+            if ev: ev[2].record(st)
+            ref.align_dev(dk[: nk * 32], dr, dres[: nk * 56], dcig, params, stream=st)
+            if ev: ev[3].record(st)
+            ref.select_dev(dk[: nk * 32], dres[: nk * 56], dkf, dout, selp, stream=st)
+            if ev: ev[4].record(st)
+            return nc, nk
+        for _ in range(max(3, args.warmup)):
+            nc, nk = step()
+        torch.cuda.synchronize()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+        for k in range(args.steps):
+            step(evs[k])
+        torch.cuda.synchronize()
+        ms = float(np.mean([e[0].elapsed_time(e[4]) for e in evs]))
+        ph = {name: float(np.mean([e[i].elapsed_time(e[i + 1]) for e in evs]))
+              for i, name in enumerate(("ms_seed_candidates", "ms_effort_limit", "ms_align", "ms_select"))}
+        kept = dk[: nk * 32].cpu().numpy().view(sa.JOB_DTYPE)
+        cells = int(np.dot(kept["read_len"].astype(np.int64), kept["win_len"].astype(np.int64)))
+        got = dout.cpu().numpy().view(sa.READ_RESULT_DTYPE)
+        # reads that come out near the position they were drawn from
+        jobs_np = kept
+        chosen = np.minimum(got["job"], max(nk - 1, 0))
+        near = np.abs(jobs_np["ref_pos"][chosen].astype(np.int64) - w.read_truth.astype(np.int64)) < 200
+        near &= got["job"] != sa.SA_NO_JOB
+        idx.close()
+    seeds_per_strand = (150 - 20) // 10 + 1
+    n_seeds = n_reads * 2 * seeds_per_strand
+    out.update({"steps": args.steps, "ms_per_step": ms, "reads_per_s": n_reads / (ms / 1e3),
+                "gcups": cells / (ms / 1e3) / 1e9, "candidates": int(nc), "kept": int(nk), "cells": cells,
+                "seeds": n_seeds, "seeds_per_s": n_seeds / (ph["ms_seed_candidates"] / 1e3),
+                "phases_ms": ph,
+                "proper_fraction": float((got["flags"] & sa.SA_READ_PROPER > 0).mean()),
+                "placed_at_source_fraction": float(near.mean()),
+                "timing": "CUDA events on the library's stream around each call (the seeding call includes "
+                          "its three host synchronisations: validation, hit total, candidate total)"})
+    return out
+
+
+def seeds_cpu_baseline(n_pairs_sample=1000, ceiling=30, frag=(300, 700)):
+    """The oracle's chain (seeding, effort limit, alignment, paired selection) on
+    the first pairs of the same workload; the lambda-mer table is built first
+    and not timed (as the device index is built before the timed steps)."""
+    import oracle
+    import workloads
+    from oracle import seed as OS
+    from oracle import select as S
+    w = workloads.pairs(seed=1, n_pairs=100_000)
+    first = w.read_first.astype(np.int64)
+    off = w.read_off[first[:-1]].astype(np.uint64)[: 2 * n_pairs_sample]
+    ln = w.read_len[first[:-1]].astype(np.uint32)[: 2 * n_pairs_sample]
+    t0 = time.perf_counter()
+    table = OS.KmerTable(w.ref, 20)
+    build_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    cand, cf = OS.seed_candidates(w.ref, w.reads, off, ln, table=table, lam=20, step=10, max_occ=256, pad=24,
+                                  join=16)
+    t_seed = time.perf_counter() - t0
+    kept, kf = S.effort_limit(cand["support"].astype(np.int64), cf.astype(np.int64), ceiling)
+    sub = workloads.Workload("seeded", w.ref, w.reads, cand["read_off"][kept], cand["read_len"][kept],
+                             cand["flags"][kept], cand["ref_pos"][kept], cand["win_len"][kept],
+                             cand["ref_pos"][kept])
+    res, _ = oracle.align(sub)
+    S.select(sub.flags, sub.read_len, res, kf, paired=True, frag_min=frag[0], frag_max=frag[1])
+    dt = time.perf_counter() - t0
+    return {"value": len(ln) / dt, "unit": "reads/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"first {n_pairs_sample} pairs ({len(ln)} reads, {sub.n_jobs} kept candidates, "
+                      f"{dt:.1f} s, of which seeding {t_seed:.1f} s); lambda-mer table built first in "
+                      f"{build_s:.1f} s (not timed)"}
+
+
 def pairs_cpu_baseline(w, ceiling=30, frag=(300, 700), budget_s=10.0):
     """The oracle's effort limit, alignment and paired selection on the first pairs
     (bounded sample), GCUPS over the kept cells."""
@@ -852,6 +967,10 @@ def run_config(args):
                           f"as unaligned)", "rows": rows}
         if not args.no_cpu:
             line["cpu_baseline"] = pairs_cpu_baseline(w)
+    elif args.config == "seeds":
+        line = seeds_line(sa, args)
+        if not args.no_cpu:
+            line["cpu_baseline"] = seeds_cpu_baseline()
     elif args.config == "c4":
         wl = workloads.lowsim(seed=1, n_jobs=args.jobs or 500_000)
         with sa.Reference(wl.ref) as ref:

@@ -445,6 +445,17 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
         max_grid = std::max(max_grid, grid_for(c, w16[c] ? kFillScore16 : kFillScore));
     }
     const bool fork_buckets = !plain && !trace.on && n_buckets > 1 && blocks_sum <= 2ull * max_grid;
+    // Large batches run the buckets' score passes in turn on two alternating
+    // streams, each with its own scratch range: a persistent launch's blocks leave
+    // the SMs one by one as its work runs out, and the next bucket's launch on the
+    // other stream takes them, so one bucket's tail overlaps the next one's start.
+    const bool pipe_buckets = !plain && !trace.on && !fork_buckets && n_buckets > 1;
+    int bucket_lane[kNumCfg] = {};
+    {
+        int k = 0;
+        for (int c = 0; c < kNumCfg; c++)
+            if (cfg_count[c]) bucket_lane[c] = pipe_buckets ? (k++ & 1) : 0;
+    }
     for (int c = 0; c < kNumCfg; c++) {
         if (plain ? c != plain_cfg : !cfg_count[c]) continue;
         const uint32_t G = 32 / cfg_L(c);
@@ -468,9 +479,18 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
         max_groups = std::max(max_groups, blocks * (kBlock / 32) * (int)G);
     }
     groups_total = std::max<uint64_t>(groups_total, (uint64_t)max_groups);
+    if (pipe_buckets) {
+        // lane 1's ranges follow lane 0's
+        for (int c = 0; c < kNumCfg; c++) {
+            cb_group0[c] = bucket_lane[c] ? (uint64_t)max_groups : 0;
+            lk_warp0[c] = bucket_lane[c] ? warps16_total : 0;
+        }
+        groups_total = 2 * (uint64_t)max_groups;
+        warps16_total *= 2;
+    }
     TRY(ws.colbest.ensure(groups_total * cb_words(max_m) * 4, "column maxima"));
     if (any16) TRY(ws.lkeys.ensure(std::max<uint64_t>(warps16_total, 1) * lane_key_words(max_m) * 4, "lane keys"));
-    if (fork_buckets) TRY(ensure_side(ws));
+    if (fork_buckets || pipe_buckets) TRY(ensure_side(ws));
 
     FillArgs base{};
     base.ref = X.d_words;
@@ -533,7 +553,8 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
         CU(cudaGetLastError());
         trace("order + pack reads");
         tm.mark_at(t1);
-        if (fork_buckets) CU(cudaEventRecord(ws.fork, st));
+        if (fork_buckets || pipe_buckets) CU(cudaEventRecord(ws.fork, st));
+        if (pipe_buckets) CU(cudaStreamWaitEvent(ws.side[0], ws.fork, 0));
         for (int c = 0; c < kNumCfg; c++) {
             if (!cfg_count[c]) continue;
             FillLaunch fl{};
@@ -553,7 +574,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             const uint32_t per_warp = (32 / cfg_L(c)) * (w16[c] ? 2 : 1);
             const uint64_t warps_needed = (cfg_count[c] + per_warp - 1) / per_warp;
             fl.grid = (int)std::min<uint64_t>(grid_for(c, fl.kind), (warps_needed + 3) / 4);
-            fl.stream = fork_buckets ? ws.side[c] : st;
+            fl.stream = fork_buckets ? ws.side[c] : (bucket_lane[c] ? ws.side[0] : st);
             if (fork_buckets) CU(cudaStreamWaitEvent(ws.side[c], ws.fork, 0));
             launch_fill_cfg(c, fl);
             if (fork_buckets) CU(cudaEventRecord(ws.join[c], ws.side[c]));
@@ -562,6 +583,10 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
         if (fork_buckets)
             for (int c = 0; c < kNumCfg; c++)
                 if (cfg_count[c]) CU(cudaStreamWaitEvent(st, ws.join[c], 0));
+        if (pipe_buckets) {
+            CU(cudaEventRecord(ws.join[0], ws.side[0]));
+            CU(cudaStreamWaitEvent(st, ws.join[0], 0));
+        }
         CU(cudaGetLastError());
         if (any16) {
             tm.mark_at(tfill16);
