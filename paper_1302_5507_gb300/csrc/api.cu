@@ -95,6 +95,7 @@ struct PlanBlock {
     uint64_t totals[4];
     uint32_t cls_count[kNumCls];   // jobs per direction-pass class (kCls*)
     uint32_t ovf_count[kNumCfg];   // jobs the 16-bit pass sent to the 32-bit rerun, per bucket
+    uint32_t rect_begin[kNumCfg + 1];  // each bucket's first job in the rectangle-pass list
 };
 
 // Device buffers of one computation at a time (grown on demand, reused).
@@ -662,19 +663,32 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
         if (want_cigar) {
             // --- reduced traceback: banded direction pass for most jobs, the
             // wavefront rectangle pass (in arena waves) for wide bands, then the walk
-            TRY(ws.blists.ensure((size_t)n_jobs * kNumBand * 4, "band lists"));
+            // band lists, then the compacted list of the rectangle pass's jobs
+            TRY(ws.blists.ensure((size_t)n_jobs * (kNumBand + 1) * 4, "band lists"));
             uint32_t* lists[kNumBand];
             for (int k = 0; k < kNumBand; k++) lists[k] = ws.blists.as<uint32_t>() + (size_t)k * n_jobs;
+            uint32_t* rect_list = ws.blists.as<uint32_t>() + (size_t)kNumBand * n_jobs;
             nvtx.next("traceback classes");
+            // the results' count and offset arrays serve as the rectangle flags and
+            // their scan here (the results phase rewrites them)
+            uint32_t* rect_flag = ws.count.as<uint32_t>();
+            uint64_t* rect_pos = ws.coff.as<uint64_t>();
+            // byte heights instead of nibbles (band and rectangle passes) when LOCAL
+            // scores stay below 255
+            const bool heights = mode == SA_LOCAL && (int64_t)sc.a * max_n <= 254;
             launch_rect_plan(d_jobs, ws.order.as<uint32_t>(), n_jobs, dp->cfg_begin, ws.state.as<JobState>(), sc,
                              min_score, 1, ws.rect.as<Rect>(), ws.sizes.as<uint64_t>(), lists,
-                             dp->cls_count, st);
+                             dp->cls_count, rect_flag, heights ? 1 : 0, st);
             launch_scan_u64(ws.sizes.as<uint64_t>(), n_jobs, ws.offs.as<uint64_t>(),
                             ws.bsum.as<uint64_t>(), &dp->totals[0], st);
-            launches += 4;
+            launch_scan_u32(rect_flag, n_jobs, rect_pos, ws.bsum.as<uint64_t>(), &dp->totals[2], st);
+            launch_rect_list(ws.order.as<uint32_t>(), n_jobs, rect_flag, rect_pos, dp->cfg_begin, &dp->totals[2],
+                             rect_list, dp->rect_begin, st);
+            launches += 9;
             CU(cudaGetLastError());
             trace("rect plan + scan");
             CU(cudaMemcpyAsync(&hp->totals[0], &dp->totals[0], 8, cudaMemcpyDeviceToHost, st));
+            CU(cudaMemcpyAsync(hp->rect_begin, dp->rect_begin, sizeof(hp->rect_begin), cudaMemcpyDeviceToHost, st));
             CU(cudaMemcpyAsync(hp->cls_count, dp->cls_count, sizeof(hp->cls_count), cudaMemcpyDeviceToHost, st));
             CU(cudaMemcpyAsync(hp->ovf_count, dp->ovf_count, sizeof(hp->ovf_count), cudaMemcpyDeviceToHost, st));
             TRY(check_bad_read(dp, hp, st));
@@ -688,8 +702,6 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             // band regions: 32 jobs of a class share a region of max_n rows x B/8 words x 32 lanes
             BandLayout bl{};
             uint64_t band_words = 0;
-            // byte heights instead of nibbles when LOCAL scores stay below 255
-            const bool heights = mode == SA_LOCAL && (int64_t)sc.a * max_n <= 254;
             for (int k = 0; k < kNumBand; k++) {
                 bl.warp_stride[k] = (uint64_t)max_n * (band_width_of(k) / (heights ? 4 : 8)) * 32;
                 bl.base[k] = band_words;
@@ -740,7 +752,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             for (int c = 0; c < kNumCfg; c++)
                 if (cfg_count[c])
                     item_max = std::max<uint64_t>(item_max, (uint64_t)(32 / cfg_L(c)) *
-                                                      dir_words(cfg_L(c), cfg_K(c), (int)max_m));
+                                                      rect_words(cfg_L(c), cfg_K(c), (int)max_m, heights));
             size_t free_b = 0, tot_b = 0;
             CU(cudaMemGetInfo(&free_b, &tot_b));
             uint64_t avail = (uint64_t)((double)(free_b + ws.arena.cap) * 0.6) / 4;
@@ -764,20 +776,22 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
                 const bool rect_fork = fork_buckets && total_words;
                 if (rect_fork) CU(cudaEventRecord(ws.fork, st));
                 for (int c = 0; c < kNumCfg && total_words; c++) {
-                    if (!cfg_count[c]) continue;
+                    const uint32_t r0 = hp->rect_begin[c], rn = hp->rect_begin[c + 1] - r0;
+                    if (!rn) continue;           // no job of this bucket needs the rectangle
                     FillLaunch fl{};
                     fl.args = base;
-                    fl.args.pos_begin = cfg_begin[c];
-                    fl.args.pos_count = cfg_count[c];
+                    fl.args.order = rect_list;
+                    fl.args.pos_begin = r0;
+                    fl.args.pos_count = rn;
                     fl.args.item_counter = next_counter();
                     fl.args.arena = ws.arena.as<uint32_t>();
                     fl.args.arena_cap = ws.arena.cap / 4;
                     fl.args.wave = (int)wv;
-                    fl.kind = kFillRect;
+                    fl.kind = heights ? kFillRectH : kFillRect;
                     fl.block = kBlock;
                     const uint32_t G = 32 / cfg_L(c);
-                    const uint64_t warps_needed = (cfg_count[c] + G - 1) / G;
-                    fl.grid = (int)std::min<uint64_t>(grid_for(c, kFillRect), (warps_needed + 3) / 4);
+                    const uint64_t warps_needed = (rn + G - 1) / G;
+                    fl.grid = (int)std::min<uint64_t>(grid_for(c, fl.kind), (warps_needed + 3) / 4);
                     fl.stream = rect_fork ? ws.side[kNumBand + c] : st;
                     if (rect_fork) CU(cudaStreamWaitEvent(fl.stream, ws.fork, 0));
                     launch_fill_cfg(c, fl);
@@ -787,11 +801,14 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
                 }
                 if (rect_fork)
                     for (int c = 0; c < kNumCfg; c++)
-                        if (cfg_count[c]) CU(cudaStreamWaitEvent(st, ws.join[kNumBand + c], 0));
+                        if (hp->rect_begin[c + 1] > hp->rect_begin[c])
+                            CU(cudaStreamWaitEvent(st, ws.join[kNumBand + c], 0));
                 if (wv == 0) trect1 = tm.mark();
+                HeightWalk hwk{heights ? 1 : 0, X.d_words, ws.rpack.as<uint32_t>(), rw, sc};
                 launch_traceback(d_jobs, 0, n_jobs, ws.state.as<JobState>(), ws.rect.as<Rect>(),
                                  ws.arena.as<uint32_t>(), bl, (int)wv, mode, 0, -1, min_score,
-                                 ws.tmp_ops.as<uint32_t>(), tmp_stride, ws.tb.as<TbOut>(), &dp->st.bad_walk, st);
+                                 ws.tmp_ops.as<uint32_t>(), tmp_stride, ws.tb.as<TbOut>(), &dp->st.bad_walk, hwk,
+                                 st);
                 launches++;
                 CU(cudaGetLastError());
                 trace("traceback");
@@ -837,7 +854,8 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             if (want_cigar) {
                 launch_traceback(d_jobs, j0, nb, ws.state.as<JobState>(), ws.rect.as<Rect>(),
                                  ws.arena.as<uint32_t>(), BandLayout{}, 0, mode, 1, c, min_score,
-                                 ws.tmp_ops.as<uint32_t>(), tmp_stride, ws.tb.as<TbOut>(), &dp->st.bad_walk, st);
+                                 ws.tmp_ops.as<uint32_t>(), tmp_stride, ws.tb.as<TbOut>(), &dp->st.bad_walk,
+                                 HeightWalk{}, st);
                 launches++;
             }
             CU(cudaGetLastError());

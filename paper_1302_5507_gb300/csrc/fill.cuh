@@ -20,9 +20,13 @@
 // The score pass and the rectangle direction pass take the match term from a
 // per-lane shared-memory profile; the plain form uses per-lane match masks.
 //
-// Three variants (template flags):
+// Four variants (template flags):
 //   BEST && !DIR  score pass: best cell, colbest(i), second best
 //   DIR && !BEST  direction pass over a sub-rectangle (reduced traceback)
+//   DIR && !BEST && HGT  the same sub-rectangle, storing each cell's H as a byte
+//                 (LOCAL, every score below 255) instead of a direction nibble:
+//                 the score pass's arithmetic, and the walk re-derives the
+//                 decisions from the heights
 //   DIR && BEST   plain form: direction bits over the whole window + best
 #pragma once
 
@@ -57,10 +61,12 @@ __device__ __forceinline__ uint32_t load_window16(const FillArgs& A, int64_t wst
     return (uint32_t)(v >> sh) & 0xFFFFu;
 }
 
-template <int L, int K, int MODE, bool DIR, bool BEST>
+template <int L, int K, int MODE, bool DIR, bool BEST, bool HGT = false>
 __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
     static_assert(32 % L == 0, "L must divide 32");
     static_assert(K >= 1 && K <= 32, "K in 1..32");
+    static_assert(!HGT || (DIR && !BEST && MODE == SA_LOCAL), "heights: LOCAL sub-rectangle pass only");
+    constexpr int KH = (K + 3) / 4;                 // height words of a lane per step
     constexpr int G = 32 / L;
     constexpr bool LOCAL = (MODE == SA_LOCAL);
     const unsigned FULL = 0xffffffffu;
@@ -204,15 +210,20 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
             // the direction passes keep the step loop rolled: their step body (K rows
             // of compare/select and nibble packing) is large, and eight copies of it
             // overflow the instruction cache
-            constexpr int kUnrollSteps = DIR ? 1 : 8;
+            constexpr int kUnrollSteps = (DIR && !HGT) ? 1 : 8;
 #pragma unroll kUnrollSteps
             for (int u = 0; u < 8; u++) {
                 const int s = 8 * b + u;
                 const int i = s - g + 1;
                 uint32_t dw[(K + 7) / 8];
+                uint32_t hw[HGT ? KH : 1];
                 if (DIR) {
 #pragma unroll
                     for (int k = 0; k < (K + 7) / 8; k++) dw[k] = 0u;
+                }
+                if (HGT) {
+#pragma unroll
+                    for (int k = 0; k < KH; k++) hw[k] = 0u;
                 }
                 int32_t hg_up = __shfl_up_sync(FULL, hg_bot, 1, L);
                 int32_t e_up = __shfl_up_sync(FULL, e_bot, 1, L);
@@ -257,10 +268,12 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
                         diag = HG[r];
                     }
                     int32_t f, h;
-                    if (!DIR) {
+                    if (!DIR || HGT) {
                         f = addmax(F[r], S.GE, HG[r]);    // max(F(i-1,j)+GE, H(i-1,j)+GO)
                         e = addmax(e, S.GE, hga);         // max(E(i,j-1)+GE, H(i,j-1)+GO)
                         h = LOCAL ? __vimax3_s32_relu(gv, e, f) : __vimax3_s32(gv, e, f);
+                        // byte r & 3 of word r / 4 (0..254: every score is below 255)
+                        if (HGT) hw[r >> 2] |= (uint32_t)h << (8 * (r & 3));
                     } else {
                         const int32_t fe = F[r] + S.GE;
                         const bool fopen = HG[r] >= fe;
@@ -335,11 +348,18 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
                         if (cb_ok(i)) cb[i - 1] = hv - S.GO;
                     }
                 }
-                if (DIR && b < nblk) {
+                if (DIR && !HGT && b < nblk) {
 #pragma unroll
                     for (int k = 0; k < (K + 7) / 8; k++) {
                         const uint64_t at = aoff + ((uint64_t)s * ((K + 7) / 8) + k) * L + g;
                         if (SA_GUARD(at < A.arena_cap, A.dbg, kSiteArena)) A.arena[at] = dw[k];
+                    }
+                }
+                if (HGT && b < nblk) {
+#pragma unroll
+                    for (int k = 0; k < KH; k++) {
+                        const uint64_t at = aoff + ((uint64_t)s * KH + k) * L + g;
+                        if (SA_GUARD(at < A.arena_cap, A.dbg, kSiteArena)) A.arena[at] = hw[k];
                     }
                 }
             }

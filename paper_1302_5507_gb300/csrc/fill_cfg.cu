@@ -17,20 +17,20 @@ constexpr int kK = kCfgs[SA_CFG].K;
 template <bool DIR, bool BEST>
 constexpr size_t smem_bytes() { return (BEST != DIR) ? 4 * prof_words_per_warp<kK>() * sizeof(int32_t) : 0; }
 
-template <int MODE, bool DIR, bool BEST>
+template <int MODE, bool DIR, bool BEST, bool HGT = false>
 void prepare() {
     static bool done = false;   // attribute set once per process (same on every device)
     if (!done) {
-        cudaFuncSetAttribute(k_fill32<kL, kK, MODE, DIR, BEST>,
+        cudaFuncSetAttribute(k_fill32<kL, kK, MODE, DIR, BEST, HGT>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<DIR, BEST>());
         done = true;
     }
 }
 
-template <int MODE, bool DIR, bool BEST>
+template <int MODE, bool DIR, bool BEST, bool HGT = false>
 void launch_one(const FillLaunch& fl) {
-    prepare<MODE, DIR, BEST>();
-    k_fill32<kL, kK, MODE, DIR, BEST><<<fl.grid, fl.block, smem_bytes<DIR, BEST>(), fl.stream>>>(fl.args);
+    prepare<MODE, DIR, BEST, HGT>();
+    k_fill32<kL, kK, MODE, DIR, BEST, HGT><<<fl.grid, fl.block, smem_bytes<DIR, BEST>(), fl.stream>>>(fl.args);
 }
 
 constexpr size_t smem16_bytes() { return 4 * prof16_words_per_warp<kK>() * sizeof(int32_t); }
@@ -44,11 +44,11 @@ void prepare16() {
     }
 }
 
-template <int MODE, bool DIR, bool BEST>
+template <int MODE, bool DIR, bool BEST, bool HGT = false>
 int blocks_per_sm() {
-    prepare<MODE, DIR, BEST>();
+    prepare<MODE, DIR, BEST, HGT>();
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fill32<kL, kK, MODE, DIR, BEST>, 128,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fill32<kL, kK, MODE, DIR, BEST, HGT>, 128,
                                                   smem_bytes<DIR, BEST>());
     return nb;
 }
@@ -71,6 +71,9 @@ void launch_fill<SA_CFG>(const FillLaunch& fl) {
         prepare16();
         k_fill16<kL, kK><<<fl.grid, fl.block, smem16_bytes(), fl.stream>>>(fl.args);
         break;
+    case kFillRectH:            // byte heights: LOCAL only
+        if (local) launch_one<SA_LOCAL, true, false, true>(fl);
+        break;
     default:
         break;
     }
@@ -86,6 +89,8 @@ int fill_blocks_per_sm<SA_CFG>(int kind, int mode) {
         return local ? blocks_per_sm<SA_LOCAL, true, false>() : blocks_per_sm<SA_GLOCAL, true, false>();
     case kFillPlain:
         return local ? blocks_per_sm<SA_LOCAL, true, true>() : blocks_per_sm<SA_GLOCAL, true, true>();
+    case kFillRectH:
+        return local ? blocks_per_sm<SA_LOCAL, true, false, true>() : 0;
     case kFillScore16: {
         prepare16();
         int nb = 0;

@@ -67,6 +67,12 @@ void launch_pack_reads(const sa_job* jobs, uint32_t n_jobs, const uint8_t* reads
 void launch_rect_plan(const sa_job* jobs, const uint32_t* order, uint32_t n_pos, const uint32_t* cfg_begin,
                       const JobState* state, const Score& sc, int32_t min_score, int allow_band,
                       Rect* rect, uint64_t* sizes, uint32_t* const* lists, uint32_t* cls_count,
+                      uint32_t* rect_flag, int heights, cudaStream_t st);
+// the rectangle-pass jobs compacted in bucketed order (rect_pos = exclusive scan of
+// rect_flag, total its sum) and each bucket's first index in the list
+// (rect_begin[kNumCfg + 1])
+void launch_rect_list(const uint32_t* order, uint32_t n_pos, const uint32_t* rect_flag, const uint64_t* rect_pos,
+                      const uint32_t* cfg_begin, const uint64_t* total, uint32_t* list, uint32_t* rect_begin,
                       cudaStream_t st);
 // heights: the byte-height form (LOCAL and every score below 255; the band
 // regions then hold B/4 words a row instead of B/8)
@@ -80,10 +86,20 @@ void launch_scan_u64(const uint64_t* in, uint64_t n, uint64_t* out, uint64_t* bs
                      cudaStream_t st);
 void launch_scan_u32(const uint32_t* in, uint64_t n, uint64_t* out, uint64_t* bsum, uint64_t* total,
                      cudaStream_t st);
+// rectangle jobs whose pass stored byte heights (LOCAL, every score below 255):
+// the walk re-derives its decisions from the heights and the bases
+struct HeightWalk {
+    int on;
+    const uint32_t* ref;           // padded packed reference
+    const uint32_t* rpack;         // packed reads, rw words per job
+    uint32_t rw;
+    Score sc;
+};
 void launch_traceback(const sa_job* jobs, uint32_t job_begin, uint32_t n_jobs, const JobState* state,
                       const Rect* rect, const uint32_t* arena, const BandLayout& band, int wave,
                       int mode, int plain, int cfg_force, int32_t min_score, uint32_t* tmp_ops,
-                      uint32_t tmp_stride, TbOut* tb, unsigned* err_job, cudaStream_t st);
+                      uint32_t tmp_stride, TbOut* tb, unsigned* err_job, const HeightWalk& hw,
+                      cudaStream_t st);
 void launch_iota(uint32_t* p, uint32_t n, cudaStream_t st);
 void launch_cigar_count(const sa_job* jobs, uint32_t n_jobs, const JobState* state, const TbOut* tb,
                         int mode, int want_cigar, int32_t min_score, uint32_t* count,

@@ -229,7 +229,7 @@ struct FillLaunch {
     int grid, block;
     cudaStream_t stream;
 };
-enum { kFillScore = 0, kFillRect = 1, kFillPlain = 2, kFillScore16 = 3 };
+enum { kFillScore = 0, kFillRect = 1, kFillPlain = 2, kFillScore16 = 3, kFillRectH = 4 };
 
 // per-configuration launchers (one translation unit per configuration)
 template <int C> void launch_fill(const FillLaunch& fl);
@@ -244,6 +244,15 @@ template <int C> int fill_blocks_per_sm(int kind, int mode);   // resident 128-t
 __host__ __device__ inline uint64_t dir_words(int L, int K, int w) {
     uint64_t blocks = (uint64_t)(w + L - 1 + 7) / 8;
     return blocks * 8 * (uint64_t)((K + 7) / 8) * (uint64_t)L;
+}
+// the byte-height form of the same layout (LOCAL, every score below 255): KH =
+// ceil(K/4) words a step and lane, the height of row r in byte r%4 of word r/4
+__host__ __device__ inline uint64_t hgt_words(int L, int K, int w) {
+    uint64_t blocks = (uint64_t)(w + L - 1 + 7) / 8;
+    return blocks * 8 * (uint64_t)((K + 3) / 4) * (uint64_t)L;
+}
+__host__ __device__ inline uint64_t rect_words(int L, int K, int w, bool heights) {
+    return heights ? hgt_words(L, K, w) : dir_words(L, K, w);
 }
 
 }  // namespace sa

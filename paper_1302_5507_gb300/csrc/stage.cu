@@ -264,7 +264,8 @@ __global__ void k_rect_plan(const sa_job* __restrict__ jobs, const uint32_t* __r
                             uint32_t n_pos, const uint32_t* __restrict__ cfg_begin,
                             const JobState* __restrict__ state, Score sc,
                             int32_t min_score, int allow_band, Rect* __restrict__ rect,
-                            uint64_t* __restrict__ sizes, BandLists lists, uint32_t* cls_count) {
+                            uint64_t* __restrict__ sizes, BandLists lists, uint32_t* cls_count,
+                            uint32_t* __restrict__ rect_flag, int heights) {
     // no early return: the class lists are appended with warp-wide ballots
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = p < n_pos;
@@ -343,35 +344,56 @@ __global__ void k_rect_plan(const sa_job* __restrict__ jobs, const uint32_t* __r
     }
     if (valid) {
         rect[job] = R;
-        sizes[p] = R.w > 0 ? dir_words(cfg_L(c), cfg_K(c), R.w) : 0;
+        sizes[p] = R.w > 0 ? rect_words(cfg_L(c), cfg_K(c), R.w, heights != 0) : 0;
+        rect_flag[p] = R.w > 0 ? 1u : 0u;
     }
+}
+
+// the jobs of the wavefront rectangle pass, in the bucketed order (rect_pos is
+// the exclusive scan of rect_flag), and where each bucket's run of them begins
+__global__ void k_rect_list(const uint32_t* __restrict__ order, uint32_t n_pos, const uint32_t* __restrict__ rect_flag,
+                            const uint64_t* __restrict__ rect_pos, uint32_t* __restrict__ list) {
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n_pos && rect_flag[p]) list[rect_pos[p]] = order[p];
+}
+__global__ void k_rect_bounds(const uint64_t* __restrict__ rect_pos, uint32_t n_pos,
+                              const uint32_t* __restrict__ cfg_begin, const uint64_t* total,
+                              uint32_t* __restrict__ rect_begin) {
+    const int c = threadIdx.x;
+    if (c <= kNumCfg) rect_begin[c] = cfg_begin[c] < n_pos ? (uint32_t)rect_pos[cfg_begin[c]] : (uint32_t)*total;
+}
+void launch_rect_list(const uint32_t* order, uint32_t n_pos, const uint32_t* rect_flag, const uint64_t* rect_pos,
+                      const uint32_t* cfg_begin, const uint64_t* total, uint32_t* list, uint32_t* rect_begin,
+                      cudaStream_t st) {
+    if (!n_pos) return;
+    k_rect_list<<<(n_pos + 255) / 256, 256, 0, st>>>(order, n_pos, rect_flag, rect_pos, list);
+    k_rect_bounds<<<1, 64, 0, st>>>(rect_pos, n_pos, cfg_begin, total, rect_begin);
 }
 
 void launch_rect_plan(const sa_job* jobs, const uint32_t* order, uint32_t n_pos, const uint32_t* cfg_begin,
                       const JobState* state, const Score& sc, int32_t min_score, int allow_band,
                       Rect* rect, uint64_t* sizes, uint32_t* const* lists, uint32_t* cls_count,
-                      cudaStream_t st) {
+                      uint32_t* rect_flag, int heights, cudaStream_t st) {
     if (!n_pos) return;
     BandLists bl;
     for (int k = 0; k < kNumBand; k++) bl.p[k] = lists[k];
     k_rect_plan<<<(n_pos + 255) / 256, 256, 0, st>>>(jobs, order, n_pos, cfg_begin, state, sc, min_score,
-                                                      allow_band, rect, sizes, bl, cls_count);
+                                                      allow_band, rect, sizes, bl, cls_count, rect_flag,
+                                                      heights);
 }
 
-// wave assignment: an item (the G jobs a warp takes at once) belongs to the wave
-// of its first job, so every item fits the arena slack (cap - item_max).
+// wave assignment: a job belongs to the wave of its first direction word, so its
+// words fit the arena slack (cap - wave words >= the largest job).
 __global__ void k_rect_assign(const uint32_t* __restrict__ order, uint32_t n_pos,
                               const uint64_t* __restrict__ offs, const uint32_t* __restrict__ cfg_begin,
                               uint64_t wave_words, Rect* __restrict__ rect, uint32_t* max_wave) {
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_pos) return;
     const uint32_t job = order[p];
-    // configuration of this position and the first position of its item
-    int c = 0;
-    while (c + 1 < kNumCfg && cfg_begin[c + 1] <= p) c++;
-    const uint32_t G = 32 / cfg_L(c);
-    const uint32_t first = cfg_begin[c] + ((p - cfg_begin[c]) / G) * G;
-    const uint64_t wv = wave_words ? offs[first] / wave_words : 0;
+    // the wave of the job's first word; a job's words (at most one item) fit the
+    // arena's slack past the wave's share
+    (void)cfg_begin;
+    const uint64_t wv = wave_words ? offs[p] / wave_words : 0;
     Rect R = rect[job];
     R.wave = (int)wv;
     R.off = offs[p] - wv * wave_words;
@@ -501,12 +523,22 @@ __device__ __forceinline__ uint32_t band_nibble(const uint32_t* __restrict__ are
     return (word >> (4 * (k & 7))) & 15u;
 }
 
+__device__ __forceinline__ int32_t rect_height(const uint32_t* __restrict__ arena, uint64_t off, int L, int K,
+                                               int pad, int i, int j) {
+    const int idx = j - 1 + pad;
+    const int g = idx / K, r = idx - g * K;
+    const int s = i - 1 + g;                 // the step at which lane g computed column i
+    const uint32_t word = arena[off + ((uint64_t)s * ((K + 3) / 4) + (r >> 2)) * L + g];
+    return (int32_t)((word >> (8 * (r & 3))) & 255u);
+}
+
 __global__ void k_traceback(const sa_job* __restrict__ jobs, uint32_t job_begin, uint32_t n_jobs,
                             const JobState* __restrict__ state, const Rect* __restrict__ rect,
                             const uint32_t* __restrict__ arena, BandLayout band, int wave, int mode,
                             int plain,
                             int cfg_force, int32_t min_score, uint32_t* __restrict__ tmp_ops,
-                            uint32_t tmp_stride, TbOut* __restrict__ tb, unsigned* err_job) {
+                            uint32_t tmp_stride, TbOut* __restrict__ tb, unsigned* err_job,
+                            HeightWalk hw) {
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= n_jobs) return;
     const uint32_t job = job_begin + tid;
@@ -551,6 +583,39 @@ __global__ void k_traceback(const sa_job* __restrict__ jobs, uint32_t job_begin,
     }
     const int imax_walk = banded ? st.i_star : R.w;
     const uint64_t off = R.off;
+    if (hw.on && !banded && !plain) {
+        // byte heights of the rectangle (LOCAL, every score below 255); column 0 of
+        // the rectangle (window column i_lo - 1) and row 0 are borders of value 0
+        const sa_job J = jobs[job];
+        const uint32_t* refw = hw.ref + kRefFrontPad;
+        const uint32_t* rp = hw.rpack + (size_t)job * hw.rw;
+        const int64_t col0 = (int64_t)J.ref_pos + R.i_lo - 2;     // reference position of rectangle column 0
+        auto height = [&](int ii, int jj) -> int32_t {
+            if (ii < 0 || jj < 0 || ii > R.w || jj > R.rows) return kNeg32;
+            if (ii == 0 || jj == 0) return 0;
+            return rect_height(arena, off, L, K, pad, ii, jj);
+        };
+        auto match = [&](int ii, int jj) -> bool {
+            const int64_t p = col0 + ii;
+            const uint32_t t = (__ldg(refw + (p >> 4)) >> (2 * (p & 15))) & 3u;
+            const uint32_t r = (__ldg(rp + ((jj - 1) >> 4)) >> (2 * ((jj - 1) & 15))) & 3u;
+            return t == r;
+        };
+        const WalkEnd e = walk_heights(si, sj, st.best, R.w, R.rows, st.best, hw.sc.GO, hw.sc.GE, hw.sc.a,
+                                       hw.sc.b, height, match, tmp_ops + (uint64_t)job * tmp_stride, tmp_stride);
+        if (e.bad) {
+            atomicMin(err_job, job);
+            out.n_rev = 0;
+            out.read_begin = 0;
+            out.ref_begin_rel = 0;
+        } else {
+            out.n_rev = e.n_rev;
+            out.read_begin = e.j;
+            out.ref_begin_rel = (R.i_lo - 1) + e.i;
+        }
+        tb[job] = out;
+        return;
+    }
     auto nib_at = [&](int ii, int jj, bool* out_bad) -> uint32_t {
         if (banded) {
             const int k = ii - jj - R.d_lo;
@@ -578,11 +643,12 @@ __global__ void k_traceback(const sa_job* __restrict__ jobs, uint32_t job_begin,
 void launch_traceback(const sa_job* jobs, uint32_t job_begin, uint32_t n_jobs, const JobState* state,
                       const Rect* rect, const uint32_t* arena, const BandLayout& band, int wave,
                       int mode, int plain, int cfg_force, int32_t min_score, uint32_t* tmp_ops,
-                      uint32_t tmp_stride, TbOut* tb, unsigned* err_job, cudaStream_t st) {
+                      uint32_t tmp_stride, TbOut* tb, unsigned* err_job, const HeightWalk& hw,
+                      cudaStream_t st) {
     if (!n_jobs) return;
     k_traceback<<<(n_jobs + 127) / 128, 128, 0, st>>>(jobs, job_begin, n_jobs, state, rect, arena,
                                                        band, wave, mode, plain, cfg_force, min_score,
-                                                       tmp_ops, tmp_stride, tb, err_job);
+                                                       tmp_ops, tmp_stride, tb, err_job, hw);
 }
 
 __global__ void k_iota(uint32_t* __restrict__ p, uint32_t n) {

@@ -77,3 +77,93 @@ __device__ __forceinline__ WalkEnd walk_nibbles(int i, int j, int imax, int rows
 }
 
 }  // namespace sa
+
+namespace sa {
+
+// Traceback walk over stored heights (LOCAL, every score below 255): the walk
+// re-derives each decision the direction nibbles would record, from the same
+// DP values -- in state H at (i, j): the diagonal when H(i-1,j-1) + delta = H;
+// else a deletion when H equals F(i,j) = max over k >= 1 of H(i-k,j) + S_GO +
+// (k-1) S_GE, an insertion otherwise; a gap run extends from (i, j) while its
+// value is strictly above H(neighbour) + S_GO -- so the CIGAR is the one the
+// nibble walk gives.  E(i,j) (the same maximum up the column) is looked at first:
+// below H it leaves the deletion as the only source, and only an E equal to H
+// needs F, whose scan stops at the first term reaching H or once no height up to
+// `hmax` could.  height(ii, jj) gives the DP value or kNeg32 off the stored area
+// (row 0 and column 0 are borders of value 0); match(ii, jj) tells whether
+// window base ii equals read base jj.
+template <class Height, class Match>
+__device__ __forceinline__ WalkEnd walk_heights(int i, int j, int32_t h, int imax, int rows, int32_t hmax,
+                                                int32_t GO, int32_t GE, int32_t sa, int32_t sb, Height height,
+                                                Match match, uint32_t* ops, uint32_t cap) {
+    int nrev = 0;
+    uint32_t cur_op = 15u, cur_len = 0;
+    auto emit = [&](uint32_t op) {
+        if (op == cur_op) { cur_len++; return; }
+        if (cur_len) ops[nrev++] = (cur_len << 4) | cur_op;
+        cur_op = op;
+        cur_len = 1;
+    };
+    // max over k >= 1 of height(i - k*di, j - k*dj) + GO + (k-1) GE, or a value
+    // below `want` once no term from there on can reach it (heights are <= hmax);
+    // only its comparison with `want` is used
+    auto gap_max = [&](int di, int dj, int32_t want) -> int32_t {
+        int32_t f = kNeg32;
+        const int n = di ? i : j;
+        for (int kk = 1; kk <= n; kk++) {
+            if (hmax + GO + (kk - 1) * GE < want) break;   // no term from here on reaches want
+            const int32_t hx = height(i - kk * di, j - kk * dj);
+            if (hx == kNeg32) break;                  // off the stored area: the rest is -inf
+            f = max(f, hx + GO + (kk - 1) * GE);
+            if (f >= want) break;                     // F and E never exceed H: f == want
+        }
+        return f;
+    };
+    int32_t cur = 0;
+    int state = 0;                                    // 0 H, 1 E (insertion), 2 F (deletion)
+    int budget = 2 * (imax + rows) + 4;
+    bool bad = (i < 1 || j < 1 || j > rows || i > imax || height(i, j) != h);
+    while (!bad) {
+        if (--budget < 0 || nrev >= (int)cap - 1) { bad = true; break; }
+        if (state == 0) {
+            if (i == 0 || j == 0 || h <= 0) break;
+            const int32_t hd = height(i - 1, j - 1);
+            if (hd != kNeg32 && hd + (match(i, j) ? sa : sb) == h) {
+                emit(0u);
+                i--; j--; h = hd;
+                continue;
+            }
+            const int32_t e = gap_max(0, 1, h);
+            if (e < h) state = 2;                     // F is the only source left
+            else state = (gap_max(1, 0, h) == h) ? 2 : 1;
+            cur = h;
+        } else if (state == 2) {
+            if (i < 1) { bad = true; break; }
+            emit(2u);
+            const int32_t hn = height(i - 1, j);
+            i--;
+            if (hn != kNeg32 && cur <= hn + GO) { state = 0; h = hn; }
+            else cur -= GE;
+        } else {
+            if (j < 1) { bad = true; break; }
+            emit(1u);
+            const int32_t hn = height(i, j - 1);
+            j--;
+            if (hn != kNeg32 && cur <= hn + GO) { state = 0; h = hn; }
+            else cur -= GE;
+        }
+    }
+    WalkEnd w;
+    w.bad = bad;
+    if (bad) {
+        w.n_rev = 0; w.i = 0; w.j = 0;
+        return w;
+    }
+    if (cur_len) ops[nrev++] = (cur_len << 4) | cur_op;
+    w.n_rev = nrev;
+    w.i = i;
+    w.j = j;
+    return w;
+}
+
+}  // namespace sa
