@@ -179,7 +179,8 @@ def direction_bound(stats, wl):
 
 
 PROBE_OPS = ("viaddmax_s32", "vimax3_s32", "vimax3_s32_relu", "iadd_s32", "imax_s32", "imad_s32",
-             "viaddmax_s16x2", "vimax3_s16x2", "prmt", "vmaxs4 (s8x4)", "vaddss4 (s8x4)")
+             "viaddmax_s16x2", "vimax3_s16x2", "prmt", "vmaxs4 (s8x4)", "vaddss4 (s8x4)",
+             "viaddmax_s16x2 + imad (half the chains each)", "viaddmax_s16x2 + prmt (half the chains each)")
 
 
 def probe_all_ops():

@@ -196,62 +196,16 @@ __device__ __forceinline__ void band_row_h(int32_t (&Hs)[B + 1], int32_t (&Es)[B
     }
 }
 
+// The walk of a byte-height band job from its best cell, deciding from the
+// stored heights (see the file comment); `out` is the job's lane of its region.
 template <int B>
-__global__ void __launch_bounds__(128) k_band_h(BandArgs A) {
-    constexpr int W = B / 4;                   // words of heights a row
-    static_assert(B == 8 || B == 16 || B == 32 || B == 64, "band widths 8, 16, 32 and 64");
-    const uint32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pos >= A.count) return;
-    const uint32_t job = A.list[pos];
-    const sa_job J = A.jobs[job];
-    const Rect R = A.rect[job];
+__device__ __forceinline__ void band_h_walk(const BandArgs& A, uint32_t pos, uint32_t job, const sa_job& J,
+                                            const Rect& R, const uint32_t* out, const uint32_t* rp,
+                                            const uint32_t* refw, int32_t GO, int32_t GE, int32_t sa, int32_t sb) {
+    constexpr int W = B / 4;
     const int rows = R.rows;
     const int dlo = R.d_lo;
-    const int32_t GO = in_reg(A.sc.GO), GE = in_reg(A.sc.GE), sa = in_reg(A.sc.a), sb = in_reg(A.sc.b);
-    const uint64_t out_base = (uint64_t)(pos >> 5) * A.warp_stride + (pos & 31);
-    uint32_t* out = A.arena + out_base;
-    const uint32_t* rp = A.rpack + (size_t)job * A.rw;
-    const uint32_t* refw = A.ref + kRefFrontPad;
-
-    int32_t Hs[B + 1], Es[B + 1];
-#pragma unroll
-    for (int k = 0; k <= B; k++) {
-        Hs[k] = (k < B && dlo + k >= 0) ? 0 : kNeg32;
-        Es[k] = kNeg32;
-    }
-    for (int j = 1; j <= rows; j++) {
-        const int i0 = j + dlo;
-        const uint64_t rb = (uint64_t)((__ldg(rp + ((j - 1) >> 4)) >> (2 * ((j - 1) & 15))) & 3u);
-        constexpr int NH = B > 32 ? 2 : 1;
-        uint64_t mmh[NH];
-#pragma unroll
-        for (int hh = 0; hh < NH; hh++) {
-            const int64_t ph = (int64_t)J.ref_pos + i0 - 1 + 32 * hh;
-            int64_t qh = ph < (int64_t)J.ref_pos ? (int64_t)J.ref_pos : ph;
-            if (qh > A.ref_len) qh = A.ref_len;
-            const int64_t wi = qh >> 4;
-            const uint32_t sh = (uint32_t)(qh & 15) * 2u;
-            const uint64_t lo = ((uint64_t)__ldg(refw + wi + 1) << 32) | (uint64_t)__ldg(refw + wi);
-            const uint64_t hi = (uint64_t)__ldg(refw + wi + 2);
-            uint64_t wb = sh ? ((lo >> sh) | (hi << (64 - sh))) : lo;
-            const int64_t lead = qh - ph;
-            wb = lead >= 32 ? 0ull : (wb << (2 * lead));
-            const uint64_t x = wb ^ (rb * 0x5555555555555555ull);
-            mmh[hh] = ~(x | (x >> 1)) & 0x5555555555555555ull;
-        }
-        uint32_t words[W];
-#pragma unroll
-        for (int w = 0; w < W; w++) words[w] = 0u;
-        if (i0 >= 1) band_row_h<B, false>(Hs, Es, words, mmh, i0, GO, GE, sa, sb);
-        else band_row_h<B, true>(Hs, Es, words, mmh, i0, GO, GE, sa, sb);
-#pragma unroll
-        for (int w = 0; w < W; w++) {
-            const uint64_t at = ((uint64_t)(j - 1) * W + w) * 32;
-            if (SA_GUARD(out_base + at < A.region_cap, A.dbg, kSiteBand)) out[at] = words[w];
-        }
-    }
-
-    // the walk from the best cell, deciding from the stored heights
+    (void)pos;
     const JobState st = A.state[job];
     auto height = [&](int ii, int jj) -> int32_t {     // band H(ii, jj); kNeg32 outside
         if (jj == 0) return ii >= 0 ? 0 : kNeg32;       // row 0
@@ -362,6 +316,79 @@ __global__ void __launch_bounds__(128) k_band_h(BandArgs A) {
     if (SA_GUARD(job < A.n_state, A.dbg, kSiteBandTb)) A.tb[job] = t;
 }
 
+template <int B, bool WALK>
+__global__ void __launch_bounds__(128) k_band_h(BandArgs A) {
+    constexpr int W = B / 4;                   // words of heights a row
+    static_assert(B == 8 || B == 16 || B == 32 || B == 64, "band widths 8, 16, 32 and 64");
+    const uint32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= A.count) return;
+    const uint32_t job = A.list[pos];
+    const sa_job J = A.jobs[job];
+    const Rect R = A.rect[job];
+    const int rows = R.rows;
+    const int dlo = R.d_lo;
+    const int32_t GO = in_reg(A.sc.GO), GE = in_reg(A.sc.GE), sa = in_reg(A.sc.a), sb = in_reg(A.sc.b);
+    const uint64_t out_base = (uint64_t)(pos >> 5) * A.warp_stride + (pos & 31);
+    uint32_t* out = A.arena + out_base;
+    const uint32_t* rp = A.rpack + (size_t)job * A.rw;
+    const uint32_t* refw = A.ref + kRefFrontPad;
+
+    int32_t Hs[B + 1], Es[B + 1];
+#pragma unroll
+    for (int k = 0; k <= B; k++) {
+        Hs[k] = (k < B && dlo + k >= 0) ? 0 : kNeg32;
+        Es[k] = kNeg32;
+    }
+    for (int j = 1; j <= rows; j++) {
+        const int i0 = j + dlo;
+        const uint64_t rb = (uint64_t)((__ldg(rp + ((j - 1) >> 4)) >> (2 * ((j - 1) & 15))) & 3u);
+        constexpr int NH = B > 32 ? 2 : 1;
+        uint64_t mmh[NH];
+#pragma unroll
+        for (int hh = 0; hh < NH; hh++) {
+            const int64_t ph = (int64_t)J.ref_pos + i0 - 1 + 32 * hh;
+            int64_t qh = ph < (int64_t)J.ref_pos ? (int64_t)J.ref_pos : ph;
+            if (qh > A.ref_len) qh = A.ref_len;
+            const int64_t wi = qh >> 4;
+            const uint32_t sh = (uint32_t)(qh & 15) * 2u;
+            const uint64_t lo = ((uint64_t)__ldg(refw + wi + 1) << 32) | (uint64_t)__ldg(refw + wi);
+            const uint64_t hi = (uint64_t)__ldg(refw + wi + 2);
+            uint64_t wb = sh ? ((lo >> sh) | (hi << (64 - sh))) : lo;
+            const int64_t lead = qh - ph;
+            wb = lead >= 32 ? 0ull : (wb << (2 * lead));
+            const uint64_t x = wb ^ (rb * 0x5555555555555555ull);
+            mmh[hh] = ~(x | (x >> 1)) & 0x5555555555555555ull;
+        }
+        uint32_t words[W];
+#pragma unroll
+        for (int w = 0; w < W; w++) words[w] = 0u;
+        if (i0 >= 1) band_row_h<B, false>(Hs, Es, words, mmh, i0, GO, GE, sa, sb);
+        else band_row_h<B, true>(Hs, Es, words, mmh, i0, GO, GE, sa, sb);
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            const uint64_t at = ((uint64_t)(j - 1) * W + w) * 32;
+            if (SA_GUARD(out_base + at < A.region_cap, A.dbg, kSiteBand)) out[at] = words[w];
+        }
+    }
+
+    if (WALK) band_h_walk<B>(A, pos, job, J, R, out, rp, refw, GO, GE, sa, sb);
+}
+
+// the walk of a byte-height band job on its own (the pass ran without it): a
+// light kernel, many resident warps to hide the walk's dependent loads
+template <int B>
+__global__ void __launch_bounds__(128) k_band_h_walk(BandArgs A) {
+    const uint32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= A.count) return;
+    const uint32_t job = A.list[pos];
+    const sa_job J = A.jobs[job];
+    const Rect R = A.rect[job];
+    const int32_t GO = in_reg(A.sc.GO), GE = in_reg(A.sc.GE), sa = in_reg(A.sc.a), sb = in_reg(A.sc.b);
+    const uint64_t out_base = (uint64_t)(pos >> 5) * A.warp_stride + (pos & 31);
+    band_h_walk<B>(A, pos, job, J, R, A.arena + out_base, A.rpack + (size_t)job * A.rw, A.ref + kRefFrontPad,
+                   GO, GE, sa, sb);
+}
+
 }  // namespace
 
 void launch_band(int cls, const BandArgs& a, bool heights, cudaStream_t st) {
@@ -369,10 +396,18 @@ void launch_band(int cls, const BandArgs& a, bool heights, cudaStream_t st) {
     const unsigned grid = (a.count + 127) / 128;
     const bool local = a.sc.mode == SA_LOCAL;
     if (heights) {                     // LOCAL, scores below 255
-        if (cls == kClsBand8) k_band_h<8><<<grid, 128, 0, st>>>(a);
-        else if (cls == kClsBand16) k_band_h<16><<<grid, 128, 0, st>>>(a);
-        else if (cls == kClsBand32) k_band_h<32><<<grid, 128, 0, st>>>(a);
-        else k_band_h<64><<<grid, 128, 0, st>>>(a);
+        // the narrow classes walk right after their pass in the same thread; the wide
+        // ones (96 and 168 registers a thread) hand the walk to a light kernel on the
+        // same stream, which keeps many more warps resident for its dependent loads
+        if (cls == kClsBand8) k_band_h<8, true><<<grid, 128, 0, st>>>(a);
+        else if (cls == kClsBand16) k_band_h<16, true><<<grid, 128, 0, st>>>(a);
+        else if (cls == kClsBand32) {
+            k_band_h<32, false><<<grid, 128, 0, st>>>(a);
+            k_band_h_walk<32><<<grid, 128, 0, st>>>(a);
+        } else {
+            k_band_h<64, false><<<grid, 128, 0, st>>>(a);
+            k_band_h_walk<64><<<grid, 128, 0, st>>>(a);
+        }
         return;
     }
     if (cls == kClsBand8) {

@@ -17,7 +17,10 @@ enum Op {
     kViaddmaxS32 = 0, kVimax3S32 = 1, kVimax3ReluS32 = 2, kIaddS32 = 3, kImaxS32 = 4, kImadS32 = 5,
     kViaddmaxS16x2 = 6, kVimax3S16x2 = 7, kPrmt = 8,
     kVmaxS8x4 = 9, kVaddS8x4 = 10,                 // 4-way byte SIMD (signed max, saturating add)
-    kNumOps = 11
+    // half the chains one operation, half another: whether the two issue side by side
+    kMixAddmaxImad = 11,                           // __viaddmax_s16x2 (ALU pipe) + IMAD (FMA pipe)
+    kMixAddmaxPrmt = 12,                           // __viaddmax_s16x2 + PRMT (both ALU pipe)
+    kNumOps = 13
 };
 
 template <int OP>
@@ -42,6 +45,10 @@ __global__ void __launch_bounds__(256) k_probe(int iters, uint32_t seed, uint32_
                 if (OP == kPrmt) x[c] = __byte_perm(x[c], y, 0x5410 + c);
                 if (OP == kVmaxS8x4) x[c] = __vmaxs4(x[c], y + c);
                 if (OP == kVaddS8x4) x[c] = __vaddss4(x[c], y);
+                if (OP == kMixAddmaxImad)
+                    x[c] = (c & 1) ? x[c] * one + y : __viaddmax_s16x2(x[c], y, z);
+                if (OP == kMixAddmaxPrmt)
+                    x[c] = (c & 1) ? __byte_perm(x[c], y, 0x5410 + c) : __viaddmax_s16x2(x[c], y, z);
             }
             y += 1;
         }
@@ -93,6 +100,8 @@ extern "C" double sa_probe_ops_per_sm_clk(int op, double sm_mhz) {
     case kPrmt: ms = run<kPrmt>(blocks, iters, sink); break;
     case kVmaxS8x4: ms = run<kVmaxS8x4>(blocks, iters, sink); break;
     case kVaddS8x4: ms = run<kVaddS8x4>(blocks, iters, sink); break;
+    case kMixAddmaxImad: ms = run<kMixAddmaxImad>(blocks, iters, sink); break;
+    case kMixAddmaxPrmt: ms = run<kMixAddmaxPrmt>(blocks, iters, sink); break;
     default: break;
     }
     cudaFree(sink);
