@@ -15,7 +15,8 @@
 //    bases, which is all backward search and the lookup table below need);
 //  - the BWT of that order in 64-byte chunks, as the paper lays its index out
 //    so that all the data for one base step is one memory access: four 32-bit
-//    counts of A, C, G, T before the chunk, then 192 BWT codes at 2 bits;
+//    counts of A, C, G, T before the chunk, then 192 two-bit BWT codes as two bit
+//    planes (one match mask per 32 rows);
 //  - a lookup table of the row interval of every 12-base pattern, which
 //    replaces the first 12 steps of each backward search;
 //  - the full suffix array for locating (4 bytes a row: the paper's index
@@ -154,17 +155,17 @@ __device__ __forceinline__ uint32_t occ_rank(const uint4* __restrict__ occ, uint
     const uint32_t chunk = i / sa::kChunkRows, in = i - chunk * sa::kChunkRows;
     const uint4* q = occ + (size_t)chunk * 4;
     const uint4 h = __ldg(q), a = __ldg(q + 1), b = __ldg(q + 2), d = __ldg(q + 3);
-    const uint32_t wv[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, d.x, d.y, d.z, d.w};
+    const uint32_t lo[6] = {a.x, a.y, a.z, a.w, b.x, b.y};      // low bit of each row's entry
+    const uint32_t hi[6] = {b.z, b.w, d.x, d.y, d.z, d.w};      // high bit
     uint32_t r = c == 0 ? h.x : (c == 1 ? h.y : (c == 2 ? h.z : h.w));
-    const uint32_t pat = c * 0x55555555u;
+    const uint32_t flip_lo = (c & 1u) ? 0u : ~0u, flip_hi = (c & 2u) ? 0u : ~0u;
 #pragma unroll
-    for (int k = 0; k < 12; k++) {
-        const int lo = 16 * k;
-        if (lo < (int)in) {
-            const uint32_t x = wv[k] ^ pat;
-            uint32_t m = ~(x | (x >> 1)) & 0x55555555u;
-            const int left = (int)in - lo;
-            if (left < 16) m &= (1u << (2 * left)) - 1u;
+    for (int k = 0; k < 6; k++) {
+        const int first = 32 * k;
+        if (first < (int)in) {
+            uint32_t m = (lo[k] ^ flip_lo) & (hi[k] ^ flip_hi);      // rows of this word holding c
+            const int left = (int)in - first;
+            if (left < 32) m &= (1u << left) - 1u;
             r += __popc(m);
         }
     }

@@ -8,9 +8,12 @@
 // in position order).  That order is exact for every pattern of up to 32 bases.
 //  - sa[row]: the suffix's position (row 0 is the empty suffix at L);
 //  - occ: 16 words per chunk of 192 rows: the counts of A, C, G, T among the
-//    BWT entries of the rows before the chunk, then the chunk's 192 BWT entries
-//    at 2 bits (entry of row i = the base before suffix sa[i]; the row of
-//    suffix 0 stores 0 and is not counted: its entry is the terminator);
+//    BWT entries of the rows before the chunk, then the chunk's 192 two-bit BWT
+//    entries as two bit planes of 6 words each (words 4..9 the low bits, 10..15
+//    the high bits; bit k of word w is row 32w + k of the chunk), so the rows
+//    holding one base are one mask per 32 rows (entry of row i = the base before
+//    suffix sa[i]; the row of suffix 0 stores 0 and is not counted: its entry is
+//    the terminator);
 //  - C[c]: the first row of the suffixes that start with base c;
 //  - lut[P]: the row interval [lo, hi) of the suffixes that start with the
 //    12-base pattern P (first base most significant).
@@ -143,7 +146,8 @@ inline void build_seed_index(const uint32_t* w, uint64_t L, SeedHostIndex& H) {
                     chunk_cnt[c * 4 + b2]++;
                 }
                 const uint64_t in = i - c * kChunkRows;
-                H.occ[c * 16 + 4 + in / 16] |= b2 << (2 * (in % 16));
+                H.occ[c * 16 + 4 + in / 32] |= (b2 & 1u) << (in % 32);         // low bit plane
+                H.occ[c * 16 + 10 + in / 32] |= (b2 >> 1) << (in % 32);        // high bit plane
             }
         }
     });

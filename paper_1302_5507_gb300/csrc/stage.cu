@@ -523,15 +523,6 @@ __device__ __forceinline__ uint32_t band_nibble(const uint32_t* __restrict__ are
     return (word >> (4 * (k & 7))) & 15u;
 }
 
-__device__ __forceinline__ int32_t rect_height(const uint32_t* __restrict__ arena, uint64_t off, int L, int K,
-                                               int pad, int i, int j) {
-    const int idx = j - 1 + pad;
-    const int g = idx / K, r = idx - g * K;
-    const int s = i - 1 + g;                 // the step at which lane g computed column i
-    const uint32_t word = arena[off + ((uint64_t)s * ((K + 3) / 4) + (r >> 2)) * L + g];
-    return (int32_t)((word >> (8 * (r & 3))) & 255u);
-}
-
 __global__ void k_traceback(const sa_job* __restrict__ jobs, uint32_t job_begin, uint32_t n_jobs,
                             const JobState* __restrict__ state, const Rect* __restrict__ rect,
                             const uint32_t* __restrict__ arena, BandLayout band, int wave, int mode,
@@ -590,10 +581,26 @@ __global__ void k_traceback(const sa_job* __restrict__ jobs, uint32_t job_begin,
         const uint32_t* refw = hw.ref + kRefFrontPad;
         const uint32_t* rp = hw.rpack + (size_t)job * hw.rw;
         const int64_t col0 = (int64_t)J.ref_pos + R.i_lo - 2;     // reference position of rectangle column 0
+        // row jj's lane g and row r in it (idx = jj - 1 + pad = g*K + r), kept for the
+        // last row asked: the walk's scans stay on one row or move one row up
+        int memo_j = -1, memo_g = 0, memo_r = 0;
+        const int KH = (K + 3) / 4;
         auto height = [&](int ii, int jj) -> int32_t {
             if (ii < 0 || jj < 0 || ii > R.w || jj > R.rows) return kNeg32;
             if (ii == 0 || jj == 0) return 0;
-            return rect_height(arena, off, L, K, pad, ii, jj);
+            if (jj != memo_j) {
+                if (jj == memo_j - 1) {
+                    if (--memo_r < 0) { memo_r = K - 1; memo_g--; }
+                } else {
+                    const int idx = jj - 1 + pad;
+                    memo_g = idx / K;
+                    memo_r = idx - memo_g * K;
+                }
+                memo_j = jj;
+            }
+            const int s = ii - 1 + memo_g;       // the step at which lane g computed column ii
+            const uint32_t word = arena[off + ((uint64_t)s * KH + (memo_r >> 2)) * L + memo_g];
+            return (int32_t)((word >> (8 * (memo_r & 3))) & 255u);
         };
         auto match = [&](int ii, int jj) -> bool {
             const int64_t p = col0 + ii;

@@ -91,7 +91,8 @@ int main(int argc, char** argv) {
         const uint32_t chunk = i / sa::kChunkRows, in = i - chunk * sa::kChunkRows;
         uint32_t r = H.occ[chunk * 16 + c];
         for (uint32_t k = 0; k < in; k++) {
-            const uint32_t e = (H.occ[chunk * 16 + 4 + k / 16] >> (2 * (k % 16))) & 3u;
+            const uint32_t e = ((H.occ[chunk * 16 + 4 + k / 32] >> (k % 32)) & 1u) |
+                               (((H.occ[chunk * 16 + 10 + k / 32] >> (k % 32)) & 1u) << 1);
             const uint32_t row = chunk * sa::kChunkRows + k;
             if (e == c && row != H.dollar_row) r++;
         }
