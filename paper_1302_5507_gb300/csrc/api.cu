@@ -664,10 +664,11 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             // --- reduced traceback: banded direction pass for most jobs, the
             // wavefront rectangle pass (in arena waves) for wide bands, then the walk
             // band lists, then the compacted list of the rectangle pass's jobs
-            TRY(ws.blists.ensure((size_t)n_jobs * (kNumBand + 1) * 4, "band lists"));
+            TRY(ws.blists.ensure((size_t)n_jobs * (kNumBand + 2) * 4, "band lists"));
             uint32_t* lists[kNumBand];
             for (int k = 0; k < kNumBand; k++) lists[k] = ws.blists.as<uint32_t>() + (size_t)k * n_jobs;
             uint32_t* rect_list = ws.blists.as<uint32_t>() + (size_t)kNumBand * n_jobs;
+            uint32_t* rect_list_pos = ws.blists.as<uint32_t>() + (size_t)(kNumBand + 1) * n_jobs;
             nvtx.next("traceback classes");
             // the results' count and offset arrays serve as the rectangle flags and
             // their scan here (the results phase rewrites them)
@@ -683,7 +684,7 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
                             ws.bsum.as<uint64_t>(), &dp->totals[0], st);
             launch_scan_u32(rect_flag, n_jobs, rect_pos, ws.bsum.as<uint64_t>(), &dp->totals[2], st);
             launch_rect_list(ws.order.as<uint32_t>(), n_jobs, rect_flag, rect_pos, dp->cfg_begin, &dp->totals[2],
-                             rect_list, dp->rect_begin, st);
+                             rect_list, rect_list_pos, dp->rect_begin, st);
             launches += 9;
             CU(cudaGetLastError());
             trace("rect plan + scan");
@@ -764,8 +765,8 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
                 wave_words = arena_words - item_max;
             }
             TRY(ws.arena.ensure(arena_words * 4, "direction arena"));
-            launch_rect_assign(ws.order.as<uint32_t>(), n_jobs, ws.offs.as<uint64_t>(), dp->cfg_begin,
-                               wave_words, ws.rect.as<Rect>(), &dp->st.max_wave, st);
+            launch_rect_assign(ws.order.as<uint32_t>(), rect_list_pos, hp->rect_begin[kNumCfg],
+                               ws.offs.as<uint64_t>(), wave_words, ws.rect.as<Rect>(), &dp->st.max_wave, st);
             launches++;
             const uint32_t waves = wave_words ? (uint32_t)((total_words + wave_words - 1) / wave_words) : 1;
             stats.waves = total_words ? waves : 0;

@@ -69,17 +69,16 @@ void launch_rect_plan(const sa_job* jobs, const uint32_t* order, uint32_t n_pos,
                       Rect* rect, uint64_t* sizes, uint32_t* const* lists, uint32_t* cls_count,
                       uint32_t* rect_flag, int heights, cudaStream_t st);
 // the rectangle-pass jobs compacted in bucketed order (rect_pos = exclusive scan of
-// rect_flag, total its sum) and each bucket's first index in the list
-// (rect_begin[kNumCfg + 1])
+// rect_flag, total its sum), their positions in that order (list_pos), and each
+// bucket's first index in the list (rect_begin[kNumCfg + 1])
 void launch_rect_list(const uint32_t* order, uint32_t n_pos, const uint32_t* rect_flag, const uint64_t* rect_pos,
-                      const uint32_t* cfg_begin, const uint64_t* total, uint32_t* list, uint32_t* rect_begin,
-                      cudaStream_t st);
+                      const uint32_t* cfg_begin, const uint64_t* total, uint32_t* list, uint32_t* list_pos,
+                      uint32_t* rect_begin, cudaStream_t st);
 // heights: the byte-height form (LOCAL and every score below 255; the band
 // regions then hold B/4 words a row instead of B/8)
 void launch_band(int cls, const BandArgs& a, bool heights, cudaStream_t st);
-void launch_rect_assign(const uint32_t* order, uint32_t n_pos, const uint64_t* offs,
-                        const uint32_t* cfg_begin, uint64_t wave_words, Rect* rect,
-                        uint32_t* max_wave, cudaStream_t st);
+void launch_rect_assign(const uint32_t* order, const uint32_t* list_pos, uint32_t n, const uint64_t* offs,
+                        uint64_t wave_words, Rect* rect, uint32_t* max_wave, cudaStream_t st);
 void launch_plain_rect(const sa_job* jobs, uint32_t j0, uint32_t nb, uint64_t stride, Rect* rect,
                        cudaStream_t st);
 void launch_scan_u64(const uint64_t* in, uint64_t n, uint64_t* out, uint64_t* bsum, uint64_t* total,

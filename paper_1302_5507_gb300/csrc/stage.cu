@@ -196,54 +196,77 @@ void launch_collect_overflow(const uint32_t* order, uint32_t n_pos, const JobSta
 }
 
 // ---------------------------------------------------------------------------
-// read packing: one warp per job; the lanes read 32 consecutive bases at a time
-// (coalesced) and two OR-reductions over half-warps form two 16-base words
+// read packing: one thread per 16-base output word.  The thread loads the (at
+// most five) aligned 32-bit words that hold its 16 source bytes, lines them up
+// with funnel shifts, and converts four bytes at a time: the 2-bit code of an
+// A/C/G/T byte (either case) is ((x >> 1) ^ (x >> 2)) & 3, and the byte is valid
+// when it equals the character its code names ("acgt", looked up with a byte
+// permute) once lower-cased.  A reverse-complemented job's word is the forward
+// packing of the mirrored source bytes with its 2-bit fields reversed and
+// complemented.
+
+__device__ __forceinline__ uint32_t pack4_codes(uint32_t x, uint32_t* bad_bytes) {
+    const uint32_t c = ((x >> 1) ^ (x >> 2)) & 0x03030303u;          // code of each byte
+    // the selector c0 | c1<<4 | c2<<8 | c3<<12 from the code bytes, then "acgt"[code]
+    const uint32_t sel = __byte_perm(c | (c >> 4), 0u, 0x4420);
+    const uint32_t want = __byte_perm(0x74676361u, 0u, sel);
+    *bad_bytes = (x | 0x20202020u) ^ want;                          // nonzero bytes: not ACGTacgt
+    // the four codes side by side in the top byte (the other products stay below it)
+    return c * 0x01041040u;
+}
 
 __global__ void k_pack_reads(const sa_job* __restrict__ jobs, uint32_t n_jobs,
                              const uint8_t* __restrict__ reads, uint32_t* __restrict__ rpack,
                              uint32_t rw, unsigned* bad_job) {
-    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= n_jobs) return;              // whole warps
-    const sa_job J = jobs[warp];
-    const uint32_t n = J.read_len;
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t job = (uint32_t)(t / rw), w = (uint32_t)(t % rw);
+    if (job >= n_jobs) return;
+    const sa_job J = jobs[job];
+    const int n = (int)J.read_len;
+    if (16 * (int)w >= n) return;                    // past the read: never read by the passes
     const bool rc = (J.flags & SA_RC) != 0u;
-    const uint8_t* r = reads + J.read_off;
-    uint32_t* out = rpack + (size_t)warp * rw;
-    bool bad = false;
-    // chunks of 32 bases; the loads of up to 8 chunks are issued before any
-    // reduction, so a job waits for one memory latency instead of one per chunk
-    for (uint32_t b0 = 0; b0 < n; b0 += 256) {
-        uint8_t ch[8];
+    // the source bytes of this word: forward [16w, 16w + cnt), reverse-complemented
+    // the mirror image [n - 16w - cnt, n - 16w)
+    const int cnt = min(16, n - 16 * (int)w);
+    const int lo = rc ? n - 16 * (int)w - cnt : 16 * (int)w;
+    const uint8_t* src = reads + J.read_off + lo;
+    const uint32_t mis = (uint32_t)((uintptr_t)src & 3u);
+    const uint32_t* wp = reinterpret_cast<const uint32_t*>((uintptr_t)src - mis);
+    const int nw = (int)((mis + (uint32_t)cnt + 3u) >> 2);       // aligned words holding the bytes
+    uint32_t q[5];
 #pragma unroll
-        for (int t = 0; t < 8; t++) {
-            const uint32_t p = b0 + 32u * t + (uint32_t)lane;
-            ch[t] = p < n ? (rc ? r[n - 1 - p] : r[p]) : (uint8_t)'A';
-        }
+    for (int k = 0; k < 5; k++) q[k] = k < nw ? __ldg(wp + k) : 0u;
+    uint32_t top[4], badw = 0u;
 #pragma unroll
-        for (int t = 0; t < 8; t++) {
-            const uint32_t b = b0 + 32u * t;
-            if (b >= n) break;                   // warp-uniform
-            int cc = base_code(ch[t]);
-            if (cc < 0) { bad = true; cc = 0; }
-            if (rc) cc = 3 - cc;                 // complement: A<->T, C<->G
-            const uint32_t c = b + (uint32_t)lane < n ? (uint32_t)cc : 0u;
-            const uint32_t v = c << (2 * (lane & 15));
-            const uint32_t lo = __reduce_or_sync(0xffffffffu, lane < 16 ? v : 0u);
-            const uint32_t hi = __reduce_or_sync(0xffffffffu, lane < 16 ? 0u : v);
-            if (lane == 0) out[b / 16] = lo;
-            if (lane == 1 && b + 16 < n) out[b / 16 + 1] = hi;
-        }
+    for (int k = 0; k < 4; k++) {
+        const uint32_t x = __funnelshift_r(q[k], q[k + 1], 8u * mis);   // bytes 4k .. 4k+3
+        uint32_t bb;
+        top[k] = pack4_codes(x, &bb);
+        // only bytes j < cnt are the read's
+        const int left = cnt - 4 * k;
+        const uint32_t keep = left >= 4 ? 0xFFFFFFFFu : (left <= 0 ? 0u : (1u << (8 * left)) - 1u);
+        badw |= bb & keep;
     }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicMin(bad_job, warp);
+    // codes of bytes 0..15 at bits 2j
+    uint32_t v = __byte_perm(__byte_perm(top[0], top[1], 0x0073), __byte_perm(top[2], top[3], 0x0073), 0x5410);
+    if (cnt < 16) v &= (1u << (2 * cnt)) - 1u;
+    if (rc) {
+        // field j -> field cnt-1-j, complemented: reverse all 32 bits, swap each
+        // field's two bits back, drop the fields past cnt, flip the codes (3 - c)
+        uint32_t r = __brev(v);
+        r = ((r >> 1) & 0x55555555u) | ((r & 0x55555555u) << 1);
+        r >>= 2 * (16 - cnt);
+        v = r ^ (cnt < 16 ? (1u << (2 * cnt)) - 1u : 0xFFFFFFFFu);
+    }
+    rpack[(size_t)job * rw + w] = v;
+    if (badw) atomicMin(bad_job, job);
 }
 
 void launch_pack_reads(const sa_job* jobs, uint32_t n_jobs, const uint8_t* reads, uint32_t* rpack,
                        uint32_t rw, unsigned* bad_job, cudaStream_t st) {
     if (!n_jobs) return;
-    const uint64_t threads = (uint64_t)n_jobs * 32;
-    k_pack_reads<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(jobs, n_jobs, reads, rpack, rw,
-                                                                      bad_job);
+    const uint64_t threads = (uint64_t)n_jobs * rw;
+    k_pack_reads<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(jobs, n_jobs, reads, rpack, rw, bad_job);
 }
 
 struct BandLists { uint32_t* p[kNumBand]; };
@@ -352,9 +375,13 @@ __global__ void k_rect_plan(const sa_job* __restrict__ jobs, const uint32_t* __r
 // the jobs of the wavefront rectangle pass, in the bucketed order (rect_pos is
 // the exclusive scan of rect_flag), and where each bucket's run of them begins
 __global__ void k_rect_list(const uint32_t* __restrict__ order, uint32_t n_pos, const uint32_t* __restrict__ rect_flag,
-                            const uint64_t* __restrict__ rect_pos, uint32_t* __restrict__ list) {
+                            const uint64_t* __restrict__ rect_pos, uint32_t* __restrict__ list,
+                            uint32_t* __restrict__ list_pos) {
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < n_pos && rect_flag[p]) list[rect_pos[p]] = order[p];
+    if (p < n_pos && rect_flag[p]) {
+        list[rect_pos[p]] = order[p];
+        list_pos[rect_pos[p]] = p;
+    }
 }
 __global__ void k_rect_bounds(const uint64_t* __restrict__ rect_pos, uint32_t n_pos,
                               const uint32_t* __restrict__ cfg_begin, const uint64_t* total,
@@ -363,10 +390,10 @@ __global__ void k_rect_bounds(const uint64_t* __restrict__ rect_pos, uint32_t n_
     if (c <= kNumCfg) rect_begin[c] = cfg_begin[c] < n_pos ? (uint32_t)rect_pos[cfg_begin[c]] : (uint32_t)*total;
 }
 void launch_rect_list(const uint32_t* order, uint32_t n_pos, const uint32_t* rect_flag, const uint64_t* rect_pos,
-                      const uint32_t* cfg_begin, const uint64_t* total, uint32_t* list, uint32_t* rect_begin,
-                      cudaStream_t st) {
+                      const uint32_t* cfg_begin, const uint64_t* total, uint32_t* list, uint32_t* list_pos,
+                      uint32_t* rect_begin, cudaStream_t st) {
     if (!n_pos) return;
-    k_rect_list<<<(n_pos + 255) / 256, 256, 0, st>>>(order, n_pos, rect_flag, rect_pos, list);
+    k_rect_list<<<(n_pos + 255) / 256, 256, 0, st>>>(order, n_pos, rect_flag, rect_pos, list, list_pos);
     k_rect_bounds<<<1, 64, 0, st>>>(rect_pos, n_pos, cfg_begin, total, rect_begin);
 }
 
@@ -382,31 +409,28 @@ void launch_rect_plan(const sa_job* jobs, const uint32_t* order, uint32_t n_pos,
                                                       heights);
 }
 
-// wave assignment: a job belongs to the wave of its first direction word, so its
+// wave assignment of the rectangle jobs (their positions in the bucketed order,
+// list_pos[0 .. n)): a job belongs to the wave of its first direction word, so its
 // words fit the arena slack (cap - wave words >= the largest job).
-__global__ void k_rect_assign(const uint32_t* __restrict__ order, uint32_t n_pos,
-                              const uint64_t* __restrict__ offs, const uint32_t* __restrict__ cfg_begin,
-                              uint64_t wave_words, Rect* __restrict__ rect, uint32_t* max_wave) {
-    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n_pos) return;
+__global__ void k_rect_assign(const uint32_t* __restrict__ order, const uint32_t* __restrict__ list_pos,
+                              uint32_t n, const uint64_t* __restrict__ offs, uint64_t wave_words,
+                              Rect* __restrict__ rect, uint32_t* max_wave) {
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const uint32_t p = list_pos[q];
     const uint32_t job = order[p];
-    // the wave of the job's first word; a job's words (at most one item) fit the
-    // arena's slack past the wave's share
-    (void)cfg_begin;
     const uint64_t wv = wave_words ? offs[p] / wave_words : 0;
     Rect R = rect[job];
     R.wave = (int)wv;
     R.off = offs[p] - wv * wave_words;
     rect[job] = R;
-    if (R.w > 0) atomicMax(max_wave, (uint32_t)wv);
+    atomicMax(max_wave, (uint32_t)wv);
 }
 
-void launch_rect_assign(const uint32_t* order, uint32_t n_pos, const uint64_t* offs,
-                        const uint32_t* cfg_begin, uint64_t wave_words, Rect* rect,
-                        uint32_t* max_wave, cudaStream_t st) {
-    if (!n_pos) return;
-    k_rect_assign<<<(n_pos + 255) / 256, 256, 0, st>>>(order, n_pos, offs, cfg_begin, wave_words,
-                                                        rect, max_wave);
+void launch_rect_assign(const uint32_t* order, const uint32_t* list_pos, uint32_t n, const uint64_t* offs,
+                        uint64_t wave_words, Rect* rect, uint32_t* max_wave, cudaStream_t st) {
+    if (!n) return;
+    k_rect_assign<<<(n + 255) / 256, 256, 0, st>>>(order, list_pos, n, offs, wave_words, rect, max_wave);
 }
 
 // ---------------------------------------------------------------------------
