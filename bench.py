@@ -328,7 +328,7 @@ def run_reference(args, rank, world):
 
 def roofline_of(cells, fill_ms, packed, dpx, sm_mhz, n_sm, config, jobs):
     """Roofline of the score pass (the dominant kernel family): achieved cells per
-    second over the score-pass phase, against (1) the survey's formula, 6 DPX
+    second over the score-pass phase, against (1) a cell-count formula, 6 DPX
     lane-ops per cell at the measured DPX rate, and (2) an issue-aware bound: the
     half-rate instructions the recurrence needs per register of cells (5.5), at the
     measured rate of add-maxima and multiply-adds interleaved (the two pipes share
