@@ -155,3 +155,41 @@ def test_full_size_serving_reference(sa):
                 bad = compare(res, cig, ores[sl], oops[sl])
                 assert not bad, "\n".join(bad[:10])
                 first += r.n_jobs
+
+
+def test_admission_follows_device_memory(sa):
+    """Admission re-reads the device's free memory: with almost all of it taken
+    by another allocation of the process after the server started, a request
+    waits instead of failing; once the memory is released it runs and its
+    results match the oracle."""
+    import torch
+    genome = workloads.genome(seed=6, length=2_000_000)
+    # 20,000 serving-shaped jobs: an estimate of several GB (the rectangle arena is
+    # charged at its largest), far above what is left free below
+    r = workloads.serving_request(genome, 6, 0, 20_000)
+    jobs = sa.jobs_array(r.read_off, r.read_len, r.flags, r.ref_pos, r.win_len)
+    with sa.Reference(genome) as ref, sa.Server(ref, max_inflight=1) as srv:
+        torch.cuda.synchronize()
+        hog = []
+        free, _ = torch.cuda.mem_get_info()
+        chunk = 1 << 30
+        while free > (256 << 20) and chunk >= (8 << 20):     # leave less than 256 MB free
+            try:
+                hog.append(torch.empty(min(chunk, free - (128 << 20)), dtype=torch.uint8, device="cuda"))
+            except RuntimeError:
+                chunk //= 2
+            free, _ = torch.cuda.mem_get_info()
+        try:
+            tk = srv.submit(jobs, r.reads)
+            rc, _, _ = srv.poll(tk, r.n_jobs, sa.cigar_max_ops(r.read_len), timeout_ms=300)
+            assert rc in (sa.SA_ETIMEOUT, sa.SA_PENDING)      # held back, not failed
+        finally:
+            del hog
+            torch.cuda.empty_cache()
+        rc, res, cig = srv.poll(tk, r.n_jobs, sa.cigar_max_ops(r.read_len), timeout_ms=-1)
+        assert rc == sa.SA_OK
+        ores, oops = oracle.align(r)
+        bad = compare(res, cig, ores, oops)
+        assert not bad, "\n".join(bad[:10])
+        st = srv.stats()
+        assert st["admission_stalls"] >= 1 and st["failed"] == 0
