@@ -1,8 +1,8 @@
 """Bounds-checked build (SA_DEBUG): every indexed global store of the kernels
 checks its index against its buffer and reports an out-of-range store as an
 internal error.  The checked library must give the oracle's results on every
-path (both widths, both modes, both forms, every traceback class) without
-reporting a store."""
+path (both widths, both modes, both forms, every traceback class, the rectangle
+arena in waves) without reporting a store."""
 import os
 import subprocess
 import sys
@@ -35,6 +35,10 @@ for wl in cases:
                 res, cig = ref.align(jobs, wl.reads, sa.make_params(mode=mode, form=form, width=width))
                 bad = compare(res, cig, ores, oops)
                 assert not bad, (wl.name, mode, form, width, bad[:5])
+            # the rectangle arena capped so that its passes and walks run in waves
+            res, cig = ref.align(jobs, wl.reads, sa.make_params(mode=mode, arena_mb=4))
+            bad = compare(res, cig, ores, oops)
+            assert not bad, (wl.name, mode, "waves", bad[:5])
 print("bounds-checked build: all cases exact")
 """.replace("ROOT", repr(ROOT))
 
