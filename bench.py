@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--jobs", type=int, default=None,
                     help="jobs per GPU (default: the configuration's size, 4M for c3, 1M for c2)")
     ap.add_argument("--no-tune", action="store_true", help="keep the default plan (skip sa_tune)")
+    ap.add_argument("--width", type=int, default=None, choices=[0, 16, 32],
+                    help="score width of the line's batches (default: 32 for c2, as its spec says; "
+                         "0 = 16-bit pairs where no job of a bucket can overflow, for c3)")
     ap.add_argument("--no-c2", action="store_true", help="skip the mate-rescue object of the headline line")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving latency run")
@@ -184,7 +187,10 @@ def direction_bound(stats, wl):
 
 PROBE_OPS = ("viaddmax_s32", "vimax3_s32", "vimax3_s32_relu", "iadd_s32", "imax_s32", "imad_s32",
              "viaddmax_s16x2", "vimax3_s16x2", "prmt", "vmaxs4 (s8x4)", "vaddss4 (s8x4)",
-             "viaddmax_s16x2 + imad (half the chains each)", "viaddmax_s16x2 + prmt (half the chains each)")
+             "viaddmax_s16x2 + imad (half the chains each)", "viaddmax_s16x2 + prmt (half the chains each)",
+             "lop3", "iadd3", "ffma (fp32)", "hmax2 (fp16x2)",
+             "viaddmax_s16x2 + lop3", "viaddmax_s16x2 + iadd3", "viaddmax_s16x2 + ffma",
+             "viaddmax_s16x2 + hmax2", "viaddmax_s16x2 + funnel shift")
 
 
 def probe_all_ops():
@@ -373,7 +379,8 @@ def run_ours(args, rank, world, dist):
     wl = make_workload(config, rank, args.jobs or DEFAULT_JOBS[config])
     jobs = sa.jobs_array(wl.read_off, wl.read_len, wl.flags, wl.ref_pos, wl.win_len)
     ref = sa.Reference(wl.ref, device=local_rank)
-    width = 32 if config == "c2" else 0           # C2's scores are int32; C3 packs 16-bit pairs
+    # C2's scores are int32; C3 packs 16-bit pairs
+    width = args.width if args.width is not None else (32 if config == "c2" else 0)
     tuned = None
     if config == "c3" and not args.no_tune:
         # the plan (configuration per read length, width per configuration) from the
@@ -492,7 +499,9 @@ def run_ours(args, rank, world, dist):
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "s16x2" if packed else "int32",
                 "data": "synthetic",
-                "config": {"workload": WORKLOADS[config], "jobs_per_gpu": wl.n_jobs, "cells_per_gpu": cells_rank,
+                "config": {"workload": WORKLOADS[config] + ("" if args.width is None else
+                                                            f" (run at width {width or 'auto'})"),
+                           "jobs_per_gpu": wl.n_jobs, "cells_per_gpu": cells_rank,
                            "mode": "LOCAL", "scoring": "match 1, mismatch 2, gap open 2, gap extend 1",
                            "width": width or "auto (16-bit pairs where no job of a bucket can overflow)",
                            "plan": "autotuned (sa_tune)" if tuned else "default",

@@ -224,14 +224,16 @@ int check_params(const sa_params* p, Score* sc) {
     return SA_OK;
 }
 
-// The 16-bit packed score pass serves LOCAL alignment: with match <= 2047 and
-// mismatch, gap open + extend <= 16383 every value it forms below its overflow
-// threshold fits a signed 16-bit half (see fill16.cuh); jobs that reach the
-// threshold are flagged and recomputed by the 32-bit pass.
+// The 16-bit packed score pass serves LOCAL alignment of schemes with
+// match + B < 1024, B = max(gap open + extend, mismatch): it holds 32 (H + B) in a
+// signed 16-bit half, exact below its overflow threshold H + B = 1024 - match (see
+// fill16.cuh); jobs that reach the threshold are flagged and recomputed by the
+// 32-bit pass, and other schemes run the 32-bit pass.
 bool use16(const sa_params* P) {
     if (P->mode != SA_LOCAL || P->width == 32 || P->form == SA_FORM_PLAIN) return false;
     const sa_scoring& s = P->sc;
-    return s.match <= 2047 && s.mismatch <= 16383 && (int64_t)s.gap_open + s.gap_extend <= 16383;
+    const int64_t B = std::max<int64_t>((int64_t)s.gap_open + s.gap_extend, s.mismatch);
+    return s.match + B < 1024;
 }
 
 int ensure_side(Workspace& ws) {
@@ -412,12 +414,13 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
     };
     // 16-bit pairs per length bucket: when asked for (width 16 in the parameters or
     // the plan), or by default when no job of the bucket can reach the 16-bit
-    // threshold (a * rows + beta < 1024 - a)
+    // threshold (a * rows + B < 1024 - a)
     bool w16[kNumCfg] = {};
     bool any16 = false;
     for (int c = 0; c < kNumCfg; c++) {
         const int64_t rows = (int64_t)cfg_L(c) * cfg_K(c);
-        const bool safe = (int64_t)P->sc.match * (rows + 1) + P->sc.gap_open + P->sc.gap_extend < 1024;
+        const int64_t B = std::max<int64_t>((int64_t)P->sc.gap_open + P->sc.gap_extend, P->sc.mismatch);
+        const bool safe = (int64_t)P->sc.match * (rows + 1) + B < 1024;
         const int pw = X.plan ? X.plan->width[c] : 0;
         const bool want16 = P->width == 16 || (P->width == 0 && (pw == 16 || (pw == 0 && safe)));
         w16[c] = !plain && cfg_count[c] && use16(P) && want16;
@@ -1708,8 +1711,8 @@ RefView ref_view(const sa_reference* R) {
 
 // Scores and mode of every alignment entry point.  The limits keep each kernel
 // exact: a LOCAL best score must fit 21 bits (the 32-bit score pass forms keys
-// H * 1024 + row tag in an int32), and every 16-bit value below the overflow
-// threshold of the packed pass must fit a signed half.
+// H * 1024 + row tag in an int32); the 16-bit pass takes the schemes it holds
+// exactly and leaves the rest to the 32-bit pass.
 int check_scoring(const sa_params* p, Score* sc) {
     if (!p) return fail(SA_EINVAL, "params is NULL");
     const sa_scoring& s = p->sc;

@@ -7,11 +7,19 @@
 // number the ALU roofline of the score pass is built from.  Used by bench.py;
 // not part of the alignment interface.
 #include <cstdint>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace {
 
 constexpr int kChains = 8;
+
+// max of two fp16x2 values held as bit patterns
+__device__ __forceinline__ uint32_t hmax2_bits(uint32_t a, uint32_t b) {
+    __half2 ha = *reinterpret_cast<__half2*>(&a), hb = *reinterpret_cast<__half2*>(&b);
+    __half2 r = __hmax2(ha, hb);
+    return *reinterpret_cast<uint32_t*>(&r);
+}
 
 enum Op {
     kViaddmaxS32 = 0, kVimax3S32 = 1, kVimax3ReluS32 = 2, kIaddS32 = 3, kImaxS32 = 4, kImadS32 = 5,
@@ -20,15 +28,20 @@ enum Op {
     // half the chains one operation, half another: whether the two issue side by side
     kMixAddmaxImad = 11,                           // __viaddmax_s16x2 (ALU pipe) + IMAD (FMA pipe)
     kMixAddmaxPrmt = 12,                           // __viaddmax_s16x2 + PRMT (both ALU pipe)
-    kNumOps = 13
+    kLop3 = 13, kIadd3 = 14, kFfma = 15, kHmax2 = 16,   // alone: 3-input logic, 3-input add, fp32 FMA, fp16x2 max
+    kMixAddmaxLop3 = 17, kMixAddmaxIadd3 = 18, kMixAddmaxFfma = 19, kMixAddmaxHmax2 = 20,
+    kMixAddmaxShf = 21,                            // __viaddmax_s16x2 + funnel shift
+    kNumOps = 22
 };
 
 template <int OP>
 __global__ void __launch_bounds__(256) k_probe(int iters, uint32_t seed, uint32_t* sink) {
     uint32_t x[kChains], y = seed ^ threadIdx.x, z = seed * 3u + 7u;
+    float xf[kChains];
+    const float af = 1.0f + 1e-7f * (float)(seed & 7u), bf = 1e-3f * (float)threadIdx.x;
     const uint32_t one = blockDim.x >> 8;          // 1 at run time
 #pragma unroll
-    for (int c = 0; c < kChains; c++) x[c] = seed + c * 977u + threadIdx.x;
+    for (int c = 0; c < kChains; c++) { x[c] = seed + c * 977u + threadIdx.x; xf[c] = (float)x[c]; }
     for (int it = 0; it < iters; it++) {
 #pragma unroll
         for (int rep = 0; rep < 16; rep++) {
@@ -49,13 +62,27 @@ __global__ void __launch_bounds__(256) k_probe(int iters, uint32_t seed, uint32_
                     x[c] = (c & 1) ? x[c] * one + y : __viaddmax_s16x2(x[c], y, z);
                 if (OP == kMixAddmaxPrmt)
                     x[c] = (c & 1) ? __byte_perm(x[c], y, 0x5410 + c) : __viaddmax_s16x2(x[c], y, z);
+                if (OP == kLop3) x[c] = (x[c] & y) ^ (z | ~x[c]);
+                if (OP == kIadd3) x[c] = x[c] + x[(c + 1) % kChains] + y;
+                if (OP == kFfma) xf[c] = fmaf(xf[c], af, bf);
+                if (OP == kHmax2) x[c] = hmax2_bits(x[c], x[(c + 1) % kChains]);
+                if (OP == kMixAddmaxLop3)
+                    x[c] = (c & 1) ? ((x[c] & y) ^ (z | ~x[c])) : __viaddmax_s16x2(x[c], y, z);
+                if (OP == kMixAddmaxIadd3) x[c] = (c & 1) ? x[c] + x[(c + 1) % kChains] + y : __viaddmax_s16x2(x[c], y, z);
+                if (OP == kMixAddmaxFfma) {
+                    if (c & 1) xf[c] = fmaf(xf[c], af, bf);
+                    else x[c] = __viaddmax_s16x2(x[c], y, z);
+                }
+                if (OP == kMixAddmaxHmax2) x[c] = (c & 1) ? hmax2_bits(x[c], x[(c + 1) % kChains]) : __viaddmax_s16x2(x[c], y, z);
+                if (OP == kMixAddmaxShf)
+                    x[c] = (c & 1) ? __funnelshift_l(x[c], y, (z + c) & 31u) : __viaddmax_s16x2(x[c], y, z);
             }
             y += 1;
         }
     }
     uint32_t acc = 0;
 #pragma unroll
-    for (int c = 0; c < kChains; c++) acc ^= x[c];
+    for (int c = 0; c < kChains; c++) acc ^= x[c] ^ __float_as_uint(xf[c]);
     if (acc == 0x9E3779B9u) sink[threadIdx.x] = acc;     // keeps the chains alive
 }
 
@@ -102,6 +129,15 @@ extern "C" double sa_probe_ops_per_sm_clk(int op, double sm_mhz) {
     case kVaddS8x4: ms = run<kVaddS8x4>(blocks, iters, sink); break;
     case kMixAddmaxImad: ms = run<kMixAddmaxImad>(blocks, iters, sink); break;
     case kMixAddmaxPrmt: ms = run<kMixAddmaxPrmt>(blocks, iters, sink); break;
+    case kLop3: ms = run<kLop3>(blocks, iters, sink); break;
+    case kIadd3: ms = run<kIadd3>(blocks, iters, sink); break;
+    case kFfma: ms = run<kFfma>(blocks, iters, sink); break;
+    case kHmax2: ms = run<kHmax2>(blocks, iters, sink); break;
+    case kMixAddmaxLop3: ms = run<kMixAddmaxLop3>(blocks, iters, sink); break;
+    case kMixAddmaxIadd3: ms = run<kMixAddmaxIadd3>(blocks, iters, sink); break;
+    case kMixAddmaxFfma: ms = run<kMixAddmaxFfma>(blocks, iters, sink); break;
+    case kMixAddmaxHmax2: ms = run<kMixAddmaxHmax2>(blocks, iters, sink); break;
+    case kMixAddmaxShf: ms = run<kMixAddmaxShf>(blocks, iters, sink); break;
     default: break;
     }
     cudaFree(sink);

@@ -2,42 +2,54 @@
 // the low and job B in the high half of every register, updated together with
 // the DPX s16x2 max/add instructions.
 //
-// Representation: every H, E, F value x is stored as x + beta with beta = -S_GO
-// (= o + e), and H additionally carries + S_GO (as in the 32-bit kernel), so the
-// recurrence of SOAP3-dp Methods section 3 becomes, per half,
-//   G  = max(HG(i-1,j-1) + (delta - S_GO), beta)      zero floor of LOCAL folded in
-//   E  = max(E(i,j-1) + S_GE, HG(i,j-1))
-//   F  = max(F(i-1,j) + S_GE, HG(i-1,j))
-//   H  = max(G, E, F),   HG = H + S_GO
-// Every stored H is >= beta, so HG = H + S_GO on both halves is one 32-bit
-// multiply-add with a fixed carry compensation (the FMA pipe), the border values
-// (H = 0 -> HG = 0, E = F = -inf -> 0) are all zero, and all maxima are signed
-// 16-bit DPX operations.
+// Representation: every value is scaled by 32, so its low 5 bits are zero and a
+// row tag fits below it in the best-cell keys.  With beta = o + e (= -S_GO),
+// B = max(beta, mismatch) and c = 32 (B - beta) (0 unless the mismatch costs
+// more than opening a gap), a half holds
+//   X = 32 H + c                                  (H >= 0 in LOCAL)
+//   E~ = 32 (E + B),  F~ = 32 (F + B),  G~ = 32 (H(i-1,j-1) + delta + B)
+// and the recurrence of SOAP3-dp Methods section 3 becomes, per half,
+//   G~ = X(i-1,j-1) + 32 (delta - S_GO)
+//   E~ = max(E~(i,j-1) + 32 S_GE, X(i,j-1))
+//   F~ = max(F~(i-1,j) + 32 S_GE, X(i-1,j))
+//   X  = max(G~, E~, F~) + 32 S_GO                 G~ floored at 32 B: the zero floor of LOCAL
+// The borders are X = c (H = 0) and E~ = F~ = 0 (E = F = -B, below every
+// H + S_GO), and every value is >= 0.
 //
-// Best cell: each cell's key (H + beta) * 32 + (31 - r) (r the row in the lane)
-// is formed with one multiply-add on both halves; a lane keeps the maximum key of
-// its rows per column (the largest H and, among equal H, the first row), stores
-// it at every step (one 128-byte line per warp and step) and passes it down the
-// group, whose last lane stores the group's column maximum.  The epilogue finds
-// the first column i* holding the largest H from the group's column maxima and
-// the first row from the lanes' stored keys of column i*.  (Storing only where a
-// lane's key rises leaves partial sectors that cost the same DRAM traffic as
-// whole lines, plus the rise test on the ALU pipe.)
+// Diagonal term: a byte permute pairs the two jobs' 16-bit profile entries, and
+// G~ = max(X(i-1,j-1) + 32 (delta - S_GO), 32 B) takes the zero floor; then
+// X = max(G~, E~, F~) + 32 S_GO is one 32-bit multiply-add on both halves with a
+// fixed carry compensation (every H~ >= 32 B >= 32 beta, so the low half always
+// carries).  (A form that keeps 32-bit profile entries and forms G~ of both halves
+// with one three-input add, the floor moved to X, needs twice the shared memory;
+// at the resulting occupancy it was slower.)
 //
-// Exact overflow detection: keys are exact while H + beta <= 1023.  A cell's H
-// is at most its diagonal predecessor + a, so while every H + beta so far is
-// below 1024 - a the next one is at most 1023; the first H that reaches the
-// threshold is therefore exact and shows up in the column maxima.  A pair in
-// which either job's maximum (over every column the pair computed) reaches it is
-// flagged (kStOverflow) and both jobs are recomputed by the 32-bit kernel (past
-// the threshold the low half's key can carry into the high half).
+// Best cell: a cell's key is X + (31 - r) (r the row in the lane), formed and
+// folded into the lane's running maximum with one DPX add-max a row; a lane keeps
+// the maximum key of its rows per column (the largest H and, among equal H, the
+// first row), stores it at every step (one 128-byte line per warp and step) and
+// passes it down the group, whose last lane stores the group's column maximum.
+// The epilogue finds the first column i* holding the largest H from the group's
+// column maxima and the first row from the lanes' stored keys of column i*.
+// (Storing only where a lane's key rises leaves partial sectors that cost the
+// same DRAM traffic as whole lines, plus the rise test on the ALU pipe.)
+//
+// Exact overflow detection: values are exact while H + B <= 1023 (32 (H + B) <
+// 2^15).  A cell's H is at most its diagonal predecessor + a, so while every
+// H + B so far is below 1024 - a the next one is at most 1023; the first H that
+// reaches the threshold is therefore exact and shows up in the column maxima.  A
+// pair in which either job's maximum (over every column the pair computed)
+// reaches it is flagged (kStOverflow) and both jobs are recomputed by the 32-bit
+// kernel (past the threshold one half can carry into the other).  The host runs
+// this pass only for schemes with a + B < 1024.
 #pragma once
 
 #include "fill.cuh"
 
 namespace sa {
 
-// words of the per-lane 16-bit profile (two jobs x 4 bases x rows rounded up to 4)
+// words of the per-lane 16-bit profile of a warp (two jobs x 4 bases x rows
+// rounded up to 4)
 template <int K>
 constexpr int prof16_words_per_warp() { return 2 * 4 * ((K + 3) / 4) * 2 * 32; }
 
@@ -48,8 +60,15 @@ __device__ __forceinline__ int32_t lo16(uint32_t v) { return (int32_t)(int16_t)(
 __device__ __forceinline__ int32_t hi16(uint32_t v) { return (int32_t)(int16_t)(v >> 16); }
 __device__ __forceinline__ int32_t half16(uint32_t v, int h) { return h ? hi16(v) : lo16(v); }
 
+// resident 128-thread blocks a SM asked of the register allocator: rows 25-28
+// then fit four blocks in 128 registers (their profiles take 56 KB a block);
+// elsewhere (0: no request) the allocator's own choice reaches the same occupancy
+// with a faster schedule
+template <int K>
+constexpr int fill16_min_blocks() { return (K >= 25 && K <= 28) ? 4 : 0; }
+
 template <int L, int K>
-__global__ void __launch_bounds__(128) k_fill16(FillArgs A) {
+__global__ void __launch_bounds__(128, fill16_min_blocks<K>()) k_fill16(FillArgs A) {
     static_assert(32 % L == 0, "L must divide 32");
     static_assert(K <= 32, "row tags are 5 bits");
     constexpr int G = 32 / L;              // groups per warp, 2 jobs per group
@@ -68,15 +87,17 @@ __global__ void __launch_bounds__(128) k_fill16(FillArgs A) {
     extern __shared__ __align__(16) int32_t s_prof[];
     int32_t* prof = s_prof + (threadIdx.x >> 5) * prof16_words_per_warp<K>();
     const uint32_t one = blockDim.x >> 7;               // 1 at run time
-    const uint32_t nf = g != 0 ? one : 0u;              // lane 0 takes the zero border
+    const uint32_t nf = g != 0 ? one : 0u;              // lane 0 takes the border
     const int32_t beta = -S.GO;
-    const uint32_t GE2 = pack2(S.GE, S.GE);
-    const uint32_t BETA2 = pack2(beta, beta);
-    // H + S_GO on both halves as one 32-bit add: with S_GO < 0 the low half always
-    // carries (every stored H is >= beta = -S_GO), so the high half's constant is
-    // S_GO - 1; with S_GO = 0 there is nothing to add
-    const uint32_t GO2C = S.GO == 0 ? 0u : (((uint32_t)S.GO & 0xFFFFu) + ((uint32_t)(S.GO - 1) << 16));
-    const int32_t thr = 1024 - S.a;                      // biased overflow threshold
+    const int32_t cH = max(0, -S.dx);                   // B - beta
+    const uint32_t C2 = pack2(32 * cH, 32 * cH);        // X of H = 0
+    const uint32_t x_border = g != 0 ? 0u : C2;
+    const uint32_t GE2 = pack2(32 * S.GE, 32 * S.GE);
+    const uint32_t FLG2 = pack2(32 * (beta + cH), 32 * (beta + cH));   // G~ of H = 0: the floor
+    // X = G~ - 32 beta on both halves as one 32-bit add: the low half always
+    // carries (G~ >= 32 B >= 32 beta), so the high half's constant is one less
+    const uint32_t GO2C = beta == 0 ? 0u : (((uint32_t)(-32 * beta) & 0xFFFFu) + ((uint32_t)(-32 * beta - 1) << 16));
+    const int32_t thr = 1024 - S.a - beta;              // overflow: (key >> 5) = H + B - beta reaches it
 
     for (;;) {
         uint32_t item = 0;
@@ -107,11 +128,10 @@ __global__ void __launch_bounds__(128) k_fill16(FillArgs A) {
         if (nblk_warp == 0) continue;
 
         // profile: entry ((h*4 + t)*K4 + r/4)*32 + lane (4 x int16 in a uint2) holds
-        // (delta - S_GO) of rows r..r+3 of job h against base t; padding rows never
-        // match.  Written and read through the same uint2 type, so the reads of the
-        // next job cannot be ordered before these stores.
+        // 32 (delta - S_GO) of rows r..r+3 of job h against base t; padding rows
+        // never match.  Written and read through the same uint2 type, so the reads
+        // of the next job cannot be ordered before these stores.
         int pad[2];
-        uint2* prof2 = reinterpret_cast<uint2*>(prof);
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             pad[h] = L * K - n[h];
@@ -129,10 +149,12 @@ __global__ void __launch_bounds__(128) k_fill16(FillArgs A) {
                 }
 #pragma unroll
                 for (int t = 0; t < 4; t++) {
+                    const int32_t e0 = 32 * (code[0] == t ? S.dm : S.dx), e1 = 32 * (code[1] == t ? S.dm : S.dx);
+                    const int32_t e2 = 32 * (code[2] == t ? S.dm : S.dx), e3 = 32 * (code[3] == t ? S.dm : S.dx);
                     uint2 v;
-                    v.x = pack2(code[0] == t ? S.dm : S.dx, code[1] == t ? S.dm : S.dx);
-                    v.y = pack2(code[2] == t ? S.dm : S.dx, code[3] == t ? S.dm : S.dx);
-                    prof2[((h * 4 + t) * K4 + q) * 32 + lane] = v;
+                    v.x = pack2(e0, e1);
+                    v.y = pack2(e2, e3);
+                    reinterpret_cast<uint2*>(prof)[((h * 4 + t) * K4 + q) * 32 + lane] = v;
                 }
             }
         }
@@ -141,15 +163,65 @@ __global__ void __launch_bounds__(128) k_fill16(FillArgs A) {
         // its own entries; with the barrier the result no longer depended on code
         // generation, see the design notes)
         __syncwarp();
-        // column 0: H(0,j) = 0 -> HG = 0; F = -inf -> 0
-        uint32_t HG[K], F[K];
+        // column 0: X = c (H = 0), F~ = 0
+        uint32_t X[K], F[K];
         auto reset_col0 = [&]() {
 #pragma unroll
-            for (int r = 0; r < K; r++) { HG[r] = 0u; F[r] = 0u; }
+            for (int r = 0; r < K; r++) { X[r] = C2; F[r] = 0u; }
         };
         reset_col0();
-        uint32_t h_up_prev = 0u;
-        uint32_t hg_bot = 0u, e_bot = 0u, cm_bot = 0u;
+        uint32_t x_up_prev = C2;
+        uint32_t x_bot = 0u, e_bot = 0u, cm_bot = 0u;
+
+        // one wavefront step: lane g computes column i = s - g + 1 of its K rows
+        // against window base tA (job A) and tB (job B)
+        auto step = [&](const int s, const uint32_t tA, const uint32_t tB, const bool first_block) {
+            const int i = s - g + 1;
+            // lane 0: the border (X = c, E~ = 0, no key)
+            const uint32_t x_up = __shfl_up_sync(FULL, x_bot, 1, L) * nf + x_border;
+            const uint32_t e_up = __shfl_up_sync(FULL, e_bot, 1, L) * nf;
+            const uint32_t cm_up = __shfl_up_sync(FULL, cm_bot, 1, L) * nf;
+            const uint32_t diag = x_up_prev;
+            x_up_prev = x_up;
+            uint32_t e = e_up, xa = x_up, lm = 0u;
+            // the diagonal term of row r+1 is formed while X[r] still holds X(i-1, j)
+            // (no copy of the old value stays live)
+            {
+                const uint2* pa = reinterpret_cast<const uint2*>(prof) + (tA * K4) * 32 + lane;
+                const uint2* pb = reinterpret_cast<const uint2*>(prof) + ((4 + tB) * K4) * 32 + lane;
+                uint2 qa = pa[0], qb = pb[0];
+                uint32_t gcur = __viaddmax_s16x2(diag, __byte_perm(qa.x, qb.x, 0x5410), FLG2);
+#pragma unroll
+                for (int r = 0; r < K; r++) {
+                    const uint32_t gv = gcur;
+                    if (r + 1 < K) {
+                        const int rn = r + 1;
+                        if ((rn & 3) == 0) { qa = pa[(rn / 4) * 32]; qb = pb[(rn / 4) * 32]; }
+                        const uint32_t xa2 = (rn & 2) ? qa.y : qa.x, xb2 = (rn & 2) ? qb.y : qb.x;
+                        const uint32_t dn = __byte_perm(xa2, xb2, (rn & 1) ? 0x7632 : 0x5410);
+                        gcur = __viaddmax_s16x2(X[r], dn, FLG2);
+                    }
+                    const uint32_t f = __viaddmax_s16x2(F[r], GE2, X[r]);
+                    e = __viaddmax_s16x2(e, GE2, xa);
+                    const uint32_t hv = __vimax3_s16x2(gv, e, f);
+                    F[r] = f;
+                    X[r] = hv * one + GO2C;
+                    xa = X[r];
+                    lm = __viaddmax_s16x2(X[r], (uint32_t)(31 - r) * 0x10001u, lm);
+                }
+            }
+            x_bot = X[K - 1];
+            e_bot = e;
+            const uint32_t cm = __vimax3_s16x2(cm_up, lm, lm);
+            cm_bot = cm;
+            // steps outside the windows land in slack slots / are never read
+            if (g == L - 1 && SA_GUARD((uint64_t)(cb_base + i - 1) < A.cb_cap, A.dbg, kSiteCb16)) cb[i - 1] = cm;
+            if (SA_GUARD(lk_base + (uint64_t)s * 32 < A.lk_cap, A.dbg, kSiteLaneKeys)) lk[(size_t)s * 32] = lm;
+            if (first_block && s < g) {       // before this lane's first column
+                reset_col0();
+                x_up_prev = C2;
+            }
+        };
 
         uint32_t wbn[2];
 #pragma unroll
@@ -162,58 +234,7 @@ __global__ void __launch_bounds__(128) k_fill16(FillArgs A) {
                 wbn[h] = load_window16<L, K>(A, wstart[h], b + 1, g);
             }
 #pragma unroll
-            for (int u = 0; u < 8; u++) {
-                const int s = 8 * b + u;
-                const int i = s - g + 1;
-                // lane 0: the border (every border value is 0 in this representation)
-                const uint32_t hg_up = __shfl_up_sync(FULL, hg_bot, 1, L) * nf;
-                const uint32_t e_up = __shfl_up_sync(FULL, e_bot, 1, L) * nf;
-                const uint32_t cm_up = __shfl_up_sync(FULL, cm_bot, 1, L) * nf;
-                const uint32_t diag = h_up_prev;
-                h_up_prev = hg_up;
-                const uint32_t tA = (wb[0] >> (2 * u)) & 3u, tB = (wb[1] >> (2 * u)) & 3u;
-                const uint2* pa = prof2 + (tA * K4) * 32 + lane;
-                const uint2* pb = prof2 + ((4 + tB) * K4) * 32 + lane;
-                uint2 qa = pa[0], qb = pb[0];
-                uint32_t e = e_up, hga = hg_up;
-                uint32_t lm = 0u, kpair = 0u;
-                // the diagonal term of row r+1 is formed while row r still holds
-                // H(i-1, j) (no copy of the old value is kept)
-                uint32_t gcur = __viaddmax_s16x2(diag, __byte_perm(qa.x, qb.x, 0x5410), BETA2);
-#pragma unroll
-                for (int r = 0; r < K; r++) {
-                    const uint32_t gv = gcur;                                  // max(G, 0) + beta
-                    if (r + 1 < K) {
-                        const int rn = r + 1;
-                        if ((rn & 3) == 0) { qa = pa[(rn / 4) * 32]; qb = pb[(rn / 4) * 32]; }
-                        const uint32_t xa = (rn & 2) ? qa.y : qa.x, xb = (rn & 2) ? qb.y : qb.x;
-                        const uint32_t dn = __byte_perm(xa, xb, (rn & 1) ? 0x7632 : 0x5410);
-                        gcur = __viaddmax_s16x2(HG[r], dn, BETA2);
-                    }
-                    const uint32_t f = __viaddmax_s16x2(F[r], GE2, HG[r]);
-                    e = __viaddmax_s16x2(e, GE2, hga);
-                    const uint32_t hv = __vimax3_s16x2(gv, e, f);
-                    F[r] = f;
-                    HG[r] = hv * one + GO2C;
-                    hga = HG[r];
-                    // key of both halves; no carry while H + beta <= 1023
-                    const uint32_t key = hv * (32u * one) + (uint32_t)(31 - r) * 0x10001u;
-                    if ((r & 1) == 1) lm = __vimax3_s16x2(lm, kpair, key);
-                    else if (r == K - 1) lm = __vimax3_s16x2(lm, key, key);
-                    else kpair = key;
-                }
-                hg_bot = HG[K - 1];
-                e_bot = e;
-                const uint32_t cm = __vimax3_s16x2(cm_up, lm, lm);
-                cm_bot = cm;
-                // steps outside the windows land in slack slots / are never read
-                if (g == L - 1 && SA_GUARD((uint64_t)(cb_base + i - 1) < A.cb_cap, A.dbg, kSiteCb16)) cb[i - 1] = cm;
-                if (SA_GUARD(lk_base + (uint64_t)s * 32 < A.lk_cap, A.dbg, kSiteLaneKeys)) lk[(size_t)s * 32] = lm;
-                if (8 * b < L && s < g) {      // before this lane's first column
-                    reset_col0();
-                    h_up_prev = 0u;
-                }
-            }
+            for (int u = 0; u < 8; u++) step(8 * b + u, (wb[0] >> (2 * u)) & 3u, (wb[1] >> (2 * u)) & 3u, 8 * b < L);
         }
 
         // per job of the pair: best, second best, overflow flag
@@ -241,7 +262,7 @@ __global__ void __launch_bounds__(128) k_fill16(FillArgs A) {
                 const int oi = __shfl_xor_sync(FULL, vi, o, L);
                 if (ov > v || (ov == v && oi < vi)) { v = ov; vi = oi; }
             }
-            const bool empty = v <= beta;
+            const bool empty = v <= cH;        // H = 0 everywhere
             // first row of that column: the lanes' stored keys of column vi
             int vj = 1 << 20;
             if (vi > 0) {
@@ -268,10 +289,10 @@ __global__ void __launch_bounds__(128) k_fill16(FillArgs A) {
             }
             if (g == 0 && has[h]) {
                 JobState st;
-                st.best = empty ? 0 : v - beta;
+                st.best = empty ? 0 : v - cH;
                 st.i_star = empty ? 0 : vi;
                 st.j_star = empty ? 0 : vj;
-                st.second = (empty || si == 0) ? SA_NO_SCORE : sv - beta;
+                st.second = (empty || si == 0) ? SA_NO_SCORE : sv - cH;
                 st.second_i = empty ? 0 : si;
                 st.flags = (empty ? kStEmpty : 0u) | (ovf ? kStOverflow : 0u);
                 if (SA_GUARD(jobv[h] < A.n_state, A.dbg, kSiteState16)) A.state[jobv[h]] = st;
