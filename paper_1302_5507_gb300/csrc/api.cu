@@ -682,7 +682,8 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             const bool heights = mode == SA_LOCAL && (int64_t)sc.a * max_n <= 254;
             launch_rect_plan(d_jobs, ws.order.as<uint32_t>(), n_jobs, dp->cfg_begin, ws.state.as<JobState>(), sc,
                              min_score, 1, ws.rect.as<Rect>(), ws.sizes.as<uint64_t>(), lists,
-                             dp->cls_count, rect_flag, heights ? 1 : 0, st);
+                             dp->cls_count, rect_flag, heights ? 1 : 0, X.d_words, ws.rpack.as<uint32_t>(), rw,
+                             st);
             launch_scan_u64(ws.sizes.as<uint64_t>(), n_jobs, ws.offs.as<uint64_t>(),
                             ws.bsum.as<uint64_t>(), &dp->totals[0], st);
             launch_scan_u32(rect_flag, n_jobs, rect_pos, ws.bsum.as<uint64_t>(), &dp->totals[2], st);

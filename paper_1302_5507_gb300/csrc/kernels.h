@@ -67,7 +67,8 @@ void launch_pack_reads(const sa_job* jobs, uint32_t n_jobs, const uint8_t* reads
 void launch_rect_plan(const sa_job* jobs, const uint32_t* order, uint32_t n_pos, const uint32_t* cfg_begin,
                       const JobState* state, const Score& sc, int32_t min_score, int allow_band,
                       Rect* rect, uint64_t* sizes, uint32_t* const* lists, uint32_t* cls_count,
-                      uint32_t* rect_flag, int heights, cudaStream_t st);
+                      uint32_t* rect_flag, int heights, const uint32_t* ref, const uint32_t* rpack, uint32_t rw,
+                      cudaStream_t st);
 // the rectangle-pass jobs compacted in bucketed order (rect_pos = exclusive scan of
 // rect_flag, total its sum), their positions in that order (list_pos), and each
 // bucket's first index in the list (rect_begin[kNumCfg + 1])

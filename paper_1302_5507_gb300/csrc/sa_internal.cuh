@@ -172,8 +172,9 @@ struct Rect {
     int32_t cfg;        // lane-group configuration of the job's score pass (its bucket)
 };
 // direction-pass classes: none (no traceback), banded passes of 8/16/32/64
-// diagonals, the wavefront rectangle, and the pure diagonal (an optimal path
-// with S = a*j* - best = 0 is all matches: its CIGAR needs no direction bits)
+// diagonals, the wavefront rectangle, and the gapless diagonal (the traceback
+// is a run of `rows` diagonal steps from the best cell, found by scoring the
+// diagonal: its CIGAR needs no direction bits)
 enum { kClsNone = 0, kClsBand16 = 1, kClsBand32 = 2, kClsRect = 3, kClsBand64 = 4, kClsDiag = 5,
        kClsBand8 = 6, kNumCls = 7 };
 constexpr int kNumBand = 4;                       // band classes 8, 16, 32, 64

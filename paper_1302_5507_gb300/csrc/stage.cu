@@ -282,13 +282,47 @@ struct BandLists { uint32_t* p[kNumBand]; };
 // left) reproduces every value on such a path and every comparison the
 // traceback makes, so the walk from its corner gives the same CIGAR.
 // With e = 0 the bound does not exist and the whole window is used.
+// Before any of that, a job whose traceback is a gapless diagonal run (below)
+// takes the diagonal class and no direction pass at all.
+
+// Steps of a gapless traceback from the best cell, or 0.  Let c_m be the score
+// of the m diagonal cells ending at (i*, j*).  If c_k = best (LOCAL: the first
+// such k; GLOCAL: k = j*, the run starting on row 0), then along the run
+// H(i*-m, j*-m) = best - c_m: each H is at least the run's prefix score (a path
+// to it) and at most H(i, j) - delta (the recurrence).  The traceback takes the
+// diagonal first on ties (SOAP3-dp Methods section 3 backtracks from the end
+// cell through the recurrence's sources), so it walks exactly that run: down to
+// the first zero, where LOCAL stops, or to row 0.  Its CIGAR is k matches /
+// mismatches and it needs no direction pass.
+__device__ int gapless_steps(const uint32_t* __restrict__ refw, uint64_t ref_pos, const uint32_t* __restrict__ rp,
+                             int istar, int jstar, int32_t best, const Score& sc) {
+    const bool local = sc.mode == SA_LOCAL;
+    if (!local && jstar > istar) return 0;            // the run would leave the window before row 0
+    const int mmax = min(istar, jstar);
+    int32_t c = 0;
+    uint64_t tw_at = ~0ull;
+    uint32_t tw = 0, rwd = 0;
+    int rw_at = -1;
+    for (int m = 1; m <= mmax; m++) {
+        const uint64_t pos = ref_pos + (uint64_t)(istar - m);          // window column i* - m + 1
+        const int jr = jstar - m;                                      // read row j* - m + 1, 0-based
+        if ((pos >> 4) != tw_at) { tw_at = pos >> 4; tw = __ldg(refw + tw_at); }
+        if ((jr >> 4) != rw_at) { rw_at = jr >> 4; rwd = __ldg(rp + rw_at); }
+        const uint32_t tb = (tw >> (2 * (pos & 15))) & 3u, rb = (rwd >> (2 * (jr & 15))) & 3u;
+        c += tb == rb ? sc.a : sc.b;
+        if (local && c == best) return m;
+        if ((int64_t)c + (int64_t)sc.a * (mmax - m) < best) return 0;   // best is out of reach
+    }
+    return (!local && c == best) ? jstar : 0;
+}
 
 __global__ void k_rect_plan(const sa_job* __restrict__ jobs, const uint32_t* __restrict__ order,
                             uint32_t n_pos, const uint32_t* __restrict__ cfg_begin,
                             const JobState* __restrict__ state, Score sc,
                             int32_t min_score, int allow_band, Rect* __restrict__ rect,
                             uint64_t* __restrict__ sizes, BandLists lists, uint32_t* cls_count,
-                            uint32_t* __restrict__ rect_flag, int heights) {
+                            uint32_t* __restrict__ rect_flag, int heights, const uint32_t* __restrict__ refw,
+                            const uint32_t* __restrict__ rpack, uint32_t rw) {
     // no early return: the class lists are appended with warp-wide ballots
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = p < n_pos;
@@ -334,6 +368,19 @@ __global__ void k_rect_plan(const sa_job* __restrict__ jobs, const uint32_t* __r
                 span = (int64_t)jstar + dmax;
             }
             R.rows = jstar;
+            if (R.cls != kClsDiag && allow_band) {
+                const int k = gapless_steps(refw, jobs[job].ref_pos, rpack + (size_t)job * rw, istar, jstar,
+                                            st.best, sc);
+                if (k > 0) {
+                    R.cls = kClsDiag;
+                    R.rows = k;
+                }
+            }
+            if (R.cls == kClsDiag) {
+                R.d_lo = istar - jstar;
+                R.start_i = istar;
+                R.start_j = jstar;
+            }
             if (R.cls == kClsRect) {
                 int64_t ilo = (int64_t)istar - span + 1;
                 if (ilo < 1) ilo = 1;
@@ -400,13 +447,14 @@ void launch_rect_list(const uint32_t* order, uint32_t n_pos, const uint32_t* rec
 void launch_rect_plan(const sa_job* jobs, const uint32_t* order, uint32_t n_pos, const uint32_t* cfg_begin,
                       const JobState* state, const Score& sc, int32_t min_score, int allow_band,
                       Rect* rect, uint64_t* sizes, uint32_t* const* lists, uint32_t* cls_count,
-                      uint32_t* rect_flag, int heights, cudaStream_t st) {
+                      uint32_t* rect_flag, int heights, const uint32_t* ref, const uint32_t* rpack, uint32_t rw,
+                      cudaStream_t st) {
     if (!n_pos) return;
     BandLists bl;
     for (int k = 0; k < kNumBand; k++) bl.p[k] = lists[k];
     k_rect_plan<<<(n_pos + 255) / 256, 256, 0, st>>>(jobs, order, n_pos, cfg_begin, state, sc, min_score,
                                                       allow_band, rect, sizes, bl, cls_count, rect_flag,
-                                                      heights);
+                                                      heights, ref + kRefFrontPad, rpack, rw);
 }
 
 // wave assignment of the rectangle jobs (their positions in the bucketed order,
@@ -565,12 +613,12 @@ __global__ void k_traceback(const sa_job* __restrict__ jobs, uint32_t job_begin,
     out.read_begin = -1;
     out.ref_begin_rel = -1;
     if (R.cls == kClsDiag && !plain) {
-        // all-match path: j* diagonal steps from (i*, j*) to (i* - j*, 0)
+        // gapless path: R.rows diagonal steps from (i*, j*) = (start_i, start_j)
         if (wave != 0) return;
         tmp_ops[(uint64_t)job * tmp_stride] = ((uint32_t)R.rows << 4) | 0u;
         out.n_rev = 1;
-        out.read_begin = 0;
-        out.ref_begin_rel = R.d_lo;
+        out.read_begin = R.start_j - R.rows;
+        out.ref_begin_rel = R.start_i - R.rows;
         tb[job] = out;
         return;
     }
