@@ -294,16 +294,48 @@ struct BandLists { uint32_t* p[kNumBand]; };
 // cell through the recurrence's sources), so it walks exactly that run: down to
 // the first zero, where LOCAL stops, or to row 0.  Its CIGAR is k matches /
 // mismatches and it needs no direction pass.
+// 16 bases p0 .. p0 + 15 of a packed sequence (base p at bits 2 (p & 15) of
+// word p >> 4), base p0 + t at bits 2t; the second word is read only when the
+// bases straddle it (so p0 + 15 is the last base the caller may touch)
+__device__ __forceinline__ uint32_t bases16_from(const uint32_t* __restrict__ w, uint64_t p0) {
+    const uint64_t wi = p0 >> 4;
+    const uint32_t sh = (uint32_t)(p0 & 15) * 2u;
+    const uint32_t lo = __ldg(w + wi);
+    return sh ? (uint32_t)((((uint64_t)__ldg(w + wi + 1) << 32) | lo) >> sh) : lo;
+}
+
 __device__ int gapless_steps(const uint32_t* __restrict__ refw, uint64_t ref_pos, const uint32_t* __restrict__ rp,
                              int istar, int jstar, int32_t best, const Score& sc) {
     const bool local = sc.mode == SA_LOCAL;
     if (!local && jstar > istar) return 0;            // the run would leave the window before row 0
     const int mmax = min(istar, jstar);
     int32_t c = 0;
+    int m = 0;
+    // 16 steps at a time: the window and read bases of steps m+1 .. m+16 compared
+    // as two words (base t of both at bits 2t is step m + 16 - t)
+    while (mmax - m >= 16) {
+        const uint32_t x = bases16_from(refw, ref_pos + (uint64_t)(istar - m - 16)) ^
+                           bases16_from(rp, (uint64_t)(jstar - m - 16));
+        const uint32_t eq = ~(x | (x >> 1)) & 0x55555555u;
+        if (local && (int64_t)c + 16 * (int64_t)sc.a >= best) {
+            // the best can be reached inside these 16 steps: take them one by one
+            for (int t = 15; t >= 0; t--) {
+                c += ((eq >> (2 * t)) & 1u) ? sc.a : sc.b;
+                m++;
+                if (c == best) return m;
+            }
+        } else {
+            const int mt = __popc(eq);
+            c += sc.a * mt + sc.b * (16 - mt);
+            m += 16;
+        }
+        if ((int64_t)c + (int64_t)sc.a * (mmax - m) < best) return 0;   // best is out of reach
+    }
     uint64_t tw_at = ~0ull;
     uint32_t tw = 0, rwd = 0;
     int rw_at = -1;
-    for (int m = 1; m <= mmax; m++) {
+    while (m < mmax) {
+        m++;
         const uint64_t pos = ref_pos + (uint64_t)(istar - m);          // window column i* - m + 1
         const int jr = jstar - m;                                      // read row j* - m + 1, 0-based
         if ((pos >> 4) != tw_at) { tw_at = pos >> 4; tw = __ldg(refw + tw_at); }
@@ -311,7 +343,7 @@ __device__ int gapless_steps(const uint32_t* __restrict__ refw, uint64_t ref_pos
         const uint32_t tb = (tw >> (2 * (pos & 15))) & 3u, rb = (rwd >> (2 * (jr & 15))) & 3u;
         c += tb == rb ? sc.a : sc.b;
         if (local && c == best) return m;
-        if ((int64_t)c + (int64_t)sc.a * (mmax - m) < best) return 0;   // best is out of reach
+        if ((int64_t)c + (int64_t)sc.a * (mmax - m) < best) return 0;
     }
     return (!local && c == best) ? jstar : 0;
 }
