@@ -709,7 +709,8 @@ def device_line(sa, ref, wl, args, label, widths=(0,), cigar=(True, False), mode
                          "ms_per_step": ms, "score_pass_gcups": wl.cells / (ph["ms_fill"] / 1e3) / 1e9,
                          "phases_ms": ph, "jobs16": int(st["jobs16"]), "overflow_reruns": int(st["overflow_reruns"]),
                          "diag_jobs": int(st["diag_jobs"]), "band_jobs": int(st["band_jobs"]),
-                         "rect_jobs": int(st["rect_jobs"]), "kernel_launches": int(st["kernel_launches"])})
+                         "rect_jobs": int(st["rect_jobs"]), "rect_pairs": int(st["rect_pairs"]),
+                         "kernel_launches": int(st["kernel_launches"])})
     return {"config": label, "jobs": int(wl.n_jobs), "cells": int(wl.cells), "steps": args.steps, "rows": rows}
 
 

@@ -143,7 +143,8 @@ typedef struct {           /* statistics of the last call on a reference or serv
     uint32_t jobs16;               /* jobs whose score pass ran in 16-bit packed pairs */
     uint32_t graph_replays;        /* 1 if the score segment ran as a replayed CUDA graph
                                       (graphs are used when profile == 0) */
-    uint32_t _pad;
+    uint32_t rect_pairs;           /* rectangle jobs whose pass ran two to a lane group in
+                                      16-bit halves (byte heights, buckets with many of them) */
 } sa_stats;
 
 typedef struct sa_reference sa_reference;

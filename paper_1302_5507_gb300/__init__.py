@@ -57,7 +57,7 @@ class sa_stats(ctypes.Structure):
                 ("ms_finalize", ctypes.c_float), ("ms_total", ctypes.c_float),
                 ("diag_jobs", ctypes.c_uint32), ("band_jobs", ctypes.c_uint32),
                 ("rect_jobs", ctypes.c_uint32), ("jobs16", ctypes.c_uint32),
-                ("graph_replays", ctypes.c_uint32), ("_pad", ctypes.c_uint32)]
+                ("graph_replays", ctypes.c_uint32), ("rect_pairs", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -102,7 +102,7 @@ struct PlanBlock {
 struct Workspace {
     DevBuf jobs, reads, out, cigar;          // inputs/outputs of the host-buffer entry points
     DevBuf key, order, rpack, state, rect, tb, count, coff, sizes, offs, bsum;
-    DevBuf colbest, tmp_ops, arena, plan, counters, blists, band, ovf, lkeys;
+    DevBuf colbest, tmp_ops, arena, plan, counters, blists, band, ovf, lkeys, rsort;
     PlanBlock* h_plan = nullptr;             // pinned mirror of the plan block
     // the score segment (order, packing, score passes, overflow rerun) as a CUDA
     // graph, replayed while a call's launches would be identical (same key)
@@ -119,14 +119,15 @@ struct Workspace {
     bool side_ok = false;
     cudaEvent_t ev[16] = {};
     bool ev_ok = false;
-    DevBuf* all_[24] = {};
+    DevBuf* all_[25] = {};
     DevBuf* const* bufs(size_t* n) {
         all_[0] = &jobs; all_[1] = &reads; all_[2] = &out; all_[3] = &cigar; all_[4] = &key;
         all_[5] = &order; all_[6] = &rpack; all_[7] = &state; all_[8] = &rect; all_[9] = &tb;
         all_[10] = &count; all_[11] = &coff; all_[12] = &sizes; all_[13] = &offs; all_[14] = &bsum;
         all_[15] = &colbest; all_[16] = &lkeys; all_[17] = &tmp_ops; all_[18] = &arena;
         all_[19] = &plan; all_[20] = &counters; all_[21] = &blists; all_[22] = &band; all_[23] = &ovf;
-        *n = 24;
+        all_[24] = &rsort;
+        *n = 25;
         return all_;
     }
     // device bytes the workspace holds
@@ -673,10 +674,9 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             uint32_t* rect_list = ws.blists.as<uint32_t>() + (size_t)kNumBand * n_jobs;
             uint32_t* rect_list_pos = ws.blists.as<uint32_t>() + (size_t)(kNumBand + 1) * n_jobs;
             nvtx.next("traceback classes");
-            // the results' count and offset arrays serve as the rectangle flags and
-            // their scan here (the results phase rewrites them)
+            // the results' count array serves as the rectangle flags here (the results
+            // phase rewrites it)
             uint32_t* rect_flag = ws.count.as<uint32_t>();
-            uint64_t* rect_pos = ws.coff.as<uint64_t>();
             // byte heights instead of nibbles (band and rectangle passes) when LOCAL
             // scores stay below 255
             const bool heights = mode == SA_LOCAL && (int64_t)sc.a * max_n <= 254;
@@ -686,10 +686,10 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
                              st);
             launch_scan_u64(ws.sizes.as<uint64_t>(), n_jobs, ws.offs.as<uint64_t>(),
                             ws.bsum.as<uint64_t>(), &dp->totals[0], st);
-            launch_scan_u32(rect_flag, n_jobs, rect_pos, ws.bsum.as<uint64_t>(), &dp->totals[2], st);
-            launch_rect_list(ws.order.as<uint32_t>(), n_jobs, rect_flag, rect_pos, dp->cfg_begin, &dp->totals[2],
-                             rect_list, rect_list_pos, dp->rect_begin, st);
-            launches += 9;
+            TRY(ws.rsort.ensure(rect_sort_bytes(), "rectangle sort"));
+            launch_rect_list(ws.order.as<uint32_t>(), n_jobs, rect_flag, ws.rect.as<Rect>(), ws.rsort.p,
+                             ws.bsum.as<uint64_t>(), &dp->totals[2], rect_list, rect_list_pos, dp->rect_begin, st);
+            launches += 10;
             CU(cudaGetLastError());
             trace("rect plan + scan");
             CU(cudaMemcpyAsync(&hp->totals[0], &dp->totals[0], 8, cudaMemcpyDeviceToHost, st));
@@ -792,9 +792,15 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
                     fl.args.arena = ws.arena.as<uint32_t>();
                     fl.args.arena_cap = ws.arena.cap / 4;
                     fl.args.wave = (int)wv;
-                    fl.kind = heights ? kFillRectH : kFillRect;
+                    // byte heights: two jobs a lane group in 16-bit halves when the bucket
+                    // has more of them than two full waves of the pair kernel's lane
+                    // groups (fewer long rectangles: one job a group, more groups)
+                    const bool pairs = heights &&
+                        (uint64_t)rn >= 2ull * grid_for(c, kFillRectH16) * (kBlock / 32) * (32 / cfg_L(c)) * 2;
+                    fl.kind = pairs ? kFillRectH16 : (heights ? kFillRectH : kFillRect);
+                    if (pairs && wv == 0) stats.rect_pairs += rn;
                     fl.block = kBlock;
-                    const uint32_t G = 32 / cfg_L(c);
+                    const uint32_t G = (32 / cfg_L(c)) * (pairs ? 2 : 1);
                     const uint64_t warps_needed = (rn + G - 1) / G;
                     fl.grid = (int)std::min<uint64_t>(grid_for(c, fl.kind), (warps_needed + 3) / 4);
                     fl.stream = rect_fork ? ws.side[kNumBand + c] : st;

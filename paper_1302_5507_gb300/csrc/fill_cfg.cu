@@ -1,6 +1,6 @@
 // One configuration's wavefront kernels (compiled once per configuration with
 // -DSA_CFG=<index>, so the translation units build in parallel).
-#include "fill16.cuh"
+#include "rect16.cuh"
 #include "kernels.h"
 
 #ifndef SA_CFG
@@ -40,6 +40,8 @@ void prepare16() {
     if (!done) {
         cudaFuncSetAttribute(k_fill16<kL, kK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem16_bytes());
+        cudaFuncSetAttribute(k_fill16h<kL, kK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem16_bytes());
         done = true;
     }
 }
@@ -74,6 +76,10 @@ void launch_fill<SA_CFG>(const FillLaunch& fl) {
     case kFillRectH:            // byte heights: LOCAL only
         if (local) launch_one<SA_LOCAL, true, false, true>(fl);
         break;
+    case kFillRectH16:          // byte heights, two jobs a lane group: LOCAL only
+        prepare16();
+        if (local) k_fill16h<kL, kK><<<fl.grid, fl.block, smem16_bytes(), fl.stream>>>(fl.args);
+        break;
     default:
         break;
     }
@@ -95,6 +101,12 @@ int fill_blocks_per_sm<SA_CFG>(int kind, int mode) {
         prepare16();
         int nb = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fill16<kL, kK>, 128, smem16_bytes());
+        return nb;
+    }
+    case kFillRectH16: {
+        prepare16();
+        int nb = 0;
+        if (local) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fill16h<kL, kK>, 128, smem16_bytes());
         return nb;
     }
     }

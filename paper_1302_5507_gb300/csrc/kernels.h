@@ -72,8 +72,9 @@ void launch_rect_plan(const sa_job* jobs, const uint32_t* order, uint32_t n_pos,
 // the rectangle-pass jobs compacted in bucketed order (rect_pos = exclusive scan of
 // rect_flag, total its sum), their positions in that order (list_pos), and each
 // bucket's first index in the list (rect_begin[kNumCfg + 1])
-void launch_rect_list(const uint32_t* order, uint32_t n_pos, const uint32_t* rect_flag, const uint64_t* rect_pos,
-                      const uint32_t* cfg_begin, const uint64_t* total, uint32_t* list, uint32_t* list_pos,
+uint64_t rect_sort_bytes();        // scratch of launch_rect_list
+void launch_rect_list(const uint32_t* order, uint32_t n_pos, const uint32_t* rect_flag, const Rect* rect,
+                      void* sort_scratch, uint64_t* bsum, uint64_t* total, uint32_t* list, uint32_t* list_pos,
                       uint32_t* rect_begin, cudaStream_t st);
 // heights: the byte-height form (LOCAL and every score below 255; the band
 // regions then hold B/4 words a row instead of B/8)

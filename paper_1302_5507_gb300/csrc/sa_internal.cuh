@@ -230,7 +230,7 @@ struct FillLaunch {
     int grid, block;
     cudaStream_t stream;
 };
-enum { kFillScore = 0, kFillRect = 1, kFillPlain = 2, kFillScore16 = 3, kFillRectH = 4 };
+enum { kFillScore = 0, kFillRect = 1, kFillPlain = 2, kFillScore16 = 3, kFillRectH = 4, kFillRectH16 = 5 };
 
 // per-configuration launchers (one translation unit per configuration)
 template <int C> void launch_fill(const FillLaunch& fl);

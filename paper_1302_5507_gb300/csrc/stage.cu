@@ -453,27 +453,62 @@ __global__ void k_rect_plan(const sa_job* __restrict__ jobs, const uint32_t* __r
 
 // the jobs of the wavefront rectangle pass, in the bucketed order (rect_pos is
 // the exclusive scan of rect_flag), and where each bucket's run of them begins
-__global__ void k_rect_list(const uint32_t* __restrict__ order, uint32_t n_pos, const uint32_t* __restrict__ rect_flag,
-                            const uint64_t* __restrict__ rect_pos, uint32_t* __restrict__ list,
-                            uint32_t* __restrict__ list_pos) {
+// The jobs of the wavefront rectangle pass, by bucket and within a bucket by
+// rectangle width, widest first (a counting sort on kRectWidthClasses classes of
+// eight columns): the lane groups of a warp then run rectangles of about the same
+// width, and a warp runs as many steps as its widest.  The order inside a class is
+// the arrival order of the scatter's atomics, which changes no result: each job's
+// direction data depends on its own rectangle only.  list_pos[q] is the bucketed
+// position of list entry q; rect_begin[c] is where bucket c's run begins.
+constexpr int kRectWidthClasses = 128;
+
+__device__ __forceinline__ uint32_t rect_sort_key(const Rect& R) {
+    const int cls = min(kRectWidthClasses - 1, (R.w + 7) >> 3);
+    return (uint32_t)(R.cfg * kRectWidthClasses + (kRectWidthClasses - 1 - cls));
+}
+
+__global__ void k_rect_hist(const uint32_t* __restrict__ order, uint32_t n_pos, const uint32_t* __restrict__ rect_flag,
+                            const Rect* __restrict__ rect, uint32_t* __restrict__ hist) {
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n_pos && rect_flag[p]) atomicAdd(&hist[rect_sort_key(rect[order[p]])], 1u);
+}
+
+__global__ void k_rect_scatter(const uint32_t* __restrict__ order, uint32_t n_pos,
+                               const uint32_t* __restrict__ rect_flag, const Rect* __restrict__ rect,
+                               const uint64_t* __restrict__ start, uint32_t* __restrict__ cursor,
+                               uint32_t* __restrict__ list, uint32_t* __restrict__ list_pos) {
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p < n_pos && rect_flag[p]) {
-        list[rect_pos[p]] = order[p];
-        list_pos[rect_pos[p]] = p;
+        const uint32_t job = order[p];
+        const uint32_t key = rect_sort_key(rect[job]);
+        const uint64_t q = start[key] + atomicAdd(&cursor[key], 1u);
+        list[q] = job;
+        list_pos[q] = p;
     }
 }
-__global__ void k_rect_bounds(const uint64_t* __restrict__ rect_pos, uint32_t n_pos,
-                              const uint32_t* __restrict__ cfg_begin, const uint64_t* total,
+
+__global__ void k_rect_bounds(const uint64_t* __restrict__ start, const uint64_t* total,
                               uint32_t* __restrict__ rect_begin) {
     const int c = threadIdx.x;
-    if (c <= kNumCfg) rect_begin[c] = cfg_begin[c] < n_pos ? (uint32_t)rect_pos[cfg_begin[c]] : (uint32_t)*total;
+    if (c < kNumCfg) rect_begin[c] = (uint32_t)start[c * kRectWidthClasses];
+    if (c == kNumCfg) rect_begin[c] = (uint32_t)*total;
 }
-void launch_rect_list(const uint32_t* order, uint32_t n_pos, const uint32_t* rect_flag, const uint64_t* rect_pos,
-                      const uint32_t* cfg_begin, const uint64_t* total, uint32_t* list, uint32_t* list_pos,
+
+uint64_t rect_sort_bytes() { return (uint64_t)kNumCfg * kRectWidthClasses * 16; }
+
+void launch_rect_list(const uint32_t* order, uint32_t n_pos, const uint32_t* rect_flag, const Rect* rect,
+                      void* sort_scratch, uint64_t* bsum, uint64_t* total, uint32_t* list, uint32_t* list_pos,
                       uint32_t* rect_begin, cudaStream_t st) {
     if (!n_pos) return;
-    k_rect_list<<<(n_pos + 255) / 256, 256, 0, st>>>(order, n_pos, rect_flag, rect_pos, list, list_pos);
-    k_rect_bounds<<<1, 64, 0, st>>>(rect_pos, n_pos, cfg_begin, total, rect_begin);
+    constexpr uint32_t nk = kNumCfg * kRectWidthClasses;
+    uint64_t* start = static_cast<uint64_t*>(sort_scratch);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(start + nk);
+    uint32_t* cursor = hist + nk;
+    cudaMemsetAsync(hist, 0, 2 * nk * sizeof(uint32_t), st);
+    k_rect_hist<<<(n_pos + 255) / 256, 256, 0, st>>>(order, n_pos, rect_flag, rect, hist);
+    launch_scan_u32(hist, nk, start, bsum, total, st);
+    k_rect_scatter<<<(n_pos + 255) / 256, 256, 0, st>>>(order, n_pos, rect_flag, rect, start, cursor, list, list_pos);
+    k_rect_bounds<<<1, 64, 0, st>>>(start, total, rect_begin);
 }
 
 void launch_rect_plan(const sa_job* jobs, const uint32_t* order, uint32_t n_pos, const uint32_t* cfg_begin,

@@ -2,7 +2,7 @@
 checks its index against its buffer and reports an out-of-range store as an
 internal error.  The checked library must give the oracle's results on every
 path (both widths, both modes, both forms, every traceback class, the rectangle
-arena in waves) without reporting a store."""
+arena in waves, the rectangle pass two jobs a lane group) without reporting a store."""
 import os
 import subprocess
 import sys
@@ -39,6 +39,16 @@ for wl in cases:
             res, cig = ref.align(jobs, wl.reads, sa.make_params(mode=mode, arena_mb=4))
             bad = compare(res, cig, ores, oops)
             assert not bad, (wl.name, mode, "waves", bad[:5])
+# enough rectangle jobs in one bucket for its pass to run two jobs a lane group
+wl = workloads.lowsim(4, 60_000, genome_len=4_000_000)
+jobs = sa.jobs_array(wl.read_off, wl.read_len, wl.flags, wl.ref_pos, wl.win_len)
+ores, oops = oracle.align(wl)
+with sa.Reference(wl.ref) as ref:
+    for arena_mb in (0, 64):
+        res, cig = ref.align(jobs, wl.reads, sa.make_params(arena_mb=arena_mb))
+        assert ref.stats()["rect_pairs"] > 0, ref.stats()
+        bad = compare(res, cig, ores, oops)
+        assert not bad, (wl.name, "rectangle pairs", arena_mb, bad[:5])
 print("bounds-checked build: all cases exact")
 """.replace("ROOT", repr(ROOT))
 
