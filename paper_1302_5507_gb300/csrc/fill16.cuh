@@ -46,6 +46,7 @@
 
 #include "fill.cuh"
 
+
 namespace sa {
 
 // words of the per-lane 16-bit profile of a warp (two jobs x 4 bases x rows
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(128, fill16_min_blocks<K>()) k_fill16(FillArgs
         for (int h = 0; h < 2; h++) {
             pad[h] = L * K - n[h];
             const uint32_t* rp = A.rpack + (size_t)jobv[h] * A.rw;
-#pragma unroll
+#pragma unroll 1
             for (int q = 0; q < K4; q++) {
                 int code[4];
 #pragma unroll
@@ -233,7 +234,10 @@ __global__ void __launch_bounds__(128, fill16_min_blocks<K>()) k_fill16(FillArgs
                 wb[h] = wbn[h];
                 wbn[h] = load_window16<L, K>(A, wstart[h], b + 1, g);
             }
-#pragma unroll
+            // four steps a loop body: the per-item code (profile, epilogue) and the
+            // step loop then fit the instruction cache together (eight steps stalled
+            // on instruction fetch where windows are short)
+#pragma unroll 4
             for (int u = 0; u < 8; u++) step(8 * b + u, (wb[0] >> (2 * u)) & 3u, (wb[1] >> (2 * u)) & 3u, 8 * b < L);
         }
 

@@ -174,7 +174,8 @@ __global__ void __launch_bounds__(128) k_fill16h(FillArgs A) {
                 wb[h] = wbn[h];
                 wbn[h] = load_window16<L, K>(A, wstart[h], b + 1, g);
             }
-#pragma unroll
+            // four steps a loop body (the whole eight overflow the instruction cache)
+#pragma unroll 4
             for (int u = 0; u < 8; u++)
                 step(b, 8 * b + u, (wb[0] >> (2 * u)) & 3u, (wb[1] >> (2 * u)) & 3u, 8 * b < L);
         }
