@@ -70,6 +70,13 @@ constexpr int fill16_min_blocks() { return (K >= 25 && K <= 28) ? 4 : 0; }
 
 template <int L, int K>
 __global__ void __launch_bounds__(128, fill16_min_blocks<K>()) k_fill16(FillArgs A) {
+    // steps a loop body and the unrolling of the per-item profile loop: past 16 rows
+    // the eight-step body and the per-item code (profile, epilogue) do not fit the
+    // instruction cache together (warps that change items often, short windows,
+    // stalled on instruction fetch), so the body takes four steps and the profile
+    // loop stays rolled
+    constexpr int kStepUnroll = K <= 16 ? 8 : 4;
+    constexpr int kProfUnroll = K <= 16 ? (K + 3) / 4 : 1;
     static_assert(32 % L == 0, "L must divide 32");
     static_assert(K <= 32, "row tags are 5 bits");
     constexpr int G = 32 / L;              // groups per warp, 2 jobs per group
@@ -137,7 +144,7 @@ __global__ void __launch_bounds__(128, fill16_min_blocks<K>()) k_fill16(FillArgs
         for (int h = 0; h < 2; h++) {
             pad[h] = L * K - n[h];
             const uint32_t* rp = A.rpack + (size_t)jobv[h] * A.rw;
-#pragma unroll 1
+#pragma unroll kProfUnroll
             for (int q = 0; q < K4; q++) {
                 int code[4];
 #pragma unroll
@@ -234,10 +241,7 @@ __global__ void __launch_bounds__(128, fill16_min_blocks<K>()) k_fill16(FillArgs
                 wb[h] = wbn[h];
                 wbn[h] = load_window16<L, K>(A, wstart[h], b + 1, g);
             }
-            // four steps a loop body: the per-item code (profile, epilogue) and the
-            // step loop then fit the instruction cache together (eight steps stalled
-            // on instruction fetch where windows are short)
-#pragma unroll 4
+#pragma unroll kStepUnroll
             for (int u = 0; u < 8; u++) step(8 * b + u, (wb[0] >> (2 * u)) & 3u, (wb[1] >> (2 * u)) & 3u, 8 * b < L);
         }
 
