@@ -947,7 +947,9 @@ def run_config(args):
         with sa.Reference(wl.ref) as ref:
             for mode in (0, 1):
                 for form in (1, 0):
-                    rows += device_line(sa, ref, wl, args, "", cigar=(True,), mode=mode, form=form)["rows"]
+                    # int32 scores as the configuration states, the default width beside them
+                    rows += device_line(sa, ref, wl, args, "", widths=(32, 0) if form == 0 else (0,),
+                                        cigar=(True,), mode=mode, form=form)["rows"]
         mate = make_workload("c2", 0, 1_000_000)
         with sa.Reference(mate.ref) as ref:
             glocal = device_line(sa, ref, mate, args, "", cigar=(True, False), mode=1)["rows"]
@@ -987,8 +989,11 @@ def run_config(args):
     elif args.config == "c4":
         wl = workloads.lowsim(seed=1, n_jobs=args.jobs or 500_000)
         with sa.Reference(wl.ref) as ref:
+            # int32 scores as the configuration states, the default width (16-bit pairs with
+            # the exact rerun) beside them; score-only and with traceback for each
             line = device_line(sa, ref, wl, args,
-                               "c4 low similarity: 500k jobs, n 250, m 1000, divergence 0-40%")
+                               "c4 low similarity: 500k jobs, n 250, m 1000, divergence 0-40%",
+                               widths=(32, 0))
     else:
         ref_acgt = workloads.serving_reference(seed=1)
         n_req = 200

@@ -745,9 +745,8 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
                 ba.dbg = &dp->st.dbg_site;
                 if (ba.count) {
                     if (fork) CU(cudaStreamWaitEvent(ws.side[k], ws.fork, 0));
-                    launch_band(band_cls(k), ba, heights, fork ? ws.side[k] : st);
+                    launches += launch_band(band_cls(k), ba, heights, fork ? ws.side[k] : st);
                     if (fork) CU(cudaEventRecord(ws.join[k], ws.side[k]));
-                    launches++;
                 }
             }
             CU(cudaGetLastError());

@@ -389,26 +389,167 @@ __global__ void __launch_bounds__(128) k_band_h_walk(BandArgs A) {
                    GO, GE, sa, sb);
 }
 
+// Match bits of one row of a job's band: bit 2k of word k >> 5 is set when the
+// window base of slot k (column i0 + k) equals read base rb.  Slots left of
+// column 1 never match (see k_band_h2).
+template <int NH>
+__device__ __forceinline__ void band_match_bits(const uint32_t* refw, int64_t ref_len, int64_t ref_pos, int i0,
+                                                uint32_t rb, uint64_t (&mm)[NH]) {
+#pragma unroll
+    for (int hh = 0; hh < NH; hh++) {
+        const int64_t ph = ref_pos + i0 - 1 + 32 * hh;
+        int64_t qh = ph < ref_pos ? ref_pos : ph;
+        if (qh > ref_len) qh = ref_len;
+        const int64_t wi = qh >> 4;
+        const uint32_t sh = (uint32_t)(qh & 15) * 2u;
+        const uint64_t lo = ((uint64_t)__ldg(refw + wi + 1) << 32) | (uint64_t)__ldg(refw + wi);
+        const uint64_t hi = (uint64_t)__ldg(refw + wi + 2);
+        const uint64_t wb = sh ? ((lo >> sh) | (hi << (64 - sh))) : lo;
+        const uint64_t x = wb ^ ((uint64_t)rb * 0x5555555555555555ull);
+        const uint64_t m = ~(x | (x >> 1)) & 0x5555555555555555ull;
+        // lead slots (left of column 1): shifted in as non-matches; a half past the
+        // reference's end (lead < 0) matches nothing
+        const int64_t lead = qh - ph;
+        mm[hh] = (lead < 0 || lead >= 32) ? 0ull : (m << (2 * lead));
+    }
+}
+
+__device__ __forceinline__ uint32_t pack_s16x2(int32_t lo, int32_t hi) {
+    return ((uint32_t)lo & 0xFFFFu) | ((uint32_t)hi << 16);
+}
+
+// Byte-height band pass, two jobs a thread in 16-bit halves: job A (list entry
+// 64c + t) in the low and job B (entry 64c + 32 + t) in the high half of every
+// register, so each store of a warp still covers 32 consecutive words of one
+// region.  Per half, with beta = o + e (= -S_GO):
+//   X = H,   E~ = E + beta,   F~ = F + beta
+//   E~(i,j) = max(E~(i,j-1) + S_GE, X(i,j-1))
+//   F~(i,j) = max(F~(i-1,j) + S_GE, X(i-1,j))
+//   G~(i,j) = max(X(i-1,j-1) + delta + beta, beta)       (the LOCAL zero floor)
+//   X(i,j)  = max(G~, E~, F~) - beta
+// which is the recurrence of SOAP3-dp Methods section 3 shifted by beta.  The
+// last subtraction is one 32-bit multiply-add on both halves: every maximum is at
+// least beta, so the low half always carries and the high half's constant is one
+// less.  delta + beta is one multiply-add of the two match bits (it needs
+// mismatch <= o + e, so that no half goes negative).
+// Cells left of column 0 are computed like window columns whose bases never
+// match: all of them get H = 0 (their E and F stay negative), so column 0 holds
+// the border's H = 0 and column 1 sees F = H(0,j) + S_GO as from the border; no
+// slot needs an edge test.  The walk never reads left of column 0.  A job with
+// fewer rows than its partner computes the extra rows without storing them.
+template <int B>
+__global__ void __launch_bounds__(128) k_band_h2(BandArgs A) {
+    constexpr int W = B / 4;                   // words of heights a row
+    constexpr int NH = B > 32 ? 2 : 1;
+    static_assert(B == 8 || B == 16 || B == 32 || B == 64, "band widths 8, 16, 32 and 64");
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t posA = (tid >> 5) * 64u + (tid & 31u);
+    if (posA >= A.count) return;
+    const uint32_t posB = posA + 32u;
+    const bool hasB = posB < A.count;
+    const uint32_t jobA = A.list[posA];
+    const uint32_t jobB = hasB ? A.list[posB] : jobA;
+    const int64_t refA = (int64_t)A.jobs[jobA].ref_pos, refB = (int64_t)A.jobs[jobB].ref_pos;
+    const int rowsA = A.rect[jobA].rows, rowsB = hasB ? A.rect[jobB].rows : 0;
+    const int dloA = A.rect[jobA].d_lo, dloB = A.rect[jobB].d_lo;
+    const uint32_t* rpA = A.rpack + (size_t)jobA * A.rw;
+    const uint32_t* rpB = A.rpack + (size_t)jobB * A.rw;
+    const uint32_t* refw = A.ref + kRefFrontPad;
+    // the two entries' regions: entry p's words at (p >> 5) * warp_stride + (p & 31)
+    const uint64_t baseA = (uint64_t)(posA >> 5) * A.warp_stride + (posA & 31u);
+    const uint64_t baseB = baseA + A.warp_stride;
+    uint32_t* outA = A.arena + baseA;
+    uint32_t* outB = A.arena + baseB;
+
+    const int32_t beta = -A.sc.GO;
+    const uint32_t one = blockDim.x >> 7;               // 1 at run time (keeps the multiply-add)
+    const uint32_t GE2 = pack_s16x2(A.sc.GE, A.sc.GE);
+    const uint32_t BETA2 = pack_s16x2(beta, beta);
+    const uint32_t SB2 = pack_s16x2(A.sc.b + beta, A.sc.b + beta);
+    const uint32_t AB = (uint32_t)(A.sc.a - A.sc.b);
+    const uint32_t GO2C = beta == 0 ? 0u : (((uint32_t)(-beta) & 0xFFFFu) + ((uint32_t)(-beta - 1) << 16));
+    const uint32_t NEG2 = pack_s16x2(-16384, -16384);   // outside the band (+ S_GE stays in range)
+
+    uint32_t Xs[B + 1], Es[B + 1];
+#pragma unroll
+    for (int k = 0; k <= B; k++) {
+        Xs[k] = k < B ? 0u : NEG2;             // row 0: H = 0 (left of column 0 too)
+        Es[k] = NEG2;
+    }
+    const int rows = max(rowsA, rowsB);
+    for (int j = 1; j <= rows; j++) {
+        const uint32_t rbA = (__ldg(rpA + ((j - 1) >> 4)) >> (2 * ((j - 1) & 15))) & 3u;
+        const uint32_t rbB = (__ldg(rpB + ((j - 1) >> 4)) >> (2 * ((j - 1) & 15))) & 3u;
+        uint64_t mA[NH], mB[NH];
+        band_match_bits<NH>(refw, A.ref_len, refA, j + dloA, rbA, mA);
+        band_match_bits<NH>(refw, A.ref_len, refB, j + dloB, rbB, mB);
+        const bool stA = j <= rowsA, stB = j <= rowsB;
+        uint32_t xleft = NEG2, fleft = NEG2, wd = 0u;
+        uint32_t xq[4];
+#pragma unroll
+        for (int k = 0; k < B; k++) {
+            if ((k & 7) == 0) {                // slots 8c .. 8c+7: A's bits low, B's high
+                const int c = k >> 3;
+                const uint32_t wa = (uint32_t)(mA[c >> 2] >> (16 * (c & 3))) & 0xFFFFu;
+                const uint32_t wb = (uint32_t)(mB[c >> 2] >> (16 * (c & 3))) << 16;
+                wd = wa | wb;
+            }
+            const uint32_t sel = (wd >> (2 * (k & 7))) & 0x00010001u;
+            const uint32_t d2 = sel * AB + SB2;                     // delta + beta, both halves
+            const uint32_t en = __viaddmax_s16x2(Es[k + 1], GE2, Xs[k + 1]);
+            const uint32_t fn = __viaddmax_s16x2(fleft, GE2, xleft);
+            const uint32_t gt = __viaddmax_s16x2(Xs[k], d2, BETA2);
+            const uint32_t x = __vimax3_s16x2(gt, en, fn) * one + GO2C;
+            Xs[k] = x;
+            Es[k] = en;
+            xleft = x;
+            fleft = fn;
+            xq[k & 3] = x;
+            if ((k & 3) == 3) {
+                // bytes of four slots: [A0 A1 B0 B1], [A2 A3 B2 B3] -> A0..A3, B0..B3
+                const uint32_t t01 = __byte_perm(xq[0], xq[1], 0x6240);
+                const uint32_t t23 = __byte_perm(xq[2], xq[3], 0x6240);
+                const uint64_t at = ((uint64_t)(j - 1) * W + (k >> 2)) * 32;
+                if (stA && SA_GUARD(baseA + at < A.region_cap, A.dbg, kSiteBand)) outA[at] = __byte_perm(t01, t23, 0x5410);
+                if (stB && SA_GUARD(baseB + at < A.region_cap, A.dbg, kSiteBand)) outB[at] = __byte_perm(t01, t23, 0x7632);
+            }
+        }
+    }
+}
+
 }  // namespace
 
-void launch_band(int cls, const BandArgs& a, bool heights, cudaStream_t st) {
-    if (!a.count) return;
+int launch_band(int cls, const BandArgs& a, bool heights, cudaStream_t st) {
+    if (!a.count) return 0;
     const unsigned grid = (a.count + 127) / 128;
     const bool local = a.sc.mode == SA_LOCAL;
     if (heights) {                     // LOCAL, scores below 255
         // the narrow classes walk right after their pass in the same thread; the wide
         // ones (96 and 168 registers a thread) hand the walk to a light kernel on the
-        // same stream, which keeps many more warps resident for its dependent loads
-        if (cls == kClsBand8) k_band_h<8, true><<<grid, 128, 0, st>>>(a);
-        else if (cls == kClsBand16) k_band_h<16, true><<<grid, 128, 0, st>>>(a);
-        else if (cls == kClsBand32) {
-            k_band_h<32, false><<<grid, 128, 0, st>>>(a);
+        // same stream, which keeps many more warps resident for its dependent loads.
+        // With mismatch <= o + e the wide passes take two jobs a thread in 16-bit
+        // halves (k_band_h2); for the narrow classes the pair form, whose walk must
+        // then run in its own kernel, measured slower
+        const bool pairs = a.sc.b - a.sc.GO >= 0;
+        const unsigned grid2 = (a.count + 255) / 256;
+        if (cls == kClsBand8) {
+            k_band_h<8, true><<<grid, 128, 0, st>>>(a);
+            return 1;
+        }
+        if (cls == kClsBand16) {
+            k_band_h<16, true><<<grid, 128, 0, st>>>(a);
+            return 1;
+        }
+        if (cls == kClsBand32) {
+            if (pairs) k_band_h2<32><<<grid2, 128, 0, st>>>(a);
+            else k_band_h<32, false><<<grid, 128, 0, st>>>(a);
             k_band_h_walk<32><<<grid, 128, 0, st>>>(a);
         } else {
-            k_band_h<64, false><<<grid, 128, 0, st>>>(a);
+            if (pairs) k_band_h2<64><<<grid2, 128, 0, st>>>(a);
+            else k_band_h<64, false><<<grid, 128, 0, st>>>(a);
             k_band_h_walk<64><<<grid, 128, 0, st>>>(a);
         }
-        return;
+        return 2;
     }
     if (cls == kClsBand8) {
         local ? k_band<8, SA_LOCAL><<<grid, 128, 0, st>>>(a) : k_band<8, SA_GLOCAL><<<grid, 128, 0, st>>>(a);
@@ -419,6 +560,7 @@ void launch_band(int cls, const BandArgs& a, bool heights, cudaStream_t st) {
     } else {
         local ? k_band<64, SA_LOCAL><<<grid, 128, 0, st>>>(a) : k_band<64, SA_GLOCAL><<<grid, 128, 0, st>>>(a);
     }
+    return 1;
 }
 
 }  // namespace sa

@@ -78,7 +78,8 @@ void launch_rect_list(const uint32_t* order, uint32_t n_pos, const uint32_t* rec
                       uint32_t* rect_begin, cudaStream_t st);
 // heights: the byte-height form (LOCAL and every score below 255; the band
 // regions then hold B/4 words a row instead of B/8)
-void launch_band(int cls, const BandArgs& a, bool heights, cudaStream_t st);
+// returns the number of kernels it launched
+int launch_band(int cls, const BandArgs& a, bool heights, cudaStream_t st);
 void launch_rect_assign(const uint32_t* order, const uint32_t* list_pos, uint32_t n, const uint64_t* offs,
                         uint64_t wave_words, Rect* rect, uint32_t* max_wave, cudaStream_t st);
 void launch_plain_rect(const sa_job* jobs, uint32_t j0, uint32_t nb, uint64_t stride, Rect* rect,
