@@ -234,7 +234,22 @@ __global__ void __launch_bounds__(128, fill16_min_blocks<K>()) k_fill16(FillArgs
         uint32_t wbn[2];
 #pragma unroll
         for (int h = 0; h < 2; h++) wbn[h] = load_window16<L, K>(A, wstart[h], 0, g);
-        for (int b = 0; b < nblk_warp; b++) {
+        // the first blocks (steps s < L), where lanes before their first column keep
+        // resetting it, run one step a loop body; the rest of the item runs without the
+        // reset, so no step of the main loop joins two definitions of X and F (which
+        // cost a register move a row)
+        int b = 0;
+        for (; b < nblk_warp && 8 * b < L; b++) {
+            uint32_t wb[2];
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                wb[h] = wbn[h];
+                wbn[h] = load_window16<L, K>(A, wstart[h], b + 1, g);
+            }
+#pragma unroll 1
+            for (int u = 0; u < 8; u++) step(8 * b + u, (wb[0] >> (2 * u)) & 3u, (wb[1] >> (2 * u)) & 3u, true);
+        }
+        for (; b < nblk_warp; b++) {
             uint32_t wb[2];
 #pragma unroll
             for (int h = 0; h < 2; h++) {
@@ -242,7 +257,7 @@ __global__ void __launch_bounds__(128, fill16_min_blocks<K>()) k_fill16(FillArgs
                 wbn[h] = load_window16<L, K>(A, wstart[h], b + 1, g);
             }
 #pragma unroll kStepUnroll
-            for (int u = 0; u < 8; u++) step(8 * b + u, (wb[0] >> (2 * u)) & 3u, (wb[1] >> (2 * u)) & 3u, 8 * b < L);
+            for (int u = 0; u < 8; u++) step(8 * b + u, (wb[0] >> (2 * u)) & 3u, (wb[1] >> (2 * u)) & 3u, false);
         }
 
         // per job of the pair: best, second best, overflow flag
