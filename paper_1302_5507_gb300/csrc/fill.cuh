@@ -203,166 +203,181 @@ __global__ void __launch_bounds__(128) k_fill32(FillArgs A) {
         const int gn = LOCAL ? 0 : (rows - 1) / K;
         const int rn = LOCAL ? 0 : (rows - 1) % K;
 
-        uint32_t wb_next = load_window16<L, K>(A, wstart, 0, g);
-        for (int b = 0; b < nblk_warp; b++) {
-            const uint32_t wb = wb_next;
-            wb_next = load_window16<L, K>(A, wstart, b + 1, g);
-            // the direction passes keep the step loop rolled: their step body (K rows
-            // of compare/select and nibble packing) is large, and eight copies of it
-            // overflow the instruction cache
-            constexpr int kUnrollSteps = (DIR && !HGT) ? 1 : 8;
-#pragma unroll kUnrollSteps
-            for (int u = 0; u < 8; u++) {
-                const int s = 8 * b + u;
-                const int i = s - g + 1;
-                uint32_t dw[(K + 7) / 8];
-                uint32_t hw[HGT ? KH : 1];
-                if (DIR) {
+        // the direction passes keep the step loop rolled: their step body (K rows of
+        // compare/select and nibble packing) is large, and eight copies of it overflow
+        // the instruction cache.  In the other LOCAL passes the first blocks (steps
+        // s < L), where lanes before their first column keep resetting it, run one step
+        // a loop body and the rest without the reset, so no step of the main loop joins
+        // two definitions of the column registers (which cost a register move a row);
+        // the GLOCAL score pass measured 1.5 % slower that way and keeps the reset test
+        constexpr int kUnrollSteps = (DIR && !HGT) ? 1 : 8;
+        constexpr bool kPeel = kUnrollSteps > 1 && LOCAL;
+        auto step = [&](const int b, const int u, const uint32_t wb, const bool first) {
+            const int s = 8 * b + u;
+            const int i = s - g + 1;
+            uint32_t dw[(K + 7) / 8];
+            uint32_t hw[HGT ? KH : 1];
+            if (DIR) {
 #pragma unroll
-                    for (int k = 0; k < (K + 7) / 8; k++) dw[k] = 0u;
-                }
-                if (HGT) {
+                for (int k = 0; k < (K + 7) / 8; k++) dw[k] = 0u;
+            }
+            if (HGT) {
 #pragma unroll
-                    for (int k = 0; k < KH; k++) hw[k] = 0u;
-                }
-                int32_t hg_up = __shfl_up_sync(FULL, hg_bot, 1, L);
-                int32_t e_up = __shfl_up_sync(FULL, e_bot, 1, L);
-                int32_t cm_up = 0;
-                if (BEST && LOCAL) cm_up = __shfl_up_sync(FULL, cm_bot, 1, L);
-                if (PROF) {
-                    hg_up = hg_up * nf + hg_c;
-                    e_up = e_up * nf + e_c;
-                    cm_up = cm_up * nf;
-                } else if (g == 0) {
-                    hg_up = S.GO; e_up = kNeg32; cm_up = 0;
-                }
-                int32_t diag = h_up_prev;
-                h_up_prev = hg_up;
-                const uint32_t t = (wb >> (2 * u)) & 3u;
-                const uint32_t mk = SPROF ? 0u : (t == 0 ? mA : (t == 1 ? mC : (t == 2 ? mG : mT)));
-                const int4* pt = reinterpret_cast<const int4*>(prof) + (t * K4) * 32 + lane;
-                int4 dq = make_int4(0, 0, 0, 0);
-                int32_t e = e_up, hga = hg_up;
-                int32_t lm = 0, hpair = 0;
-                // score pass: the diagonal term of row r+1 is formed while row r still
-                // holds H(i-1, j) (no copy of the old value is kept)
-                int32_t gcur = 0;
+                for (int k = 0; k < KH; k++) hw[k] = 0u;
+            }
+            int32_t hg_up = __shfl_up_sync(FULL, hg_bot, 1, L);
+            int32_t e_up = __shfl_up_sync(FULL, e_bot, 1, L);
+            int32_t cm_up = 0;
+            if (BEST && LOCAL) cm_up = __shfl_up_sync(FULL, cm_bot, 1, L);
+            if (PROF) {
+                hg_up = hg_up * nf + hg_c;
+                e_up = e_up * nf + e_c;
+                cm_up = cm_up * nf;
+            } else if (g == 0) {
+                hg_up = S.GO; e_up = kNeg32; cm_up = 0;
+            }
+            int32_t diag = h_up_prev;
+            h_up_prev = hg_up;
+            const uint32_t t = (wb >> (2 * u)) & 3u;
+            const uint32_t mk = SPROF ? 0u : (t == 0 ? mA : (t == 1 ? mC : (t == 2 ? mG : mT)));
+            const int4* pt = reinterpret_cast<const int4*>(prof) + (t * K4) * 32 + lane;
+            int4 dq = make_int4(0, 0, 0, 0);
+            int32_t e = e_up, hga = hg_up;
+            int32_t lm = 0, hpair = 0;
+            // score pass: the diagonal term of row r+1 is formed while row r still
+            // holds H(i-1, j) (no copy of the old value is kept)
+            int32_t gcur = 0;
+            if (SPROF) {
+                dq = pt[0];
+                gcur = add_fma(dq.x, diag, one);
+            }
+#pragma unroll
+            for (int r = 0; r < K; r++) {
+                int32_t gv;
                 if (SPROF) {
-                    dq = pt[0];
-                    gcur = add_fma(dq.x, diag, one);
-                }
-#pragma unroll
-                for (int r = 0; r < K; r++) {
-                    int32_t gv;
-                    if (SPROF) {
-                        gv = gcur;
-                        if (r + 1 < K) {
-                            const int rn = r + 1;
-                            if ((rn & 3) == 0) dq = pt[(rn / 4) * 32];
-                            const int32_t dn = (rn & 3) == 0 ? dq.x : (rn & 3) == 1 ? dq.y : (rn & 3) == 2 ? dq.z : dq.w;
-                            gcur = add_fma(dn, HG[r], one);
-                        }
-                    } else {
-                        const int32_t d = ((mk >> r) & 1u) ? S.dm : S.dx;
-                        gv = diag + d;                    // H(i-1,j-1) + delta
-                        diag = HG[r];
+                    gv = gcur;
+                    if (r + 1 < K) {
+                        const int rn = r + 1;
+                        if ((rn & 3) == 0) dq = pt[(rn / 4) * 32];
+                        const int32_t dn = (rn & 3) == 0 ? dq.x : (rn & 3) == 1 ? dq.y : (rn & 3) == 2 ? dq.z : dq.w;
+                        gcur = add_fma(dn, HG[r], one);
                     }
-                    int32_t f, h;
-                    if (!DIR || HGT) {
-                        f = addmax(F[r], S.GE, HG[r]);    // max(F(i-1,j)+GE, H(i-1,j)+GO)
-                        e = addmax(e, S.GE, hga);         // max(E(i,j-1)+GE, H(i,j-1)+GO)
-                        h = LOCAL ? __vimax3_s32_relu(gv, e, f) : __vimax3_s32(gv, e, f);
-                        // byte r & 3 of word r / 4 (0..254: every score is below 255)
-                        if (HGT) hw[r >> 2] |= (uint32_t)h << (8 * (r & 3));
-                    } else {
-                        const int32_t fe = F[r] + S.GE;
-                        const bool fopen = HG[r] >= fe;
-                        f = fopen ? HG[r] : fe;
-                        const int32_t ee = e + S.GE;
-                        const bool eopen = hga >= ee;
-                        e = eopen ? hga : ee;
-                        const bool pF = f >= e;
-                        const int32_t ef = pF ? f : e;
-                        const bool pG = gv >= ef;
-                        h = pG ? gv : ef;
-                        uint32_t src = pG ? 1u : (pF ? 2u : 3u);
-                        if (LOCAL && h <= 0) { h = 0; src = 0u; }
-                        const uint32_t nib = src | (eopen ? 0u : 4u) | (fopen ? 0u : 8u);
-                        dw[r >> 3] |= nib << (4 * (r & 7));
-                    }
-                    F[r] = f;
-                    HG[r] = SPROF ? add_fma(h, S.GO, one) : h + S.GO;
-                    hga = HG[r];
-                    if (BEST && LOCAL) {
-                        if (PROF) {
-                            // column maximum of keys H*1024 + (1023 - r): the maximum key holds the
-                            // largest H and, among equal H, the first row (two rows per 3-input max)
-                            const int32_t key = add_fma(h, 1023 - r, 1024 * one);
-                            if ((r & 1) == 1) lm = __vimax3_s32(lm, hpair, key);
-                            else if (r == K - 1) lm = max(lm, key);
-                            else hpair = key;
-                        } else {
-                            lm = max(lm, h);
-                        }
-                    }
+                } else {
+                    const int32_t d = ((mk >> r) & 1u) ? S.dm : S.dx;
+                    gv = diag + d;                    // H(i-1,j-1) + delta
+                    diag = HG[r];
                 }
-                hg_bot = HG[K - 1];
-                e_bot = e;
-                if (8 * b < L && s < g) {                 // before this lane's first column
-                    reset_col0();
-                    h_up_prev = hup0;
+                int32_t f, h;
+                if (!DIR || HGT) {
+                    f = addmax(F[r], S.GE, HG[r]);    // max(F(i-1,j)+GE, H(i-1,j)+GO)
+                    e = addmax(e, S.GE, hga);         // max(E(i,j-1)+GE, H(i,j-1)+GO)
+                    h = LOCAL ? __vimax3_s32_relu(gv, e, f) : __vimax3_s32(gv, e, f);
+                    // byte r & 3 of word r / 4 (0..254: every score is below 255)
+                    if (HGT) hw[r >> 2] |= (uint32_t)h << (8 * (r & 3));
+                } else {
+                    const int32_t fe = F[r] + S.GE;
+                    const bool fopen = HG[r] >= fe;
+                    f = fopen ? HG[r] : fe;
+                    const int32_t ee = e + S.GE;
+                    const bool eopen = hga >= ee;
+                    e = eopen ? hga : ee;
+                    const bool pF = f >= e;
+                    const int32_t ef = pF ? f : e;
+                    const bool pG = gv >= ef;
+                    h = pG ? gv : ef;
+                    uint32_t src = pG ? 1u : (pF ? 2u : 3u);
+                    if (LOCAL && h <= 0) { h = 0; src = 0u; }
+                    const uint32_t nib = src | (eopen ? 0u : 4u) | (fopen ? 0u : 8u);
+                    dw[r >> 3] |= nib << (4 * (r & 7));
                 }
-                const bool active = (unsigned)(i - 1) < (unsigned)w;
-                if (BEST) {
+                F[r] = f;
+                HG[r] = SPROF ? add_fma(h, S.GO, one) : h + S.GO;
+                hga = HG[r];
+                if (BEST && LOCAL) {
                     if (PROF) {
-                        // the group's column maximum (LOCAL: key; GLOCAL: H(n, i) + S_GO)
-                        // goes to the column's slot from the last lane, for every step
-                        // (steps outside the window land in the slack slots)
-                        if (LOCAL) {
-                            const int32_t cm = __viaddmax_s32(lm, key_shift, cm_up);
-                            cm_bot = cm;
-                            if (g == L - 1 && cb_ok(i)) cb[i - 1] = cm;
-                        } else {
-                            if (g == L - 1 && cb_ok(i)) cb[i - 1] = HG[K - 1];
-                        }
-                    } else if (LOCAL) {
-                        const int32_t cm = max(cm_up, lm);
-                        cm_bot = cm;
-                        if (active) {
-                            if (g == L - 1 && cb_ok(i)) cb[i - 1] = cm;
-                            if (lm > bv) {
-                                bv = lm;
-                                bi = i;
-                                int rr = K - 1;
-#pragma unroll
-                                for (int r = K - 1; r >= 0; r--)
-                                    if (HG[r] - S.GO == lm) rr = r;
-                                br = rr;
-                            }
-                        }
-                    } else if (active && g == gn) {
-                        int32_t hv = HG[0];
-#pragma unroll
-                        for (int r = 1; r < K; r++)
-                            if (r == rn) hv = HG[r];
-                        if (cb_ok(i)) cb[i - 1] = hv - S.GO;
-                    }
-                }
-                if (DIR && !HGT && b < nblk) {
-#pragma unroll
-                    for (int k = 0; k < (K + 7) / 8; k++) {
-                        const uint64_t at = aoff + ((uint64_t)s * ((K + 7) / 8) + k) * L + g;
-                        if (SA_GUARD(at < A.arena_cap, A.dbg, kSiteArena)) A.arena[at] = dw[k];
-                    }
-                }
-                if (HGT && b < nblk) {
-#pragma unroll
-                    for (int k = 0; k < KH; k++) {
-                        const uint64_t at = aoff + ((uint64_t)s * KH + k) * L + g;
-                        if (SA_GUARD(at < A.arena_cap, A.dbg, kSiteArena)) A.arena[at] = hw[k];
+                        // column maximum of keys H*1024 + (1023 - r): the maximum key holds the
+                        // largest H and, among equal H, the first row (two rows per 3-input max)
+                        const int32_t key = add_fma(h, 1023 - r, 1024 * one);
+                        if ((r & 1) == 1) lm = __vimax3_s32(lm, hpair, key);
+                        else if (r == K - 1) lm = max(lm, key);
+                        else hpair = key;
+                    } else {
+                        lm = max(lm, h);
                     }
                 }
             }
+            hg_bot = HG[K - 1];
+            e_bot = e;
+            if (first && s < g) {                     // before this lane's first column
+                reset_col0();
+                h_up_prev = hup0;
+            }
+            const bool active = (unsigned)(i - 1) < (unsigned)w;
+            if (BEST) {
+                if (PROF) {
+                    // the group's column maximum (LOCAL: key; GLOCAL: H(n, i) + S_GO)
+                    // goes to the column's slot from the last lane, for every step
+                    // (steps outside the window land in the slack slots)
+                    if (LOCAL) {
+                        const int32_t cm = __viaddmax_s32(lm, key_shift, cm_up);
+                        cm_bot = cm;
+                        if (g == L - 1 && cb_ok(i)) cb[i - 1] = cm;
+                    } else {
+                        if (g == L - 1 && cb_ok(i)) cb[i - 1] = HG[K - 1];
+                    }
+                } else if (LOCAL) {
+                    const int32_t cm = max(cm_up, lm);
+                    cm_bot = cm;
+                    if (active) {
+                        if (g == L - 1 && cb_ok(i)) cb[i - 1] = cm;
+                        if (lm > bv) {
+                            bv = lm;
+                            bi = i;
+                            int rr = K - 1;
+#pragma unroll
+                            for (int r = K - 1; r >= 0; r--)
+                                if (HG[r] - S.GO == lm) rr = r;
+                            br = rr;
+                        }
+                    }
+                } else if (active && g == gn) {
+                    int32_t hv = HG[0];
+#pragma unroll
+                    for (int r = 1; r < K; r++)
+                        if (r == rn) hv = HG[r];
+                    if (cb_ok(i)) cb[i - 1] = hv - S.GO;
+                }
+            }
+            if (DIR && !HGT && b < nblk) {
+#pragma unroll
+                for (int k = 0; k < (K + 7) / 8; k++) {
+                    const uint64_t at = aoff + ((uint64_t)s * ((K + 7) / 8) + k) * L + g;
+                    if (SA_GUARD(at < A.arena_cap, A.dbg, kSiteArena)) A.arena[at] = dw[k];
+                }
+            }
+            if (HGT && b < nblk) {
+#pragma unroll
+                for (int k = 0; k < KH; k++) {
+                    const uint64_t at = aoff + ((uint64_t)s * KH + k) * L + g;
+                    if (SA_GUARD(at < A.arena_cap, A.dbg, kSiteArena)) A.arena[at] = hw[k];
+                }
+            }
+        };
+        uint32_t wb_next = load_window16<L, K>(A, wstart, 0, g);
+        int b0 = 0;
+        if (kPeel) {
+            for (; b0 < nblk_warp && 8 * b0 < L; b0++) {
+                const uint32_t wb = wb_next;
+                wb_next = load_window16<L, K>(A, wstart, b0 + 1, g);
+#pragma unroll 1
+                for (int u = 0; u < 8; u++) step(b0, u, wb, true);
+            }
+        }
+        for (; b0 < nblk_warp; b0++) {
+            const uint32_t wb = wb_next;
+            wb_next = load_window16<L, K>(A, wstart, b0 + 1, g);
+#pragma unroll kUnrollSteps
+            for (int u = 0; u < 8; u++) step(b0, u, wb, !kPeel && 8 * b0 < L);
         }
 
         if (BEST) {
