@@ -167,7 +167,21 @@ __global__ void __launch_bounds__(128) k_fill16h(FillArgs A) {
         uint32_t wbn[2];
 #pragma unroll
         for (int h = 0; h < 2; h++) wbn[h] = load_window16<L, K>(A, wstart[h], 0, g);
-        for (int b = 0; b < nblk_warp; b++) {
+        // the first blocks (steps s < L, column-0 resets) one step a loop body, the
+        // rest without the reset (no register move a row to join two definitions)
+        int b = 0;
+        for (; b < nblk_warp && 8 * b < L; b++) {
+            uint32_t wb[2];
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                wb[h] = wbn[h];
+                wbn[h] = load_window16<L, K>(A, wstart[h], b + 1, g);
+            }
+#pragma unroll 1
+            for (int u = 0; u < 8; u++)
+                step(b, 8 * b + u, (wb[0] >> (2 * u)) & 3u, (wb[1] >> (2 * u)) & 3u, true);
+        }
+        for (; b < nblk_warp; b++) {
             uint32_t wb[2];
 #pragma unroll
             for (int h = 0; h < 2; h++) {
@@ -177,7 +191,7 @@ __global__ void __launch_bounds__(128) k_fill16h(FillArgs A) {
             // four steps a loop body (the whole eight overflow the instruction cache)
 #pragma unroll 4
             for (int u = 0; u < 8; u++)
-                step(b, 8 * b + u, (wb[0] >> (2 * u)) & 3u, (wb[1] >> (2 * u)) & 3u, 8 * b < L);
+                step(b, 8 * b + u, (wb[0] >> (2 * u)) & 3u, (wb[1] >> (2 * u)) & 3u, false);
         }
         __syncwarp();
     }
