@@ -88,14 +88,22 @@ namespace sa {
 // value is strictly above H(neighbour) + S_GO -- so the CIGAR is the one the
 // nibble walk gives.  E(i,j) (the same maximum up the column) is looked at first:
 // below H it leaves the deletion as the only source, and only an E equal to H
-// needs F, whose scan stops at the first term reaching H or once no height up to
-// `hmax` could.  height(ii, jj) gives the DP value or kNeg32 off the stored area
-// (row 0 and column 0 are borders of value 0); match(ii, jj) tells whether
-// window base ii equals read base jj.
+// needs F.  height(ii, jj) gives the DP value or kNeg32 off the stored area (row
+// 0 and column 0 are borders of value 0); match(ii, jj) tells whether window
+// base ii equals read base jj.
+//
+// The walk is one flat loop that reads one height an iteration: the two gap scans
+// are states of it (SCAN_E, SCAN_F), not inner loops, so a lane scanning a long
+// row or column no longer holds the other lanes of its warp at every step.  A
+// scan term H(i',j') + S_GO + (k-1) S_GE is bounded with H(i',j') <= hmax and,
+// in LOCAL, H(i',j') <= a min(i',j') (a path to (i',j') has at most that many
+// matches); once the bound is below H no later term can reach it, and the scan
+// stops -- only its comparison with H is used, so the decisions are unchanged.
 template <class Height, class Match>
 __device__ __forceinline__ WalkEnd walk_heights(int i, int j, int32_t h, int imax, int rows, int32_t hmax,
                                                 int32_t GO, int32_t GE, int32_t sa, int32_t sb, Height height,
                                                 Match match, uint32_t* ops, uint32_t cap) {
+    enum { kAtH = 0, kInsRun = 1, kDelRun = 2, kScanE = 3, kScanF = 4 };
     int nrev = 0;
     uint32_t cur_op = 15u, cur_len = 0;
     auto emit = [&](uint32_t op) {
@@ -104,52 +112,71 @@ __device__ __forceinline__ WalkEnd walk_heights(int i, int j, int32_t h, int ima
         cur_op = op;
         cur_len = 1;
     };
-    // max over k >= 1 of height(i - k*di, j - k*dj) + GO + (k-1) GE, or a value
-    // below `want` once no term from there on can reach it (heights are <= hmax);
-    // only its comparison with `want` is used
-    auto gap_max = [&](int di, int dj, int32_t want) -> int32_t {
-        int32_t f = kNeg32;
-        const int n = di ? i : j;
-        for (int kk = 1; kk <= n; kk++) {
-            if (hmax + GO + (kk - 1) * GE < want) break;   // no term from here on reaches want
-            const int32_t hx = height(i - kk * di, j - kk * dj);
-            if (hx == kNeg32) break;                  // off the stored area: the rest is -inf
-            f = max(f, hx + GO + (kk - 1) * GE);
-            if (f >= want) break;                     // F and E never exceed H: f == want
-        }
-        return f;
-    };
-    int32_t cur = 0;
-    int state = 0;                                    // 0 H, 1 E (insertion), 2 F (deletion)
+    int32_t cur = 0, acc = kNeg32;                    // gap run value; a scan's running maximum
+    int state = kAtH, kk = 0;
     int budget = 2 * (imax + rows) + 4;
     bool bad = (i < 1 || j < 1 || j > rows || i > imax || height(i, j) != h);
     while (!bad) {
-        if (--budget < 0 || nrev >= (int)cap - 1) { bad = true; break; }
-        if (state == 0) {
-            if (i == 0 || j == 0 || h <= 0) break;
-            const int32_t hd = height(i - 1, j - 1);
-            if (hd != kNeg32 && hd + (match(i, j) ? sa : sb) == h) {
-                emit(0u);
-                i--; j--; h = hd;
-                continue;
+        // the cell this iteration reads (ii < 0: none, the scan stops)
+        int ii = -1, jj = 0;
+        if (state == kScanE || state == kScanF) {
+            const bool up = state == kScanE;
+            const int n = up ? j : i;
+            const int32_t hb = min(hmax, sa * (up ? j - kk : min(j, i - kk)));
+            if (kk <= n && hb + GO + (kk - 1) * GE >= h) {
+                ii = up ? i : i - kk;
+                jj = up ? j - kk : j;
             }
-            const int32_t e = gap_max(0, 1, h);
-            if (e < h) state = 2;                     // F is the only source left
-            else state = (gap_max(1, 0, h) == h) ? 2 : 1;
-            cur = h;
-        } else if (state == 2) {
-            if (i < 1) { bad = true; break; }
+        } else {
+            if (--budget < 0 || nrev >= (int)cap - 1) { bad = true; break; }
+            if (state == kAtH) {
+                if (i == 0 || j == 0 || h <= 0) break;
+                ii = i - 1;
+                jj = j - 1;
+            } else if (state == kDelRun) {
+                if (i < 1) { bad = true; break; }
+                ii = i - 1;
+                jj = j;
+            } else {
+                if (j < 1) { bad = true; break; }
+                ii = i;
+                jj = j - 1;
+            }
+        }
+        const int32_t hx = ii >= 0 ? height(ii, jj) : kNeg32;
+        if (state == kAtH) {
+            if (hx != kNeg32 && hx + (match(i, j) ? sa : sb) == h) {
+                emit(0u);
+                i--; j--; h = hx;
+            } else {
+                state = kScanE;
+                kk = 1;
+                acc = kNeg32;
+                cur = h;
+            }
+        } else if (state == kScanE || state == kScanF) {
+            bool stop = hx == kNeg32;                 // off the stored area or the bound: done
+            if (!stop) {
+                acc = max(acc, hx + GO + (kk - 1) * GE);
+                stop = acc >= h;                      // F and E never exceed H: acc == h
+            }
+            if (!stop) {
+                kk++;
+            } else if (state == kScanE) {
+                if (acc < h) state = kDelRun;         // F is the only source left
+                else { state = kScanF; kk = 1; acc = kNeg32; }
+            } else {
+                state = (acc == h) ? kDelRun : kInsRun;
+            }
+        } else if (state == kDelRun) {
             emit(2u);
-            const int32_t hn = height(i - 1, j);
             i--;
-            if (hn != kNeg32 && cur <= hn + GO) { state = 0; h = hn; }
+            if (hx != kNeg32 && cur <= hx + GO) { state = kAtH; h = hx; }
             else cur -= GE;
         } else {
-            if (j < 1) { bad = true; break; }
             emit(1u);
-            const int32_t hn = height(i, j - 1);
             j--;
-            if (hn != kNeg32 && cur <= hn + GO) { state = 0; h = hn; }
+            if (hx != kNeg32 && cur <= hx + GO) { state = kAtH; h = hx; }
             else cur -= GE;
         }
     }
