@@ -277,11 +277,15 @@ __device__ __forceinline__ void band_h_walk(const BandArgs& A, uint32_t pos, uin
                 i--; j--; h = hd;
                 continue;
             }
+            // F(i,j) compared with H: the scan stops once it reaches H (F never exceeds
+            // it) or once no later term can (H(i',j) <= min(best, a min(i',j)) in LOCAL)
             int32_t f = kNeg32;
             for (int kk = 1; kk <= i; kk++) {
+                if (min(st.best, sa * min(j, i - kk)) + GO + (kk - 1) * GE < h) break;
                 const int32_t hx = height(i - kk, j);
                 if (hx == kNeg32) break;                 // left of the band: the rest is -inf
                 f = max(f, hx + GO + (kk - 1) * GE);
+                if (f >= h) break;
             }
             state = (f == h) ? 2 : 1;
             cur = h;
