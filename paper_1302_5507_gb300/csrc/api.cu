@@ -30,6 +30,10 @@ using namespace sa;
 
 namespace {
 
+// rectangle jobs from which their height walks run over the rectangle list instead of
+// one thread per job of the batch (about two waves of warps of the walk kernel)
+constexpr uint32_t kListWalkMin = 16384;
+
 thread_local char g_err[512] = "";
 
 int fail(int code, const char* fmt, ...) {
@@ -815,10 +819,30 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
                             CU(cudaStreamWaitEvent(st, ws.join[kNumBand + c], 0));
                 if (wv == 0) trect1 = tm.mark();
                 HeightWalk hwk{heights ? 1 : 0, X.d_words, ws.rpack.as<uint32_t>(), rw, sc};
-                launch_traceback(d_jobs, 0, n_jobs, ws.state.as<JobState>(), ws.rect.as<Rect>(),
-                                 ws.arena.as<uint32_t>(), bl, (int)wv, mode, 0, -1, min_score,
-                                 ws.tmp_ops.as<uint32_t>(), tmp_stride, ws.tb.as<TbOut>(), &dp->st.bad_walk, hwk,
-                                 st);
+                const uint32_t n_rect = hp->rect_begin[kNumCfg];
+                if (heights && n_rect >= kListWalkMin) {
+                    // many rectangle jobs: the height walks one thread per rectangle-list
+                    // entry (every lane walks, fewer warps); the rest (gapless jobs) once,
+                    // with the first wave.  Few of them walk faster one a warp, in
+                    // parallel (low-similarity batch, 286k walks: 3.47 -> 3.2 ms; uneven
+                    // batch, 1.8k walks packed: 0.45 -> 0.86 ms)
+                    if (wv == 0) {
+                        launch_traceback(d_jobs, 0, n_jobs, ws.state.as<JobState>(), ws.rect.as<Rect>(),
+                                         ws.arena.as<uint32_t>(), bl, 0, mode, 0, -1, min_score,
+                                         ws.tmp_ops.as<uint32_t>(), tmp_stride, ws.tb.as<TbOut>(),
+                                         &dp->st.bad_walk, hwk, st, nullptr, 1);
+                        launches++;
+                    }
+                    launch_traceback(d_jobs, 0, n_rect, ws.state.as<JobState>(), ws.rect.as<Rect>(),
+                                     ws.arena.as<uint32_t>(), bl, (int)wv, mode, 0, -1, min_score,
+                                     ws.tmp_ops.as<uint32_t>(), tmp_stride, ws.tb.as<TbOut>(), &dp->st.bad_walk,
+                                     hwk, st, rect_list, 2);
+                } else {
+                    launch_traceback(d_jobs, 0, n_jobs, ws.state.as<JobState>(), ws.rect.as<Rect>(),
+                                     ws.arena.as<uint32_t>(), bl, (int)wv, mode, 0, -1, min_score,
+                                     ws.tmp_ops.as<uint32_t>(), tmp_stride, ws.tb.as<TbOut>(), &dp->st.bad_walk,
+                                     hwk, st);
+                }
                 launches++;
                 CU(cudaGetLastError());
                 trace("traceback");

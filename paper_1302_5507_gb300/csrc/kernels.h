@@ -97,11 +97,13 @@ struct HeightWalk {
     uint32_t rw;
     Score sc;
 };
+// part 0: every job of [job_begin, job_begin + n_jobs); part 1: the same jobs but the
+// rectangle jobs' height walks; part 2: those walks for list[job_begin ..] (job ids)
 void launch_traceback(const sa_job* jobs, uint32_t job_begin, uint32_t n_jobs, const JobState* state,
                       const Rect* rect, const uint32_t* arena, const BandLayout& band, int wave,
                       int mode, int plain, int cfg_force, int32_t min_score, uint32_t* tmp_ops,
                       uint32_t tmp_stride, TbOut* tb, unsigned* err_job, const HeightWalk& hw,
-                      cudaStream_t st);
+                      cudaStream_t st, const uint32_t* list = nullptr, int part = 0);
 void launch_iota(uint32_t* p, uint32_t n, cudaStream_t st);
 void launch_cigar_count(const sa_job* jobs, uint32_t n_jobs, const JobState* state, const TbOut* tb,
                         int mode, int want_cigar, int32_t min_score, uint32_t* count,

@@ -668,10 +668,14 @@ __global__ void k_traceback(const sa_job* __restrict__ jobs, uint32_t job_begin,
                             int plain,
                             int cfg_force, int32_t min_score, uint32_t* __restrict__ tmp_ops,
                             uint32_t tmp_stride, TbOut* __restrict__ tb, unsigned* err_job,
-                            HeightWalk hw) {
+                            HeightWalk hw, const uint32_t* __restrict__ list, int part) {
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= n_jobs) return;
-    const uint32_t job = job_begin + tid;
+    // part 0: every job; part 1: every job but the rectangle jobs' height walks;
+    // part 2: only those walks, one thread per entry of the rectangle list (every
+    // lane of a warp walks, and neighbouring entries have rectangles of about the
+    // same size)
+    const uint32_t job = list ? list[job_begin + tid] : job_begin + tid;
     const Rect R = rect[job];
     const int bidx = band_index(R.cls);
     const bool banded = bidx >= 0;
@@ -681,7 +685,7 @@ __global__ void k_traceback(const sa_job* __restrict__ jobs, uint32_t job_begin,
     out.ref_begin_rel = -1;
     if (R.cls == kClsDiag && !plain) {
         // gapless path: R.rows diagonal steps from (i*, j*) = (start_i, start_j)
-        if (wave != 0) return;
+        if (wave != 0 || part == 2) return;
         tmp_ops[(uint64_t)job * tmp_stride] = ((uint32_t)R.rows << 4) | 0u;
         out.n_rev = 1;
         out.read_begin = R.start_j - R.rows;
@@ -713,7 +717,9 @@ __global__ void k_traceback(const sa_job* __restrict__ jobs, uint32_t job_begin,
     }
     const int imax_walk = banded ? st.i_star : R.w;
     const uint64_t off = R.off;
+    if (part == 2 && !(hw.on && !plain)) return;
     if (hw.on && !banded && !plain) {
+        if (part == 1) return;                       // walked by the list launch
         // byte heights of the rectangle (LOCAL, every score below 255); column 0 of
         // the rectangle (window column i_lo - 1) and row 0 are borders of value 0
         const sa_job J = jobs[job];
@@ -790,11 +796,11 @@ void launch_traceback(const sa_job* jobs, uint32_t job_begin, uint32_t n_jobs, c
                       const Rect* rect, const uint32_t* arena, const BandLayout& band, int wave,
                       int mode, int plain, int cfg_force, int32_t min_score, uint32_t* tmp_ops,
                       uint32_t tmp_stride, TbOut* tb, unsigned* err_job, const HeightWalk& hw,
-                      cudaStream_t st) {
+                      cudaStream_t st, const uint32_t* list, int part) {
     if (!n_jobs) return;
     k_traceback<<<(n_jobs + 127) / 128, 128, 0, st>>>(jobs, job_begin, n_jobs, state, rect, arena,
                                                        band, wave, mode, plain, cfg_force, min_score,
-                                                       tmp_ops, tmp_stride, tb, err_job, hw);
+                                                       tmp_ops, tmp_stride, tb, err_job, hw, list, part);
 }
 
 __global__ void k_iota(uint32_t* __restrict__ p, uint32_t n) {
