@@ -441,7 +441,7 @@ __device__ __forceinline__ uint32_t pack_s16x2(int32_t lo, int32_t hi) {
 // the border's H = 0 and column 1 sees F = H(0,j) + S_GO as from the border; no
 // slot needs an edge test.  The walk never reads left of column 0.  A job with
 // fewer rows than its partner computes the extra rows without storing them.
-template <int B>
+template <int B, bool ROWS2>
 __global__ void __launch_bounds__(128) k_band_h2(BandArgs A) {
     constexpr int W = B / 4;                   // words of heights a row
     constexpr int NH = B > 32 ? 2 : 1;
@@ -481,43 +481,76 @@ __global__ void __launch_bounds__(128) k_band_h2(BandArgs A) {
         Es[k] = NEG2;
     }
     const int rows = max(rowsA, rowsB);
-    for (int j = 1; j <= rows; j++) {
+    // one row of the pair: its match bits, the ends of its F chain and four slots'
+    // heights awaiting their byte stores
+    struct Row {
+        uint64_t mA[NH], mB[NH];
+        uint32_t wd, xleft, fleft, xq[4];
+        int j;
+        bool stA, stB;
+    };
+    auto row_begin = [&](Row& R, const int j) {
         const uint32_t rbA = (__ldg(rpA + ((j - 1) >> 4)) >> (2 * ((j - 1) & 15))) & 3u;
         const uint32_t rbB = (__ldg(rpB + ((j - 1) >> 4)) >> (2 * ((j - 1) & 15))) & 3u;
-        uint64_t mA[NH], mB[NH];
-        band_match_bits<NH>(refw, A.ref_len, refA, j + dloA, rbA, mA);
-        band_match_bits<NH>(refw, A.ref_len, refB, j + dloB, rbB, mB);
-        const bool stA = j <= rowsA, stB = j <= rowsB;
-        uint32_t xleft = NEG2, fleft = NEG2, wd = 0u;
-        uint32_t xq[4];
+        band_match_bits<NH>(refw, A.ref_len, refA, j + dloA, rbA, R.mA);
+        band_match_bits<NH>(refw, A.ref_len, refB, j + dloB, rbB, R.mB);
+        R.j = j;
+        R.stA = j <= rowsA;
+        R.stB = j <= rowsB;
+        R.xleft = NEG2;
+        R.fleft = NEG2;
+        R.wd = 0u;
+    };
+    // slot k of row R.j: reads the previous row's slots k (diagonal) and k + 1 (up)
+    // and leaves its own values in slot k
+    auto slot = [&](Row& R, const int k) {
+        if ((k & 7) == 0) {                    // slots 8c .. 8c+7: A's bits low, B's high
+            const int c = k >> 3;
+            const uint32_t wa = (uint32_t)(R.mA[c >> 2] >> (16 * (c & 3))) & 0xFFFFu;
+            const uint32_t wb = (uint32_t)(R.mB[c >> 2] >> (16 * (c & 3))) << 16;
+            R.wd = wa | wb;
+        }
+        const uint32_t sel = (R.wd >> (2 * (k & 7))) & 0x00010001u;
+        const uint32_t d2 = sel * AB + SB2;                         // delta + beta, both halves
+        const uint32_t en = __viaddmax_s16x2(Es[k + 1], GE2, Xs[k + 1]);
+        const uint32_t fn = __viaddmax_s16x2(R.fleft, GE2, R.xleft);
+        const uint32_t gt = __viaddmax_s16x2(Xs[k], d2, BETA2);
+        const uint32_t x = __vimax3_s16x2(gt, en, fn) * one + GO2C;
+        Xs[k] = x;
+        Es[k] = en;
+        R.xleft = x;
+        R.fleft = fn;
+        R.xq[k & 3] = x;
+        if ((k & 3) == 3) {
+            // bytes of four slots: [A0 A1 B0 B1], [A2 A3 B2 B3] -> A0..A3, B0..B3
+            const uint32_t t01 = __byte_perm(R.xq[0], R.xq[1], 0x6240);
+            const uint32_t t23 = __byte_perm(R.xq[2], R.xq[3], 0x6240);
+            const uint64_t at = ((uint64_t)(R.j - 1) * W + (k >> 2)) * 32;
+            if (R.stA && SA_GUARD(baseA + at < A.region_cap, A.dbg, kSiteBand)) outA[at] = __byte_perm(t01, t23, 0x5410);
+            if (R.stB && SA_GUARD(baseB + at < A.region_cap, A.dbg, kSiteBand)) outB[at] = __byte_perm(t01, t23, 0x7632);
+        }
+    };
+    int j = 1;
+    if (ROWS2) {
+        // two rows at once, the second one slot behind: its slot k - 1 reads the first
+        // row's slots k - 1 and k, both final by then, and the first row's slot k still
+        // finds the row above in slots k and k + 1; two independent F chains a thread
+        for (; j + 1 <= rows; j += 2) {
+            Row r0, r1;
+            row_begin(r0, j);
+            row_begin(r1, j + 1);
 #pragma unroll
-        for (int k = 0; k < B; k++) {
-            if ((k & 7) == 0) {                // slots 8c .. 8c+7: A's bits low, B's high
-                const int c = k >> 3;
-                const uint32_t wa = (uint32_t)(mA[c >> 2] >> (16 * (c & 3))) & 0xFFFFu;
-                const uint32_t wb = (uint32_t)(mB[c >> 2] >> (16 * (c & 3))) << 16;
-                wd = wa | wb;
-            }
-            const uint32_t sel = (wd >> (2 * (k & 7))) & 0x00010001u;
-            const uint32_t d2 = sel * AB + SB2;                     // delta + beta, both halves
-            const uint32_t en = __viaddmax_s16x2(Es[k + 1], GE2, Xs[k + 1]);
-            const uint32_t fn = __viaddmax_s16x2(fleft, GE2, xleft);
-            const uint32_t gt = __viaddmax_s16x2(Xs[k], d2, BETA2);
-            const uint32_t x = __vimax3_s16x2(gt, en, fn) * one + GO2C;
-            Xs[k] = x;
-            Es[k] = en;
-            xleft = x;
-            fleft = fn;
-            xq[k & 3] = x;
-            if ((k & 3) == 3) {
-                // bytes of four slots: [A0 A1 B0 B1], [A2 A3 B2 B3] -> A0..A3, B0..B3
-                const uint32_t t01 = __byte_perm(xq[0], xq[1], 0x6240);
-                const uint32_t t23 = __byte_perm(xq[2], xq[3], 0x6240);
-                const uint64_t at = ((uint64_t)(j - 1) * W + (k >> 2)) * 32;
-                if (stA && SA_GUARD(baseA + at < A.region_cap, A.dbg, kSiteBand)) outA[at] = __byte_perm(t01, t23, 0x5410);
-                if (stB && SA_GUARD(baseB + at < A.region_cap, A.dbg, kSiteBand)) outB[at] = __byte_perm(t01, t23, 0x7632);
+            for (int k = 0; k <= B; k++) {
+                if (k < B) slot(r0, k);
+                if (k >= 1) slot(r1, k - 1);
             }
         }
+    }
+    for (; j <= rows; j++) {
+        Row r0;
+        row_begin(r0, j);
+#pragma unroll
+        for (int k = 0; k < B; k++) slot(r0, k);
     }
 }
 
@@ -545,11 +578,11 @@ int launch_band(int cls, const BandArgs& a, bool heights, cudaStream_t st) {
             return 1;
         }
         if (cls == kClsBand32) {
-            if (pairs) k_band_h2<32><<<grid2, 128, 0, st>>>(a);
+            if (pairs) k_band_h2<32, true><<<grid2, 128, 0, st>>>(a);
             else k_band_h<32, false><<<grid, 128, 0, st>>>(a);
             k_band_h_walk<32><<<grid, 128, 0, st>>>(a);
         } else {
-            if (pairs) k_band_h2<64><<<grid2, 128, 0, st>>>(a);
+            if (pairs) k_band_h2<64, true><<<grid2, 128, 0, st>>>(a);
             else k_band_h<64, false><<<grid, 128, 0, st>>>(a);
             k_band_h_walk<64><<<grid, 128, 0, st>>>(a);
         }
