@@ -781,7 +781,13 @@ int run_device(Ctx& X, const sa_params* P, const Score& sc, const sa_job* d_jobs
             // writes only its jobs' arena ranges); a wave's fork re-records ws.fork,
             // whose earlier waits were already taken
             for (uint32_t wv = 0; wv < waves; wv++) {
-                const bool rect_fork = fork_buckets && total_words;
+                // several buckets with rectangle jobs: their passes run concurrently on
+                // the buckets' side streams (a large batch's few long rectangles a bucket
+                // leave most of the GPU idle in each launch)
+                int rect_buckets = 0;
+                for (int c = 0; c < kNumCfg; c++) rect_buckets += hp->rect_begin[c + 1] > hp->rect_begin[c];
+                const bool rect_fork = (fork_buckets || rect_buckets > 1) && !trace.on && total_words;
+                if (rect_fork) TRY(ensure_side(ws));
                 if (rect_fork) CU(cudaEventRecord(ws.fork, st));
                 for (int c = 0; c < kNumCfg && total_words; c++) {
                     const uint32_t r0 = hp->rect_begin[c], rn = hp->rect_begin[c + 1] - r0;
