@@ -10,7 +10,8 @@ X = H, E~ = E + beta, F~ = F + beta, G~ = max(X(i-1,j-1) + delta + beta, beta),
 X = max(G~, E~, F~) - beta, the last subtraction one 32-bit add with a fixed carry
 (every maximum is >= beta), delta + beta one multiply-add of the two match bits.
 Cells left of column 0 are computed as columns that never match (they come out
-H = 0, which makes column 0 the border).  The walk from (i*, j*) over the stored
+H = 0, which makes column 0 the border).  The kernel runs two rows at once, the second
+one slot behind, in place; that order must give the same heights as row by row.  The walk from (i*, j*) over the stored
 heights (diagonal first; else F(i,j) = H decides a deletion, scanned along the row
 and stopped once it reaches H or a bound min(best, a min(i',j)) puts every later
 term below it; gap runs while strictly above H(neighbour) + S_GO) must give the
@@ -62,8 +63,10 @@ def band_of(a, o, e, istar, jstar, best):
     return None, None
 
 
-def pair_pass(jobs, B, a, b, o, e):
-    """Heights of both jobs: {(i, j): H} for the band cells of real columns (i >= 0)."""
+def pair_pass(jobs, B, a, b, o, e, two_rows=False):
+    """Heights of both jobs: {(i, j): H} for the band cells of real columns (i >= 0).
+    two_rows: the kernel's order, rows j and j + 1 together with the second one slot
+    behind (row j + 1's slot k - 1 computed right after row j's slot k), in place."""
     beta = o + e
     GE2, BETA2 = pk(-e, -e), pk(beta, beta)
     SB2, AB = pk(-b + beta, -b + beta), a + b
@@ -72,27 +75,47 @@ def pair_pass(jobs, B, a, b, o, e):
     X = [0 if k < B else NEG2 for k in range(B + 1)]
     E = [NEG2] * (B + 1)
     out = [{}, {}]
-    for j in range(1, max(jb["rows"] for jb in jobs) + 1):
-        xleft = fleft = NEG2
+    rows = max(jb["rows"] for jb in jobs)
+    left = {}                                          # row -> [xleft, fleft]
+
+    def cell(j, k):
+        xleft, fleft = left[j]
+        sel = 0
+        for h, jb in enumerate(jobs):
+            i = j + jb["dlo"] + k
+            rb = jb["read"][j - 1] if j - 1 < len(jb["read"]) else -1
+            if 1 <= i <= len(jb["win"]) and jb["win"][i - 1] == rb:
+                sel |= 1 << (16 * h)
+        d2 = (sel * AB + SB2) & 0xFFFFFFFF
+        en = addmax(E[k + 1], GE2, X[k + 1])
+        fn = addmax(fleft, GE2, xleft)
+        gt = addmax(X[k], d2, BETA2)
+        x = (max3(gt, en, fn) + GO2C) & 0xFFFFFFFF
+        X[k], E[k] = x, en
+        left[j] = [x, fn]
+        for h, jb in enumerate(jobs):
+            i = j + jb["dlo"] + k
+            if j <= jb["rows"] and i >= 0:
+                v = lo16(x) if h == 0 else hi16(x)
+                assert 0 <= v <= 254
+                out[h][(i, j)] = v
+
+    j = 1
+    if two_rows:
+        while j + 1 <= rows:
+            left[j] = [NEG2, NEG2]
+            left[j + 1] = [NEG2, NEG2]
+            for k in range(B + 1):
+                if k < B:
+                    cell(j, k)
+                if k >= 1:
+                    cell(j + 1, k - 1)
+            j += 2
+    while j <= rows:
+        left[j] = [NEG2, NEG2]
         for k in range(B):
-            sel = 0
-            for h, jb in enumerate(jobs):
-                i = j + jb["dlo"] + k
-                rb = jb["read"][j - 1] if j - 1 < len(jb["read"]) else -1
-                if 1 <= i <= len(jb["win"]) and jb["win"][i - 1] == rb:
-                    sel |= 1 << (16 * h)
-            d2 = (sel * AB + SB2) & 0xFFFFFFFF
-            en = addmax(E[k + 1], GE2, X[k + 1])
-            fn = addmax(fleft, GE2, xleft)
-            gt = addmax(X[k], d2, BETA2)
-            x = (max3(gt, en, fn) + GO2C) & 0xFFFFFFFF
-            X[k], E[k], xleft, fleft = x, en, x, fn
-            for h, jb in enumerate(jobs):
-                i = j + jb["dlo"] + k
-                if j <= jb["rows"] and i >= 0:
-                    v = lo16(x) if h == 0 else hi16(x)
-                    assert 0 <= v <= 254
-                    out[h][(i, j)] = v
+            cell(j, k)
+        j += 1
     return out
 
 
@@ -224,6 +247,7 @@ def test_paired_band_pass_and_walk_match_the_oracle(scoring, alphabet):
         for p in pair:
             p["B"] = Bp
         hts = pair_pass(pair, Bp, a, b, o, e)
+        assert pair_pass(pair, Bp, a, b, o, e, two_rows=True) == hts   # the two-row order
         for h, p in enumerate(pair):
             out = band_walk(hts[h], p, a, b, o, e)
             assert out is not None, (p["cig"], scoring)
